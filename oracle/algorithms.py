@@ -1,0 +1,188 @@
+"""Deterministic and randomized Tucker algorithms of Secs. 3-5, plain FP64.
+
+Each function follows the paper's steps in its order and notation; dense
+linear algebra is delegated to NumPy/LAPACK (QR = Householder, SVD = gesdd).
+Random test matrices are inputs (explicit arrays), never drawn here, so the
+GPU path and this oracle can be run on identical Omegas.
+
+Readings taken where the paper is silent or garbled:
+* sketch width K_n = min(R_n + p, I_n, J_n) with J_n the number of columns of
+  the unfolding being sketched (oversampling of Remark 1 applied to Alg. 6);
+* the power iteration of Alg. 1 step 2 is evaluated as subspace iteration with
+  an orthonormalisation after every product (the stability note after Alg. 1):
+  Z = orth(A^T Q), Q = orth(A Z), q times;
+* Alg. 8 starts from S = X (its first line prints S = X_(n));
+* R-PET step 5 ("truncate") is a truncated HOSVD of the small recovered core,
+  whose factors are lifted through Q_n.
+"""
+from __future__ import annotations
+
+from typing import Sequence
+
+import numpy as np
+
+from .tensor import fold, multi_ttm, ttm, unfold
+
+
+def orth(y: np.ndarray) -> np.ndarray:
+    """Orthonormal basis of range(Y) from the economic QR Y = QR (Sec. 3.1)."""
+    q, _ = np.linalg.qr(np.asarray(y, dtype=np.float64), mode="reduced")
+    return q
+
+
+def sketch_width(r: int, p: int, i_n: int, j_n: int) -> int:
+    """K_n = min(R_n + p, I_n, J_n)."""
+    return int(min(r + p, i_n, j_n))
+
+
+def brsvd(a: np.ndarray, r: int, q: int, omega: np.ndarray, return_q: bool = False):
+    """Algorithm 1 (basic randomized SVD with oversampling and power iteration).
+
+    a      I x J data matrix
+    r      target rank R
+    q      number of power iterations
+    omega  J x K Gaussian test matrix, K = R + p (step 1, drawn by the caller)
+
+    Returns U = Q Ubar(:, 1:R) (I x R) and Ubar(:, 1:R)^T B = S V^T (R x J),
+    the latter being the projected unfolding used by STHOSVD (the shortcut
+    stated after Alg. 4).
+    """
+    a = np.asarray(a, dtype=np.float64)
+    y = a @ np.asarray(omega, dtype=np.float64)          # step 2, q = 0 part
+    qm = orth(y)                                         # step 3
+    for _ in range(q):                                   # step 2, (A A^T)^q A Omega
+        z = orth(a.T @ qm)
+        qm = orth(a @ z)
+    b = qm.T @ a                                         # step 4
+    ubar, _, _ = np.linalg.svd(b, full_matrices=False)   # step 5
+    ubar_r = ubar[:, :r]
+    u = qm @ ubar_r                                      # steps 6-7
+    out = (u, ubar_r.T @ b)
+    if return_q:
+        out = out + (qm,)
+    return out
+
+
+def leading_left_singular_vectors(a: np.ndarray, r: int) -> np.ndarray:
+    """Leading r left singular vectors of A (LAPACK SVD).  For a very wide A the
+    SVD is taken of the triangular factor of A^T = Q R (A = R^T Q^T has the same
+    left singular vectors), which avoids forming the huge right factor."""
+    a = np.asarray(a, dtype=np.float64)
+    if a.shape[1] > 8 * a.shape[0]:
+        a = np.linalg.qr(a.T, mode="r").T
+    u, _, _ = np.linalg.svd(a, full_matrices=False)
+    return u[:, :r]
+
+
+def thosvd(x: np.ndarray, ranks: Sequence[int]):
+    """Truncated HOSVD (Sec. 4): Q^(n) = leading R_n left singular vectors of X_(n),
+    S = X x_1 Q^(1)T ... x_N Q^(N)T (Eq. "Core")."""
+    us = [leading_left_singular_vectors(unfold(x, n), ranks[n]) for n in range(x.ndim)]
+    return multi_ttm(x, us, transpose=True), us
+
+
+def sthosvd(x: np.ndarray, ranks: Sequence[int]):
+    """Algorithm 4 (STHOSVD), fixed-rank form, ascending mode order."""
+    s = np.asarray(x, dtype=np.float64)
+    us = []
+    for n in range(s.ndim):
+        u = leading_left_singular_vectors(unfold(s, n), ranks[n])   # line 3
+        s = ttm(s, u.T, n)                                           # line 4
+        us.append(u)
+    return s, us
+
+
+def hooi_sweep(x: np.ndarray, us: Sequence[np.ndarray], ranks: Sequence[int]):
+    """One outer iteration of Algorithm 5 (HOOI): for each n in turn,
+    Z = X x_{p != n} Q^(p)T with the latest factors, Q^(n) = leading R_n left
+    singular vectors of Z_(n); then S = X x_1 Q^(1)T ... x_N Q^(N)T."""
+    us = list(us)
+    for n in range(x.ndim):
+        mats = [None if p == n else us[p].T for p in range(x.ndim)]
+        z = multi_ttm(x, mats)
+        us[n] = leading_left_singular_vectors(unfold(z, n), ranks[n])
+    return multi_ttm(x, us, transpose=True), us
+
+
+def hooi(x: np.ndarray, ranks: Sequence[int], sweeps: int = 20):
+    """HOOI initialised by the truncated HOSVD (Alg. 5), a fixed number of sweeps."""
+    _, us = thosvd(x, ranks)
+    g = None
+    for _ in range(sweeps):
+        g, us = hooi_sweep(x, us, ranks)
+    return g, us
+
+
+def rhosvd(x: np.ndarray, ranks: Sequence[int], q: int, omegas: Sequence[np.ndarray]):
+    """Algorithm 6 (RP-HOSVD) with each factor from Algorithm 1 on the original X:
+    Q^(n) from X_(n) Omega^(n) (J_n = prod_{k != n} I_k rows), then
+    S = X x_1 Q^(1)T ... x_N Q^(N)T."""
+    us = [brsvd(unfold(x, n), ranks[n], q, omegas[n])[0] for n in range(x.ndim)]
+    return multi_ttm(x, us, transpose=True), us
+
+
+def rsthosvd(x: np.ndarray, ranks: Sequence[int], q: int, omegas: Sequence[np.ndarray]):
+    """Algorithm 8 (R-STHOSVD): S = X; for n = 1..N apply Alg. 1 to S_(n) with target
+    rank R_n (Omega^(n) has prod_{k<n} R_k prod_{k>n} I_k rows) and set
+    S = S x_n Q^(n)T, i.e. S_(n) = Ubar_R^T B."""
+    s = np.asarray(x, dtype=np.float64)
+    us = []
+    for n in range(s.ndim):
+        u, sn = brsvd(unfold(s, n), ranks[n], q, omegas[n])
+        dims = list(s.shape)
+        dims[n] = ranks[n]
+        s = fold(sn, n, dims)
+        us.append(u)
+    return s, us
+
+
+def pinv_lstsq(a: np.ndarray) -> np.ndarray:
+    """Moore-Penrose pseudo-inverse of a full-column-rank A by least squares."""
+    a = np.asarray(a, dtype=np.float64)
+    sol, *_ = np.linalg.lstsq(a, np.eye(a.shape[0]), rcond=None)
+    return sol
+
+
+def rpet(x: np.ndarray, ranks: Sequence[int], omegas: Sequence[np.ndarray],
+         omegas_tilde: Sequence[np.ndarray]):
+    """Algorithm 9 (R-PET, single pass over X).
+
+    omegas[n]        J_n x K_n factor sketch matrices (J_n = prod_{k != n} I_k)
+    omegas_tilde[n]  S_n x I_n core sketch matrices, R_n <= K_n <= S_n
+    Steps: Y_n = X_(n) Omega_n; Q^(n) = QR(Y_n); H = X x_1 Omega~_1 ... x_N Omega~_N;
+    S = H x_1 (Omega~_1 Q^(1))^+ ... x_N (Omega~_N Q^(N))^+; truncate with a
+    truncated HOSVD of S: S ~ G x_n V_n, U_n = Q^(n) V_n.
+    Returns (G, U, extras) with extras holding Y, Q, H and the untruncated core.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    ys = [unfold(x, n) @ np.asarray(omegas[n], dtype=np.float64) for n in range(x.ndim)]
+    qs = [orth(y) for y in ys]
+    h = multi_ttm(x, [np.asarray(o, dtype=np.float64) for o in omegas_tilde])
+    c = multi_ttm(h, [pinv_lstsq(np.asarray(omegas_tilde[n], np.float64) @ qs[n])
+                      for n in range(x.ndim)])
+    g, vs = thosvd(c, ranks)
+    us = [qs[n] @ vs[n] for n in range(x.ndim)]
+    return g, us, {"Y": ys, "Q": qs, "H": h, "C": c}
+
+
+def omega_shapes(algo: str, dims: Sequence[int], ranks: Sequence[int], p: int,
+                 K: Sequence[int] | None = None, S: Sequence[int] | None = None):
+    """Sizes (rows, cols) of the Gaussian test matrices each algorithm consumes.
+
+    rhosvd / rpet: J_n = prod_{k != n} I_k rows; rsthosvd: prod_{k<n} R_k prod_{k>n} I_k.
+    rpet also returns the core sketch sizes (S_n, I_n)."""
+    dims = [int(d) for d in dims]
+    ranks = [int(r) for r in ranks]
+    nmodes = len(dims)
+    shapes = []
+    cur = list(dims)
+    for n in range(nmodes):
+        j_n = int(np.prod([cur[k] for k in range(nmodes) if k != n], dtype=np.int64))
+        k_n = int(K[n]) if K is not None else sketch_width(ranks[n], p, dims[n], j_n)
+        shapes.append((j_n, k_n))
+        if algo == "rsthosvd":
+            cur[n] = ranks[n]
+    if algo == "rpet":
+        tilde = [(int(S[n]) if S is not None else 2 * shapes[n][1] + 1, dims[n]) for n in range(nmodes)]
+        return shapes, tilde
+    return shapes
