@@ -1,0 +1,352 @@
+"""Benchmark: randomized Tucker decompositions per second on one GB300 per rank.
+
+Default workload: 512^3 FP32 tensor of multilinear rank (32,32,32) with a
+0.9^(i+j+k) core decay and 1e-4 relative noise, decomposed by R-STHOSVD
+(Alg. 8) with oversampling p = 10 and q = 1 power iteration, test matrices
+drawn on the device from seed 0.  One step = one full decomposition (all
+modes: Omega generation, sketches, power-iteration TTMs, orthonormalisations,
+projections, truncations, core).  X (512 MiB) is larger than L2, so no flush is
+needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on the host cores instead (the comparison arm of this project).
+Multi-GPU: every rank decomposes its own tensor (independent replicas, no
+data-path collective); value = all decompositions / slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+_CORES = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, str(_CORES))
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import WORKLOADS, device_layout  # noqa: E402
+
+METRIC = "decomps/s (R-STHOSVD 512^3 FP32, rank 32, p=10, q=1)"
+UNIT = "decomps/s"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path:
+                try:
+                    os.unlink(self.path)
+                except OSError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                if any(r[3].replace(".", "").isdigit() for r in rows) else None}
+
+
+def _traffic_for(kernel_src: str, key: str):
+    """DRAM bytes per launch from the committed ncu summary, valid only for the
+    kernel source it was captured on (null otherwise)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        data = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    h = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    ent = data.get(key)
+    if not ent or ent.get("source_sha") != h:
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def oracle_decompose(w, x32):
+    """Time one oracle decomposition (FP64 NumPy) with the generator's own test matrices."""
+    from oracle import algorithms as A
+    from oracle import philox
+    shapes = A.omega_shapes(w.algo, w.dims, w.ranks, w.p, K=w.K, S=w.S)
+    t0 = time.perf_counter()
+    if w.algo == "rpet":
+        fs, ts = shapes
+        N = len(w.dims)
+        om = [philox.omega(w.omega_seed, n, r, c).astype(np.float64) for n, (r, c) in enumerate(fs)]
+        ot = [philox.omega(w.omega_seed, N + n, r, c).astype(np.float64) for n, (r, c) in enumerate(ts)]
+        g, u, _ = A.rpet(x32, w.ranks, om, ot)
+    else:
+        om = [philox.omega(w.omega_seed, n, r, c).astype(np.float64) for n, (r, c) in enumerate(shapes)]
+        g, u = getattr(A, w.algo)(x32, w.ranks, w.q, om)
+    return time.perf_counter() - t0, g, u
+
+
+def run_reference(args, w, rank):
+    if rank != 0:
+        return
+    x = w.tensor()
+    x32 = np.asfortranarray(x.astype(np.float32).astype(np.float64))
+    del x
+    for _ in range(args.warmup):
+        oracle_decompose(w, x32)
+    times = [oracle_decompose(w, x32)[0] for _ in range(args.steps)]
+    total = sum(times)
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded low-rank tensor, seeded Philox test matrices)",
+        "config": {"workload": w.name, "dims": list(w.dims), "ranks": list(w.ranks), "p": w.p, "q": w.q,
+                   "algo": w.algo, "l2_flush": "input 512 MiB > L2"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _CORES, "kind": "oracle",
+                         "sample": f"full workload, {args.steps} decompositions"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="decay512_rsthosvd", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    w = WORKLOADS[args.workload]
+
+    if args.impl == "reference":
+        return run_reference(args, w, rank)
+
+    import torch
+    import paper_2001_07124_gb300 as pkg
+    from paper_2001_07124_gb300 import rhosvd as R
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pkg.build()
+    R.lib()
+
+    # each replica decomposes its own tensor (data seed + rank)
+    import dataclasses
+    wr = dataclasses.replace(w, seed=w.seed + rank)
+    x = wr.tensor()
+    x_host = torch.from_numpy(device_layout(x))
+    x32 = None
+    if rank == 0 and not args.no_cpu_baseline:
+        x32 = np.asfortranarray(x.astype(np.float32).astype(np.float64))
+    del x
+    X = x_host.cuda()
+    dims, ranks = w.dims, w.ranks
+    kw = dict(algo=w.algo, p=w.p, q=w.q, seed=w.omega_seed, K=w.K, S=w.S)
+    ws = R.Workspace(R.rhosvd_workspace_size(dims, ranks, w.algo, w.p, w.q, K=w.K, S=w.S))
+    G = R.empty_colmajor(ranks)
+    Us = [R.empty_colmajor((dims[n], ranks[n])) for n in range(len(dims))]
+    out = (G, Us)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        R.rhosvd_decompose(X, dims, ranks, ws=ws, out=out, check=False, **kw)
+
+    for _ in range(args.warmup):
+        step()
+    code, flags = R.rhosvd_device_status(ws)
+    if code != 0:
+        raise RuntimeError(f"device status {code} after warm-up")
+    st_words = ws.buf[:16].view(torch.int32).cpu().tolist()   # code, flags, orth_fail, fallbacks
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    # ---------------------------------------------------------------- timed region (device)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    clocks = clk.summary()
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    code, _ = R.rhosvd_device_status(ws)
+    if code != 0:
+        raise RuntimeError(f"device status {code} in timed region")
+    value = world * args.steps / (elapsed_ms / 1e3)
+
+    # ---------------------------------------------------------------- e2e through host buffers
+    g_host = torch.empty(G.numel(), dtype=torch.float32).pin_memory()
+    u_host = [torch.empty(u.numel(), dtype=torch.float32).pin_memory() for u in Us]
+    xh = x_host.pin_memory()
+    Xd = X
+
+    def e2e_step():
+        Xd.copy_(xh, non_blocking=True)
+        step()
+        g_host.copy_(G, non_blocking=True)
+        for a, b in zip(u_host, Us):
+            a.copy_(b, non_blocking=True)
+
+    e2e_steps = max(3, min(args.steps, 50))
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * e2e_steps / (e2e_ms / 1e3)
+    h2d = X.numel() * 4
+    d2h = (G.numel() + sum(u.numel() for u in Us)) * 4
+
+    # ---------------------------------------------------------------- dominant kernel: mode-1 sketch pass
+    peaks, peak_src = _peaks()
+    I0 = dims[0]
+    J0 = int(np.prod(dims)) // I0
+    Kp, _, _ = R.rhosvd_plan(dims, ranks, w.algo, w.p, w.q, K=w.K, S=w.S)
+    K0 = Kp[0]
+    om = R.rhosvd_omega(w.omega_seed, 0, J0, K0)
+    om_buf = om.t().contiguous().reshape(-1)
+    pws = R.Workspace(R.rhosvd_primitive_workspace_size(dims, K0))
+    Y0 = R.empty_colmajor((I0, K0))
+    reps = 50
+    for _ in range(3):
+        R.rhosvd_sketch(X, dims, 0, K0, Omega=om_buf, Y=Y0, ws=pws)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(reps):
+        R.rhosvd_sketch(X, dims, 0, K0, Omega=om_buf, Y=Y0, ws=pws)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    sk_ms = ev0.elapsed_time(ev1) / reps
+    sk_bytes = (X.numel() + J0 * K0 + I0 * K0) * 4      # X once, Omega_1 once, Y once
+    sk_gbs = sk_bytes / (sk_ms * 1e-3) / 1e9
+    hbm_peak = float(peaks["hbm_gbs"])
+    roofline = {"bound": "hbm", "kernel": "sketch_partial_kernel (mode-1 sketch Y = X_(1) Omega_1 + reduce)",
+                "achieved": round(sk_gbs, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(sk_gbs / hbm_peak, 4),
+                "peak_source": peak_src, "algorithmic_bytes_per_launch": sk_bytes, "ms_per_launch": sk_ms,
+                "traffic": _traffic_for(os.path.join(ROOT, "paper_2001_07124_gb300", "csrc", "sketch.cu"),
+                                        "sketch_mode1_512")}
+
+    # ---------------------------------------------------------------- CPU oracle and error gate
+    cpu = None
+    accuracy = None
+    if rank == 0 and x32 is not None:
+        from oracle import metrics as M
+        t_or, g_or, u_or = oracle_decompose(w, x32)
+        g_gpu = R.fortran_view(G, ranks).cpu().numpy().astype(np.float64)
+        u_gpu = [R.matrix(u, dims[n], ranks[n]).cpu().numpy().astype(np.float64) for n, u in enumerate(Us)]
+        e_gpu = M.rel_error(x32, g_gpu, u_gpu)
+        e_or = M.rel_error(x32, g_or, u_or)
+        sine = max(M.max_principal_sine(a, b) for a, b in zip(u_gpu, u_or))
+        accuracy = {"E_gpu": e_gpu, "E_oracle": e_or, "max_principal_sine": sine,
+                    "pass": bool(abs(e_gpu - e_or) <= 1e-5 and sine <= 1e-4)}
+        cpu = {"value": 1.0 / t_or, "unit": UNIT, "cores": _CORES, "kind": "oracle",
+               "sample": "one full 512^3 R-STHOSVD decomposition in FP64 NumPy (seeded Philox test matrices)"}
+
+    launches = R.rhosvd_launch_count(dims, ranks, w.algo, w.p, w.q, K=w.K, S=w.S)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded low-rank tensor, device-drawn Philox test matrices)",
+            "config": {"workload": w.name, "dims": list(dims), "ranks": list(ranks), "algo": w.algo, "p": w.p,
+                       "q": w.q, "parallelism": f"replicas{world}", "l2_flush": "input 512 MiB > 129 MB L2"},
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": launches * args.steps,
+            "roofline": roofline,
+            "cpu_baseline": cpu,
+            "accuracy": accuracy,
+            "householder_fallbacks_per_step": st_words[3],
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * rhosvd.h -- C ABI of the GB300 (sm_103a) randomized HOSVD / Tucker library.
+ *
+ * The library computes the hot path of randomized Tucker decomposition
+ * (Ahmadi-Asl et al., "Randomized Algorithms for Computation of Tucker
+ * Decomposition and Higher Order SVD (HOSVD)"): Gaussian mode-n sketches
+ * Y_n = X_(n) Omega_n, power-iteration TTMs, thin orthonormalisation Y_n -> Q_n,
+ * the core projection G = X x_1 Q_1^T ... x_N Q_N^T, and the single-pass
+ * variant (R-PET) that sketches every mode and the core from one read of X.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Layout.   An N-way tensor X of sizes (I_1..I_N) is a dense FP32 array stored
+ *           column-major, i_1 fastest (the column order of the n-unfolding,
+ *           Sec. 2).  A torch tensor of shape (I_N, ..., I_1), contiguous, has
+ *           this layout.  Matrices are column-major with the stated leading
+ *           dimension.  Mode indices are 0-based (mode n is the paper's n+1).
+ * Memory.   Every pointer named X, Y, Q, U, G, Omega, H or ws is a DEVICE
+ *           pointer owned by the caller.  The library never allocates or frees
+ *           device memory; it needs a caller-provided workspace `ws` of at
+ *           least the size reported by the matching *_workspace_size query
+ *           (256-byte aligned).  Host pointers are the shape/option structs,
+ *           the int arrays (ranks, K, S) and the pointer arrays themselves
+ *           (`const float* const*`), which are read before the call returns.
+ * Streams.  `stream` is a cudaStream_t (NULL = legacy default stream).  All
+ *           device work is enqueued on it; calls return without waiting for
+ *           the GPU unless stated otherwise.
+ * Errors.   Argument errors are detected on the host, before anything is
+ *           enqueued, and returned synchronously (RHOSVD_EINVAL, RHOSVD_ENOMEM
+ *           for a short workspace).  Conditions met on the GPU (non-finite
+ *           values, breakdown of the orthonormalisation even after its
+ *           Householder fallback, a bounded device wait that gave up) are
+ *           recorded in a status word at the start of `ws` and returned by
+ *           rhosvd_device_status(), which synchronises the stream.  No entry
+ *           point exits, aborts or traps.  Calls with distinct workspaces are
+ *           thread-safe; calls sharing a workspace must be stream-ordered.
+ */
+#ifndef RHOSVD_H
+#define RHOSVD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RHOSVD_MAX_MODES 8
+#define RHOSVD_MAX_K 128          /* largest sketch width K_n accepted */
+
+typedef enum rhosvd_status {
+  RHOSVD_OK = 0,
+  RHOSVD_EINVAL = 1,        /* invalid argument; nothing was enqueued */
+  RHOSVD_ENOMEM = 2,        /* workspace smaller than the size query reports */
+  RHOSVD_ECUDA = 3,         /* a CUDA runtime call failed (launch or sync) */
+  RHOSVD_ENONFINITE = 4,    /* a NaN/Inf reached a sketch or Gram matrix */
+  RHOSVD_EBREAKDOWN = 5,    /* orthonormalisation failed even after the fallback */
+  RHOSVD_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
+  RHOSVD_EUNSUPPORTED = 7   /* valid request outside what this build implements */
+} rhosvd_status;
+
+typedef enum rhosvd_algo {
+  RHOSVD_ALGO_RHOSVD = 0,     /* RP-HOSVD, Alg. 6, factors by Alg. 1 on the original X */
+  RHOSVD_ALGO_RSTHOSVD = 1,   /* R-STHOSVD, Alg. 8 (Alg. 1 on the shrinking core) */
+  RHOSVD_ALGO_RPET = 2        /* R-PET, Alg. 9 (single pass over X) */
+} rhosvd_algo;
+
+/* device status flags (bit set in the `flags` output of rhosvd_device_status) */
+#define RHOSVD_FLAG_FALLBACK 1    /* a Householder fallback ran in some orthonormalisation */
+
+typedef struct rhosvd_shape {
+  int32_t N;                          /* number of modes, 1..RHOSVD_MAX_MODES */
+  int64_t dims[RHOSVD_MAX_MODES];     /* I_1..I_N, each >= 1 */
+} rhosvd_shape;
+
+typedef struct rhosvd_opts {
+  int32_t algo;                       /* rhosvd_algo */
+  int32_t p;                          /* oversampling p >= 0 (Remark 1) */
+  int32_t q;                          /* power iterations q >= 0 (Remark 1) */
+  int32_t flags;                      /* reserved, 0 */
+  uint64_t seed;                      /* seed of the Gaussian test matrices */
+  int32_t K[RHOSVD_MAX_MODES];        /* R-PET factor sketch widths, 0 => R_n + p */
+  int32_t S[RHOSVD_MAX_MODES];        /* R-PET core sketch widths, 0 => 2 K_n + 1 */
+} rhosvd_opts;
+
+/* ---------------------------------------------------------------- sizing */
+
+/* Sketch widths a decomposition uses.  K_out[n] = min(R_n + p, I_n, J_n)
+ * where J_n is the number of columns of the unfolding that mode n sketches
+ * (prod_{k != n} I_k for RP-HOSVD and R-PET, prod_{k<n} R_k prod_{k>n} I_k for
+ * R-STHOSVD); for R-PET the opts.K/opts.S overrides apply and S_out[n] is the
+ * core sketch width (S_n >= K_n).  J_out[n] receives J_n.  Any output
+ * pointer may be NULL.  Returns RHOSVD_EINVAL on an invalid request. */
+rhosvd_status rhosvd_plan(const rhosvd_shape* shape, const int32_t* ranks, const rhosvd_opts* opts,
+                          int32_t* K_out, int32_t* S_out, int64_t* J_out);
+
+/* Workspace bytes rhosvd_decompose needs for this request (0 on invalid input). */
+size_t rhosvd_workspace_size(const rhosvd_shape* shape, const int32_t* ranks, const rhosvd_opts* opts);
+
+/* Number of kernel launches one rhosvd_decompose of this request enqueues
+ * with seed-drawn test matrices (-1 on invalid input); for profiling. */
+int64_t rhosvd_launch_count(const rhosvd_shape* shape, const int32_t* ranks, const rhosvd_opts* opts);
+
+/* Workspace bytes the primitive calls (sketch, sketch_all, power, orth, core)
+ * need on a tensor of this shape with sketch widths up to Kmax. */
+size_t rhosvd_primitive_workspace_size(const rhosvd_shape* shape, int32_t Kmax);
+
+/* ---------------------------------------------------------------- primitives */
+
+/* Gaussian test matrix (Alg. 1 step 1; Omega_n of Alg. 6 and Alg. 9):
+ * Omega(j, k), j < rows, k < cols, written at Omega[j + k*ld] (ld >= rows).
+ * Entry (j,k) is a deterministic function of (seed, stream_id, j, k):
+ * Philox4x32-10 (Salmon et al. 2011) on counter (j mod 2^32, j div 2^32,
+ * k div 4, stream_id) with key (seed mod 2^32, seed div 2^32), its four words
+ * turned into four normals by Box-Muller on 24-bit uniforms.  Inside
+ * rhosvd_decompose mode n draws Omega_n on stream_id n and the R-PET core
+ * sketch Omega~_n on stream_id N + n. */
+rhosvd_status rhosvd_omega(uint64_t seed, uint32_t stream_id, int64_t rows, int32_t cols,
+                           float* Omega, int64_t ld, void* stream);
+
+/* Mode-n sketch Y = X_(n) Omega (Alg. 1 step 2 with q = 0; Alg. 6 line 3;
+ * Alg. 9 line 1).  Omega is J_n x K with leading dimension J_n
+ * (J_n = prod_{k != mode} I_k); if Omega is NULL it is drawn from
+ * (seed, stream_id = mode) as in rhosvd_omega.  Y is I_mode x K, ld = I_mode. */
+rhosvd_status rhosvd_sketch(const float* X, const rhosvd_shape* shape, int32_t mode, int32_t K,
+                            uint64_t seed, const float* Omega, float* Y,
+                            void* ws, size_t ws_bytes, void* stream);
+
+/* Every sketch R-PET needs (Alg. 9 lines 1 and 3): Y[n] = X_(n) Omega_n
+ * (I_n x K[n], ld = I_n) for all n, and, if H is not NULL, the core sketch
+ * H = X x_1 Omega~_1 ... x_N Omega~_N (S[0] x ... x S[N-1], column-major) with
+ * Omega~_n of size S[n] x I_n (ld = S[n]).  NULL Omega / Omega_tilde arrays
+ * (or NULL entries) are drawn from the seed on stream_ids n and N + n. */
+rhosvd_status rhosvd_sketch_all(const float* X, const rhosvd_shape* shape, const int32_t* K,
+                                const int32_t* S, uint64_t seed,
+                                const float* const* Omega, const float* const* Omega_tilde,
+                                float* const* Y, float* H, void* ws, size_t ws_bytes, void* stream);
+
+/* One power iteration of Alg. 1 step 2 in its stable form (the remark after
+ * Alg. 1): on entry Y_inout holds an I_n x K matrix Q with orthonormal
+ * columns; the call forms Z = orth(X_(n)^T Q) (J_n x K) and writes the new
+ * sketch X_(n) Z into Y_inout (not orthonormalised; call rhosvd_orth). */
+rhosvd_status rhosvd_power(const float* X, const rhosvd_shape* shape, int32_t mode, int32_t K,
+                           float* Y_inout, void* ws, size_t ws_bytes, void* stream);
+
+/* Thin orthonormalisation Y = QR, Q overwriting Y (Alg. 1 step 3).  Y is
+ * m x K, leading dimension ld >= m, K <= RHOSVD_MAX_K, m >= K.  Method:
+ * CholeskyQR2 (Yamamoto et al. 2015) with an FP64-accurate Gram; if a
+ * Cholesky pivot is non-positive or too small, a Householder QR (the LAPACK
+ * geqr2/org2r sequence) runs instead.  If fallback_used is not NULL the call
+ * synchronises the stream and stores 1 there when the fallback ran. */
+rhosvd_status rhosvd_orth(float* Y, int64_t m, int32_t K, int64_t ld, int32_t* fallback_used,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* Core projection G = X x_1 Q_1^T x_2 ... x_N Q_N^T (Eq. "Core"; Alg. 6
+ * line 5).  Q[n] is I_n x K[n] with ld = I_n; a NULL Q[n] skips mode n
+ * (requires K[n] == I_n, the small-mode remark of Sec. 4).  G is
+ * K[0] x ... x K[N-1], column-major. */
+rhosvd_status rhosvd_core(const float* X, const rhosvd_shape* shape, const float* const* Q,
+                          const int32_t* K, float* G, void* ws, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------- driver */
+
+/* Full randomized Tucker decomposition [[G; U_1..U_N]] of X with multilinear
+ * rank (R_1..R_N) by the algorithm in opts->algo (Alg. 6 + Alg. 1, Alg. 8, or
+ * Alg. 9 with a truncated HOSVD of the recovered core).  U[n] is I_n x R_n
+ * (ld = I_n) with orthonormal columns; G is R_1 x ... x R_N column-major.
+ * Omega (nullable, or NULL entries) supplies explicit test matrices with the
+ * sizes rhosvd_plan reports (J_n x K_n, ld = J_n); missing ones are drawn
+ * from opts->seed.  Omega_tilde likewise supplies the R-PET core sketches
+ * (S_n x I_n, ld = S_n).  Requires 1 <= R_n <= min(I_n, J_n). */
+rhosvd_status rhosvd_decompose(const float* X, const rhosvd_shape* shape, const int32_t* ranks,
+                               const rhosvd_opts* opts, const float* const* Omega,
+                               const float* const* Omega_tilde, float* const* U, float* G,
+                               void* ws, size_t ws_bytes, void* stream);
+
+/* Synchronise `stream`, read the device status word kept at the start of `ws`
+ * and return the first error recorded there by earlier calls (RHOSVD_OK if
+ * none); `flags` (nullable) receives the RHOSVD_FLAG_* bits.  The word is
+ * cleared at the start of every rhosvd_decompose and primitive call. */
+rhosvd_status rhosvd_device_status(const void* ws, size_t ws_bytes, void* stream, int32_t* flags);
+
+/* Static description of a status code. */
+const char* rhosvd_status_string(rhosvd_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RHOSVD_H */

@@ -1,0 +1,826 @@
+// C ABI of the randomized HOSVD library: argument validation, workspace
+// planning and the algorithm drivers (RP-HOSVD = Alg. 6 with Alg. 1 per mode,
+// R-STHOSVD = Alg. 8, R-PET = Alg. 9).  Every driver is written once and run
+// either "dry" (only carving the workspace, to size it) or for real, so the
+// size query and the execution can never disagree.  All device work goes to
+// the caller's stream; nothing here synchronises except rhosvd_device_status
+// and rhosvd_orth with a non-NULL fallback_used.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rhosvd {
+namespace {
+
+constexpr size_t ALIGN = 256;
+
+struct Ctx {
+  bool dry = true;
+  char* base = nullptr;
+  size_t off = 0, high = 0;
+  cudaStream_t s = nullptr;
+  DevStatus* st = nullptr;
+  cudaError_t err = cudaSuccess;
+  int64_t launches = 0;   // kernels enqueued (counted in dry runs too)
+
+  template <class T>
+  T* take(size_t n) {
+    off = (off + ALIGN - 1) / ALIGN * ALIGN;
+    T* p = dry ? nullptr : reinterpret_cast<T*>(base + off);
+    off += std::max<size_t>(n, 1) * sizeof(T);
+    high = std::max(high, off);
+    return p;
+  }
+  void check(cudaError_t e) {
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+  }
+};
+
+struct Scope {   // stack discipline for temporaries
+  Ctx& c;
+  size_t saved;
+  explicit Scope(Ctx& c_) : c(c_), saved(c_.off) {}
+  ~Scope() { c.off = saved; }
+};
+
+struct Geom {
+  int N = 0;
+  int64_t d[RHOSVD_MAX_MODES] = {0};
+  int64_t L(int n) const { int64_t v = 1; for (int k = 0; k < n; ++k) v *= d[k]; return v; }
+  int64_t Rt(int n) const { int64_t v = 1; for (int k = n + 1; k < N; ++k) v *= d[k]; return v; }
+  int64_t J(int n) const { return L(n) * Rt(n); }
+  int64_t numel() const { int64_t v = 1; for (int k = 0; k < N; ++k) v *= d[k]; return v; }
+};
+
+View mode_view(const float* p, const Geom& g, int n) {
+  View v;
+  v.p = p;
+  v.L = g.L(n);
+  v.I = g.d[n];
+  v.Rt = g.Rt(n);
+  v.s_i = v.L;
+  v.s_r = v.L * v.I;
+  return v;
+}
+// A tall column-major matrix (m x K, ld) seen as the mode-2 unfolding of an
+// (m, K) tensor: X(i = column, j = row).
+View matrix_view(const float* p, int64_t m, int K, int64_t ld) {
+  View v;
+  v.p = p;
+  v.L = m;
+  v.I = K;
+  v.Rt = 1;
+  v.s_i = ld;
+  v.s_r = 0;
+  return v;
+}
+
+// ------------------------------------------------------------------ primitive ops
+
+// Y (I x K, ld) = X_(n) W with W(j,k) = w.p[l + r*w_r + k*w_k]
+void op_sketch(Ctx& c, const View& x, const WView& w, int K, float* Y, int64_t ldy) {
+  Scope sc(c);
+  SketchPlan pl = plan_sketch(x.I, K, x.L * x.Rt);
+  float* part = c.take<float>(sketch_partial_floats(pl, x.I, K));
+  c.launches += 2;
+  if (!c.dry) c.check(launch_sketch(x, w, K, Y, ldy, part, c.s));
+}
+
+// Gd (I x I, FP64) = X_(n) W accumulated in double-float
+void op_gram_df(Ctx& c, const View& x, const WView& w, int K, double* Gd) {
+  Scope sc(c);
+  SketchPlan pl = plan_sketch(x.I, K, x.L * x.Rt);
+  double* part = c.take<double>(sketch_partial_floats(pl, x.I, K));
+  c.launches += 2;
+  if (!c.dry) c.check(launch_sketch_df(x, w, K, Gd, x.I, part, c.s));
+}
+
+void op_gram_matrix(Ctx& c, const float* A, int64_t m, int K, int64_t ld, double* Gd) {
+  WView w{A, 0, ld};
+  op_gram_df(c, matrix_view(A, m, K, ld), w, K, Gd);
+}
+
+void op_ttm(Ctx& c, const View& x, const float* M, int64_t m_i, int64_t m_k, int K, const OView& out,
+            const DevStatus* skip = nullptr) {
+  if (x.L * x.Rt > 0 && K > 0) c.launches += 1;
+  if (!c.dry) c.check(launch_ttm(x, M, m_i, m_k, K, out, skip, c.s));
+}
+
+// CholeskyQR2 with device-side Householder fallback, in place on Y (m x K, ld)
+void op_orth(Ctx& c, float* Y, int64_t m, int K, int64_t ld) {
+  Scope sc(c);
+  double* G = c.take<double>((size_t)K * K);
+  float* Rinv = c.take<float>((size_t)K * K);
+  const View yv = matrix_view(Y, m, K, ld);
+  const OView yo{Y, ld, 0};
+  for (int pass = 0; pass < 2; ++pass) {
+    op_gram_matrix(c, Y, m, K, ld, G);
+    c.launches += 1;
+    if (!c.dry) c.check(launch_chol_inv(G, K, Rinv, pass, 0, c.st, c.s));
+    op_ttm(c, yv, Rinv, 1, K, K, yo, c.st);
+  }
+  c.launches += 1;
+  if (!c.dry) c.check(launch_householder(Y, m, K, ld, c.st, false, c.s));
+}
+
+// Leading R eigenvectors (K x R) of the Gram of a tall matrix Bt (m x K, ld)
+void op_truncate(Ctx& c, const float* Bt, int64_t m, int K, int64_t ld, int R, float* Ub) {
+  Scope sc(c);
+  double* G = c.take<double>((size_t)K * K);
+  op_gram_matrix(c, Bt, m, K, ld, G);
+  c.launches += 1;
+  if (!c.dry) c.check(launch_small_eig(G, K, R, Ub, nullptr, c.st, c.s));
+}
+
+void op_omega(Ctx& c, uint64_t seed, uint32_t stream_id, int64_t rows, int cols, float* out) {
+  c.launches += 1;
+  if (!c.dry) c.check(launch_omega(seed, stream_id, rows, cols, out, rows, c.s));
+}
+
+// ------------------------------------------------------------------ Alg. 1 on one mode
+
+struct ModeResult {
+  float* Q;     // I x K orthonormal (ld I)
+  float* Bt;    // J x K: Bt(j, k) = (Q^T X_(n))(k, j)   (Z layout, ld J)
+  float* Ub;    // K x R leading eigenvectors of B B^T
+};
+
+// Steps 1-5 of Alg. 1 on the mode-n unfolding of the tensor at x (geometry g):
+// sketch, orth, q power iterations, projection B, truncation of B B^T.
+// Buffers Yb (I x K), Zb (J x K), Om (J x K, unless explicit) and Ub (K x R)
+// belong to the caller.
+void alg1_mode(Ctx& c, const float* x, const Geom& g, int n, int K, int R, int q, uint64_t seed,
+               const float* omega_explicit, float* Yb, float* Zb, float* Om, float* Ub) {
+  const View xv = mode_view(x, g, n);
+  const int64_t I = g.d[n], L = g.L(n), J = g.J(n);
+  const float* W = omega_explicit;
+  if (W == nullptr) {
+    op_omega(c, seed, (uint32_t)n, J, K, Om);
+    W = Om;
+  }
+  op_sketch(c, xv, WView{W, L, J}, K, Yb, I);            // Y = X_(n) Omega
+  op_orth(c, Yb, I, K, I);                               // Q = orth(Y)
+  const OView zo{Zb, J, L};                              // Z(j,k) at j + k*J
+  for (int it = 0; it < q; ++it) {
+    op_ttm(c, xv, Yb, 1, I, K, zo);                      // Z = X_(n)^T Q
+    op_orth(c, Zb, J, K, J);                             // Z = orth(Z)
+    op_sketch(c, xv, WView{Zb, L, J}, K, Yb, I);         // Y = X_(n) Z
+    op_orth(c, Yb, I, K, I);                             // Q = orth(Y)
+  }
+  op_ttm(c, xv, Yb, 1, I, K, zo);                        // B^T = X_(n)^T Q
+  op_truncate(c, Zb, J, K, J, R, Ub);                    // Ubar_R of B
+}
+
+// U (I x R) = Q Ub
+void lift_factor(Ctx& c, const float* Q, int64_t I, int K, const float* Ub, int R, float* U) {
+  op_ttm(c, matrix_view(Q, I, K, I), Ub, 1, K, R, OView{U, I, 0});
+}
+
+// S_new[l, a, r] = sum_k Ub(k, a) Bt(l + L r, k): the shortcut S_(n) = Ubar_R^T B
+void refold_core(Ctx& c, const float* Bt, const Geom& g, int n, int K, const float* Ub, int R, float* Snew) {
+  const int64_t L = g.L(n), J = g.J(n);
+  View bv;
+  bv.p = Bt;
+  bv.L = L;
+  bv.I = K;
+  bv.Rt = g.Rt(n);
+  bv.s_i = J;
+  bv.s_r = L;
+  op_ttm(c, bv, Ub, 1, K, R, OView{Snew, L, L * R});
+}
+
+// T = X x_n M^T with M (I_n x K, m_i/m_k strides): output dims d[n] -> K
+void ttm_mode(Ctx& c, const float* x, const Geom& g, int n, const float* M, int64_t m_i, int64_t m_k, int K,
+              float* out) {
+  const int64_t L = g.L(n);
+  op_ttm(c, mode_view(x, g, n), M, m_i, m_k, K, OView{out, L, L * K});
+}
+
+// ------------------------------------------------------------------ widths
+
+struct Plan {
+  int K[RHOSVD_MAX_MODES];
+  int S[RHOSVD_MAX_MODES];
+  int64_t J[RHOSVD_MAX_MODES];
+};
+
+rhosvd_status validate_shape(const rhosvd_shape* sh, Geom& g) {
+  if (sh == nullptr || sh->N < 1 || sh->N > RHOSVD_MAX_MODES) return RHOSVD_EINVAL;
+  g.N = sh->N;
+  int64_t tot = 1;
+  for (int n = 0; n < g.N; ++n) {
+    if (sh->dims[n] < 1 || sh->dims[n] > (int64_t(1) << 40)) return RHOSVD_EINVAL;
+    g.d[n] = sh->dims[n];
+    if (tot > (int64_t(1) << 62) / g.d[n]) return RHOSVD_EINVAL;
+    tot *= g.d[n];
+  }
+  return RHOSVD_OK;
+}
+
+rhosvd_status make_plan(const Geom& g, const int32_t* ranks, const rhosvd_opts* o, Plan& pl) {
+  if (ranks == nullptr || o == nullptr) return RHOSVD_EINVAL;
+  if (o->algo < RHOSVD_ALGO_RHOSVD || o->algo > RHOSVD_ALGO_RPET) return RHOSVD_EINVAL;
+  if (o->p < 0 || o->q < 0 || o->q > 64) return RHOSVD_EINVAL;
+  int64_t cur[RHOSVD_MAX_MODES];
+  for (int n = 0; n < g.N; ++n) cur[n] = g.d[n];
+  for (int n = 0; n < g.N; ++n) {
+    int64_t J = 1;
+    for (int k = 0; k < g.N; ++k)
+      if (k != n) J *= cur[k];
+    const int64_t R = ranks[n];
+    if (R < 1 || R > g.d[n] || R > J) return RHOSVD_EINVAL;
+    int64_t K;
+    if (o->algo == RHOSVD_ALGO_RPET && o->K[n] > 0) K = o->K[n];
+    else K = std::min<int64_t>(R + o->p, std::min<int64_t>(g.d[n], J));
+    if (K < R || K > g.d[n] || K > J || K > RHOSVD_MAX_K) return RHOSVD_EINVAL;
+    pl.K[n] = (int)K;
+    pl.J[n] = J;
+    pl.S[n] = 0;
+    if (o->algo == RHOSVD_ALGO_RPET) {
+      int64_t S = o->S[n] > 0 ? o->S[n] : 2 * K + 1;
+      if (S < K || S > (int64_t(1) << 20)) return RHOSVD_EINVAL;
+      pl.S[n] = (int)S;
+    }
+    if (o->algo == RHOSVD_ALGO_RSTHOSVD) cur[n] = R;
+  }
+  return RHOSVD_OK;
+}
+
+// ------------------------------------------------------------------ drivers
+
+void run_rsthosvd(Ctx& c, const float* X, const Geom& g0, const int32_t* ranks, const Plan& pl, int q,
+                  uint64_t seed, const float* const* Omega, float* const* U, float* G) {
+  size_t max_jk = 1, max_ik = 1, max_s = 1, max_kk = 1;
+  {
+    Geom g = g0;
+    for (int n = 0; n < g.N; ++n) {
+      max_jk = std::max<size_t>(max_jk, (size_t)g.J(n) * pl.K[n]);
+      max_ik = std::max<size_t>(max_ik, (size_t)g.d[n] * pl.K[n]);
+      max_kk = std::max<size_t>(max_kk, (size_t)pl.K[n] * ranks[n]);
+      g.d[n] = ranks[n];
+      max_s = std::max<size_t>(max_s, (size_t)g.numel());
+    }
+  }
+  float* Yb = c.take<float>(max_ik);
+  float* Zb = c.take<float>(max_jk);
+  float* Ub = c.take<float>(max_kk);
+  bool need_om = false;
+  for (int n = 0; n < g0.N; ++n) need_om |= (Omega == nullptr || Omega[n] == nullptr);
+  float* Om = need_om ? c.take<float>(max_jk) : nullptr;
+  float* Sb[2] = {c.take<float>(max_s), c.take<float>(max_s)};
+  Geom g = g0;
+  const float* cur = X;
+  int ping = 0;
+  for (int n = 0; n < g.N; ++n) {
+    const int K = pl.K[n], R = ranks[n];
+    const int64_t I = g.d[n];
+    const bool last = (n == g.N - 1);
+    if (R == I) {   // nothing to reduce in this mode (the small-mode remark of Sec. 4)
+      c.launches += 1;
+      if (!c.dry) c.check(launch_fill_identity(U[n], I, R, c.s));
+      if (last && !c.dry) c.check(cudaMemcpyAsync(G, cur, sizeof(float) * g.numel(), cudaMemcpyDeviceToDevice, c.s));
+      continue;
+    }
+    const float* om = (Omega != nullptr) ? Omega[n] : nullptr;
+    alg1_mode(c, cur, g, n, K, R, q, seed, om, Yb, Zb, Om, Ub);
+    lift_factor(c, Yb, I, K, Ub, R, U[n]);
+    float* dst = last ? G : Sb[ping];
+    refold_core(c, Zb, g, n, K, Ub, R, dst);
+    g.d[n] = R;
+    cur = dst;
+    ping ^= 1;
+  }
+}
+
+void run_rhosvd(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const Plan& pl, int q,
+                uint64_t seed, const float* const* Omega, float* const* U, float* G) {
+  size_t max_jk = 1, max_ik = 1, max_kk = 1;
+  for (int n = 0; n < g.N; ++n) {
+    max_jk = std::max<size_t>(max_jk, (size_t)g.J(n) * pl.K[n]);
+    max_ik = std::max<size_t>(max_ik, (size_t)g.d[n] * pl.K[n]);
+    max_kk = std::max<size_t>(max_kk, (size_t)pl.K[n] * ranks[n]);
+  }
+  // core chain sizes: T_n = X x_1 U_1^T ... x_n U_n^T
+  size_t max_t = 1;
+  {
+    Geom t = g;
+    for (int n = 0; n < g.N; ++n) {
+      t.d[n] = ranks[n];
+      max_t = std::max<size_t>(max_t, (size_t)t.numel());
+    }
+  }
+  float* Yb = c.take<float>(max_ik);
+  float* Zb = c.take<float>(max_jk);
+  float* Ub = c.take<float>(max_kk);
+  bool need_om = false;
+  for (int n = 0; n < g.N; ++n) need_om |= (Omega == nullptr || Omega[n] == nullptr);
+  float* Om = need_om ? c.take<float>(max_jk) : nullptr;
+  float* Tb[2] = {c.take<float>(max_t), c.take<float>(max_t)};
+  // factors of modes N-1..1 first, mode 0 last so its projection B_1 (still in
+  // Zb) gives the first core step X x_1 U_1^T = Ubar^T B_1 without a pass over X
+  const float* chain = X;
+  Geom t = g;
+  int ping = 0;
+  for (int n = g.N - 1; n >= 0; --n) {
+    const int K = pl.K[n], R = ranks[n];
+    const int64_t I = g.d[n];
+    if (R == I) {
+      c.launches += 1;
+      if (!c.dry) c.check(launch_fill_identity(U[n], I, R, c.s));
+      continue;
+    }
+    const float* om = (Omega != nullptr) ? Omega[n] : nullptr;
+    alg1_mode(c, X, g, n, K, R, q, seed, om, Yb, Zb, Om, Ub);
+    lift_factor(c, Yb, I, K, Ub, R, U[n]);
+    if (n == 0) {
+      float* dst = (g.N == 1) ? G : Tb[ping];
+      refold_core(c, Zb, g, 0, K, Ub, R, dst);
+      t.d[0] = R;
+      chain = dst;
+      ping ^= 1;
+    }
+  }
+  // remaining core steps S = T x_n U_n^T (Eq. "Core")
+  int last_reduced = -1;
+  for (int n = 1; n < g.N; ++n)
+    if (ranks[n] != g.d[n]) last_reduced = n;
+  for (int n = 1; n < g.N; ++n) {
+    const int R = ranks[n];
+    if (R == g.d[n]) continue;
+    float* dst = (n == last_reduced) ? G : Tb[ping];
+    ttm_mode(c, chain, t, n, U[n], 1, g.d[n], R, dst);
+    t.d[n] = R;
+    chain = dst;
+    ping ^= 1;
+  }
+  if (chain != G && !c.dry)
+    c.check(cudaMemcpyAsync(G, chain, sizeof(float) * t.numel(), cudaMemcpyDeviceToDevice, c.s));
+}
+
+// Core sketch chain H = X x_1 Omega~_1 ... x_N Omega~_N (Alg. 9 line 3).
+void core_sketch_chain(Ctx& c, const float* X, const Geom& g, const int* S, uint64_t seed,
+                       const float* const* Om_t, float* const* om_t_buf, float* H) {
+  size_t max_t = 1;
+  {
+    Geom t = g;
+    for (int n = 0; n < g.N; ++n) {
+      t.d[n] = S[n];
+      max_t = std::max<size_t>(max_t, (size_t)t.numel());
+    }
+  }
+  Scope sc(c);
+  float* Tb[2] = {c.take<float>(max_t), c.take<float>(max_t)};
+  Geom t = g;
+  const float* cur = X;
+  int ping = 0;
+  for (int n = 0; n < g.N; ++n) {
+    const float* om = (Om_t != nullptr && Om_t[n] != nullptr) ? Om_t[n] : om_t_buf[n];
+    float* dst = (n == g.N - 1) ? H : Tb[ping];
+    // M(i, s) = Omega~(s, i) at om[s + i*S]
+    ttm_mode(c, cur, t, n, om, S[n], 1, S[n], dst);
+    t.d[n] = S[n];
+    cur = dst;
+    ping ^= 1;
+  }
+}
+
+void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const Plan& pl, uint64_t seed,
+              const float* const* Omega, const float* const* Omega_t, float* const* U, float* G) {
+  const int N = g.N;
+  size_t max_jk = 1, max_kk = 1;
+  for (int n = 0; n < N; ++n) {
+    max_jk = std::max<size_t>(max_jk, (size_t)g.J(n) * pl.K[n]);
+    max_kk = std::max<size_t>(max_kk, (size_t)pl.K[n] * pl.K[n]);
+  }
+  float* Ys[RHOSVD_MAX_MODES];
+  float* Omt[RHOSVD_MAX_MODES];
+  float* Pt[RHOSVD_MAX_MODES];
+  float* Vb[RHOSVD_MAX_MODES];
+  for (int n = 0; n < N; ++n) {
+    Ys[n] = c.take<float>((size_t)g.d[n] * pl.K[n]);
+    const bool gen = (Omega_t == nullptr || Omega_t[n] == nullptr);
+    Omt[n] = gen ? c.take<float>((size_t)pl.S[n] * g.d[n]) : nullptr;
+    Pt[n] = c.take<float>((size_t)pl.S[n] * pl.K[n]);
+    Vb[n] = c.take<float>((size_t)pl.K[n] * ranks[n]);
+  }
+  bool need_om = false;
+  for (int n = 0; n < N; ++n) need_om |= (Omega == nullptr || Omega[n] == nullptr);
+  float* Om = need_om ? c.take<float>(max_jk) : nullptr;
+  Geom hs = g, cs = g;
+  for (int n = 0; n < N; ++n) {
+    hs.d[n] = pl.S[n];
+    cs.d[n] = pl.K[n];
+  }
+  float* H = c.take<float>((size_t)hs.numel());
+  size_t max_c = 1;
+  {
+    Geom t = hs;
+    for (int n = 0; n < N; ++n) {
+      t.d[n] = pl.K[n];
+      max_c = std::max<size_t>(max_c, (size_t)t.numel());
+    }
+  }
+  float* Cb[2] = {c.take<float>(max_c), c.take<float>(max_c)};
+  double* Gd = c.take<double>(max_kk);
+  float* Rinv = c.take<float>(max_kk);
+
+  // lines 1-2: factor sketches and their orthonormal bases
+  for (int n = 0; n < N; ++n) {
+    const float* W = (Omega != nullptr) ? Omega[n] : nullptr;
+    if (W == nullptr) {
+      op_omega(c, seed, (uint32_t)n, g.J(n), pl.K[n], Om);
+      W = Om;
+    }
+    op_sketch(c, mode_view(X, g, n), WView{W, g.L(n), g.J(n)}, pl.K[n], Ys[n], g.d[n]);
+    op_orth(c, Ys[n], g.d[n], pl.K[n], g.d[n]);
+  }
+  // line 3: core sketch
+  for (int n = 0; n < N; ++n)
+    if (Omt[n] != nullptr) op_omega(c, seed, (uint32_t)(N + n), pl.S[n], (int)g.d[n], Omt[n]);
+  core_sketch_chain(c, X, g, pl.S, seed, Omega_t, Omt, H);
+  // line 4: C = H x_n (Omega~_n Q_n)^+ with the pseudo-inverse from the normal
+  // equations (Omega~_n Q_n is a well-conditioned Gaussian-times-orthonormal
+  // matrix): P^T = A (A^T A)^-1 = (A R^-1) R^-T, R^T R = A^T A
+  Geom t = hs;
+  const float* cur = H;
+  int ping = 0;
+  for (int n = 0; n < N; ++n) {
+    const int K = pl.K[n], S = pl.S[n];
+    const int64_t I = g.d[n];
+    const float* om = (Omega_t != nullptr && Omega_t[n] != nullptr) ? Omega_t[n] : Omt[n];
+    float* A = Pt[n];
+    {
+      // A(s, k) = sum_i Omega~(s, i) Q(i, k)
+      View qv;
+      qv.p = Ys[n];
+      qv.L = 1;
+      qv.I = I;
+      qv.Rt = K;
+      qv.s_i = 1;
+      qv.s_r = I;
+      op_ttm(c, qv, om, S, 1, S, OView{A, 1, S});
+    }
+    op_gram_matrix(c, A, S, K, S, Gd);
+    c.launches += 1;
+    if (!c.dry) c.check(launch_chol_inv(Gd, K, Rinv, 0, RHOSVD_EBREAKDOWN, c.st, c.s));
+    op_ttm(c, matrix_view(A, S, K, S), Rinv, 1, K, K, OView{A, S, 0});     // A R^-1, in place
+    {
+      Scope sc(c);
+      float* T1 = c.take<float>((size_t)S * K);
+      if (!c.dry) c.check(cudaMemcpyAsync(T1, A, sizeof(float) * S * K, cudaMemcpyDeviceToDevice, c.s));
+      op_ttm(c, matrix_view(T1, S, K, S), Rinv, K, 1, K, OView{A, S, 0}); // (A R^-1) R^-T
+    }
+    float* dst = Cb[ping];
+    ttm_mode(c, cur, t, n, A, 1, S, K, dst);   // M(s, k) = P^T(s, k)
+    t.d[n] = K;
+    cur = dst;
+    ping ^= 1;
+  }
+  // line 5: truncated HOSVD of the recovered core C (K_1 x ... x K_N)
+  for (int n = 0; n < N; ++n) {
+    const int K = pl.K[n], R = ranks[n];
+    const int64_t L = cs.L(n), Rt = cs.Rt(n);
+    View cv;
+    cv.p = cur;
+    cv.L = L;
+    cv.I = K;
+    cv.Rt = Rt;
+    cv.s_i = L;
+    cv.s_r = L * K;
+    op_gram_df(c, cv, WView{cur, L * K, L}, K, Gd);
+    c.launches += 1;
+    if (!c.dry) c.check(launch_small_eig(Gd, K, R, Vb[n], nullptr, c.st, c.s));
+    lift_factor(c, Ys[n], g.d[n], K, Vb[n], R, U[n]);
+  }
+  Geom tc = cs;
+  const float* chain = cur;
+  float* bufs[2] = {Cb[0], Cb[1]};
+  int which = (cur == Cb[0]) ? 1 : 0;   // the buffer not holding C
+  for (int n = 0; n < N; ++n) {
+    float* dst = (n == N - 1) ? G : bufs[which];
+    ttm_mode(c, chain, tc, n, Vb[n], 1, pl.K[n], ranks[n], dst);
+    tc.d[n] = ranks[n];
+    chain = dst;
+    which ^= 1;
+  }
+}
+
+rhosvd_status finish(const Ctx& c) { return c.err == cudaSuccess ? RHOSVD_OK : RHOSVD_ECUDA; }
+
+rhosvd_status begin(Ctx& c, void* ws, size_t ws_bytes, void* stream) {
+  if (ws == nullptr || ws_bytes < sizeof(DevStatus) || (reinterpret_cast<uintptr_t>(ws) % ALIGN) != 0)
+    return RHOSVD_EINVAL;
+  c.dry = false;
+  c.base = static_cast<char*>(ws);
+  c.off = sizeof(DevStatus);
+  c.high = c.off;
+  c.s = static_cast<cudaStream_t>(stream);
+  c.st = static_cast<DevStatus*>(ws);
+  if (cudaMemsetAsync(ws, 0, sizeof(DevStatus), c.s) != cudaSuccess) return RHOSVD_ECUDA;
+  return RHOSVD_OK;
+}
+
+Ctx dry_ctx() {
+  Ctx c;
+  c.dry = true;
+  c.off = sizeof(DevStatus);
+  c.high = c.off;
+  return c;
+}
+
+size_t primitive_ws(const Geom& g, int Kmax) {
+  // largest temporaries of the primitive calls: Z (J x K), Omega (J x K),
+  // a core chain ping-pong, sketch partials and orth scratch
+  Ctx c = dry_ctx();
+  size_t max_jk = 1, max_n = (size_t)g.numel();
+  for (int n = 0; n < g.N; ++n) max_jk = std::max<size_t>(max_jk, (size_t)g.J(n) * Kmax);
+  c.take<float>(max_jk);
+  c.take<float>(max_jk);
+  c.take<float>(max_n);
+  c.take<float>(max_n);
+  size_t fixed = c.off;
+  size_t extra = 0;
+  for (int n = 0; n < g.N; ++n) {
+    SketchPlan pl = plan_sketch(g.d[n], Kmax, g.J(n));
+    extra = std::max(extra, sketch_partial_floats(pl, g.d[n], Kmax) * sizeof(double));
+    SketchPlan pz = plan_sketch(Kmax, Kmax, g.J(n));
+    extra = std::max(extra, sketch_partial_floats(pz, Kmax, Kmax) * sizeof(double));
+  }
+  extra += 4 * (size_t)RHOSVD_MAX_K * RHOSVD_MAX_K * sizeof(double) + 8 * ALIGN;
+  return fixed + extra;
+}
+
+}  // namespace
+}  // namespace rhosvd
+
+using namespace rhosvd;
+
+extern "C" {
+
+const char* rhosvd_status_string(rhosvd_status s) {
+  switch (s) {
+    case RHOSVD_OK: return "ok";
+    case RHOSVD_EINVAL: return "invalid argument";
+    case RHOSVD_ENOMEM: return "workspace too small";
+    case RHOSVD_ECUDA: return "CUDA runtime error";
+    case RHOSVD_ENONFINITE: return "non-finite value in the input or a sketch";
+    case RHOSVD_EBREAKDOWN: return "orthonormalisation breakdown";
+    case RHOSVD_ETIMEOUT: return "device wait timed out";
+    case RHOSVD_EUNSUPPORTED: return "unsupported request";
+  }
+  return "unknown status";
+}
+
+rhosvd_status rhosvd_plan(const rhosvd_shape* shape, const int32_t* ranks, const rhosvd_opts* opts,
+                          int32_t* K_out, int32_t* S_out, int64_t* J_out) {
+  Geom g;
+  rhosvd_status s = validate_shape(shape, g);
+  if (s != RHOSVD_OK) return s;
+  Plan pl;
+  s = make_plan(g, ranks, opts, pl);
+  if (s != RHOSVD_OK) return s;
+  for (int n = 0; n < g.N; ++n) {
+    if (K_out) K_out[n] = pl.K[n];
+    if (S_out) S_out[n] = pl.S[n];
+    if (J_out) J_out[n] = pl.J[n];
+  }
+  return RHOSVD_OK;
+}
+
+static size_t decompose_ws(const Geom& g, const int32_t* ranks, const rhosvd_opts* o, const Plan& pl,
+                           const float* const* Omega, const float* const* Omega_t) {
+  Ctx c = dry_ctx();
+  float* U[RHOSVD_MAX_MODES] = {nullptr};
+  if (o->algo == RHOSVD_ALGO_RSTHOSVD) run_rsthosvd(c, nullptr, g, ranks, pl, o->q, o->seed, Omega, U, nullptr);
+  else if (o->algo == RHOSVD_ALGO_RHOSVD) run_rhosvd(c, nullptr, g, ranks, pl, o->q, o->seed, Omega, U, nullptr);
+  else run_rpet(c, nullptr, g, ranks, pl, o->seed, Omega, Omega_t, U, nullptr);
+  return c.high;
+}
+
+int64_t rhosvd_launch_count(const rhosvd_shape* shape, const int32_t* ranks, const rhosvd_opts* opts) {
+  Geom g;
+  if (validate_shape(shape, g) != RHOSVD_OK) return -1;
+  Plan pl;
+  if (make_plan(g, ranks, opts, pl) != RHOSVD_OK) return -1;
+  Ctx c = dry_ctx();
+  float* U[RHOSVD_MAX_MODES] = {nullptr};
+  if (opts->algo == RHOSVD_ALGO_RSTHOSVD) run_rsthosvd(c, nullptr, g, ranks, pl, opts->q, opts->seed, nullptr, U, nullptr);
+  else if (opts->algo == RHOSVD_ALGO_RHOSVD) run_rhosvd(c, nullptr, g, ranks, pl, opts->q, opts->seed, nullptr, U, nullptr);
+  else run_rpet(c, nullptr, g, ranks, pl, opts->seed, nullptr, nullptr, U, nullptr);
+  return c.launches;
+}
+
+size_t rhosvd_workspace_size(const rhosvd_shape* shape, const int32_t* ranks, const rhosvd_opts* opts) {
+  Geom g;
+  if (validate_shape(shape, g) != RHOSVD_OK) return 0;
+  Plan pl;
+  if (make_plan(g, ranks, opts, pl) != RHOSVD_OK) return 0;
+  return decompose_ws(g, ranks, opts, pl, nullptr, nullptr);
+}
+
+size_t rhosvd_primitive_workspace_size(const rhosvd_shape* shape, int32_t Kmax) {
+  Geom g;
+  if (validate_shape(shape, g) != RHOSVD_OK || Kmax < 1 || Kmax > RHOSVD_MAX_K) return 0;
+  return primitive_ws(g, Kmax);
+}
+
+rhosvd_status rhosvd_omega(uint64_t seed, uint32_t stream_id, int64_t rows, int32_t cols, float* Omega,
+                           int64_t ld, void* stream) {
+  if (rows < 0 || cols < 0 || ld < rows || (Omega == nullptr && rows * (int64_t)cols > 0)) return RHOSVD_EINVAL;
+  if (rows == 0 || cols == 0) return RHOSVD_OK;
+  cudaError_t e = launch_omega(seed, stream_id, rows, cols, Omega, ld, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? RHOSVD_OK : RHOSVD_ECUDA;
+}
+
+rhosvd_status rhosvd_sketch(const float* X, const rhosvd_shape* shape, int32_t mode, int32_t K, uint64_t seed,
+                            const float* Omega, float* Y, void* ws, size_t ws_bytes, void* stream) {
+  Geom g;
+  rhosvd_status s = validate_shape(shape, g);
+  if (s != RHOSVD_OK) return s;
+  if (X == nullptr || Y == nullptr || mode < 0 || mode >= g.N || K < 1 || K > RHOSVD_MAX_K) return RHOSVD_EINVAL;
+  if (ws_bytes < primitive_ws(g, K)) return RHOSVD_ENOMEM;
+  Ctx c;
+  if ((s = begin(c, ws, ws_bytes, stream)) != RHOSVD_OK) return s;
+  const int64_t J = g.J(mode);
+  const float* W = Omega;
+  if (W == nullptr) {
+    float* Om = c.take<float>((size_t)J * K);
+    op_omega(c, seed, (uint32_t)mode, J, K, Om);
+    W = Om;
+  }
+  op_sketch(c, mode_view(X, g, mode), WView{W, g.L(mode), J}, K, Y, g.d[mode]);
+  return finish(c);
+}
+
+rhosvd_status rhosvd_sketch_all(const float* X, const rhosvd_shape* shape, const int32_t* K, const int32_t* S,
+                                uint64_t seed, const float* const* Omega, const float* const* Omega_tilde,
+                                float* const* Y, float* H, void* ws, size_t ws_bytes, void* stream) {
+  Geom g;
+  rhosvd_status s = validate_shape(shape, g);
+  if (s != RHOSVD_OK) return s;
+  if (X == nullptr || K == nullptr || Y == nullptr || (H != nullptr && S == nullptr)) return RHOSVD_EINVAL;
+  int kmax = 1;
+  for (int n = 0; n < g.N; ++n) {
+    if (K[n] < 1 || K[n] > RHOSVD_MAX_K || Y[n] == nullptr) return RHOSVD_EINVAL;
+    if (H != nullptr && (S[n] < 1 || S[n] > (1 << 20))) return RHOSVD_EINVAL;
+    kmax = std::max(kmax, (int)K[n]);
+  }
+  // core sketch chain needs two ping-pong tensors and the generated Omega~
+  size_t need = primitive_ws(g, kmax);
+  if (H != nullptr) {
+    Geom t = g;
+    size_t mt = 1, om = 0;
+    for (int n = 0; n < g.N; ++n) {
+      t.d[n] = S[n];
+      mt = std::max<size_t>(mt, (size_t)t.numel());
+      om += ((size_t)S[n] * g.d[n] * sizeof(float) + ALIGN);
+    }
+    need += 2 * (mt * sizeof(float) + ALIGN) + om;
+  }
+  if (ws_bytes < need) return RHOSVD_ENOMEM;
+  Ctx c;
+  if ((s = begin(c, ws, ws_bytes, stream)) != RHOSVD_OK) return s;
+  {
+    Scope sc(c);
+    for (int n = 0; n < g.N; ++n) {
+      const int64_t J = g.J(n);
+      const float* W = (Omega != nullptr) ? Omega[n] : nullptr;
+      Scope inner(c);
+      if (W == nullptr) {
+        float* Om = c.take<float>((size_t)J * K[n]);
+        op_omega(c, seed, (uint32_t)n, J, K[n], Om);
+        W = Om;
+      }
+      op_sketch(c, mode_view(X, g, n), WView{W, g.L(n), J}, K[n], Y[n], g.d[n]);
+    }
+  }
+  if (H != nullptr) {
+    float* Omt[RHOSVD_MAX_MODES] = {nullptr};
+    for (int n = 0; n < g.N; ++n) {
+      if (Omega_tilde == nullptr || Omega_tilde[n] == nullptr) {
+        Omt[n] = c.take<float>((size_t)S[n] * g.d[n]);
+        op_omega(c, seed, (uint32_t)(g.N + n), S[n], (int)g.d[n], Omt[n]);
+      }
+    }
+    int Si[RHOSVD_MAX_MODES];
+    for (int n = 0; n < g.N; ++n) Si[n] = S[n];
+    core_sketch_chain(c, X, g, Si, seed, Omega_tilde, Omt, H);
+  }
+  return finish(c);
+}
+
+rhosvd_status rhosvd_power(const float* X, const rhosvd_shape* shape, int32_t mode, int32_t K, float* Y_inout,
+                           void* ws, size_t ws_bytes, void* stream) {
+  Geom g;
+  rhosvd_status s = validate_shape(shape, g);
+  if (s != RHOSVD_OK) return s;
+  if (X == nullptr || Y_inout == nullptr || mode < 0 || mode >= g.N || K < 1 || K > RHOSVD_MAX_K ||
+      K > g.d[mode] || K > g.J(mode))
+    return RHOSVD_EINVAL;
+  if (ws_bytes < primitive_ws(g, K)) return RHOSVD_ENOMEM;
+  Ctx c;
+  if ((s = begin(c, ws, ws_bytes, stream)) != RHOSVD_OK) return s;
+  const View xv = mode_view(X, g, mode);
+  const int64_t I = g.d[mode], L = g.L(mode), J = g.J(mode);
+  float* Zb = c.take<float>((size_t)J * K);
+  op_ttm(c, xv, Y_inout, 1, I, K, OView{Zb, J, L});
+  op_orth(c, Zb, J, K, J);
+  op_sketch(c, xv, WView{Zb, L, J}, K, Y_inout, I);
+  return finish(c);
+}
+
+rhosvd_status rhosvd_orth(float* Y, int64_t m, int32_t K, int64_t ld, int32_t* fallback_used, void* ws,
+                          size_t ws_bytes, void* stream) {
+  if (Y == nullptr || K < 1 || K > RHOSVD_MAX_K || m < K || ld < m) return RHOSVD_EINVAL;
+  Geom g;
+  g.N = 2;
+  g.d[0] = m;
+  g.d[1] = K;
+  if (ws_bytes < primitive_ws(g, K)) return RHOSVD_ENOMEM;
+  Ctx c;
+  rhosvd_status s;
+  if ((s = begin(c, ws, ws_bytes, stream)) != RHOSVD_OK) return s;
+  op_orth(c, Y, m, K, ld);
+  if (c.err != cudaSuccess) return RHOSVD_ECUDA;
+  if (fallback_used != nullptr) {
+    int32_t flags = 0;
+    s = rhosvd_device_status(ws, ws_bytes, stream, &flags);
+    *fallback_used = (flags & RHOSVD_FLAG_FALLBACK) ? 1 : 0;
+    return s;
+  }
+  return RHOSVD_OK;
+}
+
+rhosvd_status rhosvd_core(const float* X, const rhosvd_shape* shape, const float* const* Q, const int32_t* K,
+                          float* G, void* ws, size_t ws_bytes, void* stream) {
+  Geom g;
+  rhosvd_status s = validate_shape(shape, g);
+  if (s != RHOSVD_OK) return s;
+  if (X == nullptr || Q == nullptr || K == nullptr || G == nullptr) return RHOSVD_EINVAL;
+  for (int n = 0; n < g.N; ++n) {
+    if (K[n] < 1 || K[n] > g.d[n]) return RHOSVD_EINVAL;
+    if (Q[n] == nullptr && K[n] != g.d[n]) return RHOSVD_EINVAL;
+  }
+  Geom t = g;
+  size_t mt = 1;
+  for (int n = 0; n < g.N; ++n) {
+    t.d[n] = K[n];
+    mt = std::max<size_t>(mt, (size_t)t.numel());
+  }
+  if (ws_bytes < sizeof(DevStatus) + 2 * (mt * sizeof(float) + ALIGN)) return RHOSVD_ENOMEM;
+  Ctx c;
+  if ((s = begin(c, ws, ws_bytes, stream)) != RHOSVD_OK) return s;
+  float* Tb[2] = {c.take<float>(mt), c.take<float>(mt)};
+  int last = -1;
+  for (int n = 0; n < g.N; ++n)
+    if (Q[n] != nullptr) last = n;
+  Geom cur_g = g;
+  const float* cur = X;
+  int ping = 0;
+  for (int n = 0; n < g.N; ++n) {
+    if (Q[n] == nullptr) continue;
+    float* dst = (n == last) ? G : Tb[ping];
+    ttm_mode(c, cur, cur_g, n, Q[n], 1, g.d[n], K[n], dst);
+    cur_g.d[n] = K[n];
+    cur = dst;
+    ping ^= 1;
+  }
+  if (last < 0 && !c.dry)
+    c.check(cudaMemcpyAsync(G, X, sizeof(float) * g.numel(), cudaMemcpyDeviceToDevice, c.s));
+  return finish(c);
+}
+
+rhosvd_status rhosvd_decompose(const float* X, const rhosvd_shape* shape, const int32_t* ranks,
+                               const rhosvd_opts* opts, const float* const* Omega, const float* const* Omega_tilde,
+                               float* const* U, float* G, void* ws, size_t ws_bytes, void* stream) {
+  Geom g;
+  rhosvd_status s = validate_shape(shape, g);
+  if (s != RHOSVD_OK) return s;
+  Plan pl;
+  if ((s = make_plan(g, ranks, opts, pl)) != RHOSVD_OK) return s;
+  if (X == nullptr || U == nullptr || G == nullptr) return RHOSVD_EINVAL;
+  for (int n = 0; n < g.N; ++n)
+    if (U[n] == nullptr) return RHOSVD_EINVAL;
+  if (ws_bytes < decompose_ws(g, ranks, opts, pl, Omega, Omega_tilde)) return RHOSVD_ENOMEM;
+  Ctx c;
+  if ((s = begin(c, ws, ws_bytes, stream)) != RHOSVD_OK) return s;
+  if (opts->algo == RHOSVD_ALGO_RSTHOSVD) run_rsthosvd(c, X, g, ranks, pl, opts->q, opts->seed, Omega, U, G);
+  else if (opts->algo == RHOSVD_ALGO_RHOSVD) run_rhosvd(c, X, g, ranks, pl, opts->q, opts->seed, Omega, U, G);
+  else run_rpet(c, X, g, ranks, pl, opts->seed, Omega, Omega_tilde, U, G);
+  return finish(c);
+}
+
+rhosvd_status rhosvd_device_status(const void* ws, size_t ws_bytes, void* stream, int32_t* flags) {
+  if (ws == nullptr || ws_bytes < sizeof(DevStatus)) return RHOSVD_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return RHOSVD_ECUDA;
+  DevStatus h;
+  if (cudaMemcpy(&h, ws, sizeof(DevStatus), cudaMemcpyDeviceToHost) != cudaSuccess) return RHOSVD_ECUDA;
+  if (flags) *flags = h.flags;
+  return static_cast<rhosvd_status>(h.code);
+}
+
+}  // extern "C"

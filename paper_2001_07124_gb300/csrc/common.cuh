@@ -1,0 +1,126 @@
+// Shared device-side definitions for the randomized HOSVD kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rhosvd.h"
+
+namespace rhosvd {
+
+// ---------------------------------------------------------------- status word
+// The first 256 bytes of every workspace hold a DevStatus.  Kernels record the
+// first error they meet with atomicCAS (so the earliest error wins) and OR
+// informational flags; the host reads the block back in rhosvd_device_status.
+struct DevStatus {
+  int32_t code;           // rhosvd_status of the first device-detected error
+  int32_t flags;          // RHOSVD_FLAG_* bits
+  int32_t orth_fail;      // set by a Cholesky pass that broke down, cleared per orth call
+  int32_t fallbacks;      // number of Householder fallbacks that ran
+  int32_t fallback_rows;  // rows m of the last matrix that needed the fallback
+  int32_t pad[59];
+};
+static_assert(sizeof(DevStatus) == 256, "status block is 256 bytes");
+
+__device__ __forceinline__ void set_error(DevStatus* st, int32_t code) {
+  if (st) atomicCAS(&st->code, 0, code);
+}
+
+// ---------------------------------------------------------------- mode views
+// X of sizes (I_1..I_N), column-major, seen along mode n as a 3-way array
+// [L, I, Rt] with L = prod_{k<n} I_k and Rt = prod_{k>n} I_k.  Column j of the
+// unfolding X_(n) is j = l + L*r (Sec. 2 with 0-based indices), so
+// X_(n)(i, j) = X[l + L*i + L*I*r].
+struct ModeView {
+  int64_t L, I, Rt;
+  __host__ __device__ int64_t J() const { return L * Rt; }
+};
+
+// ---------------------------------------------------------------- df64 arithmetic
+// Double-float accumulation from FP32 products: TwoProd by FMA (the product
+// error is exact), TwoSum of Knuth; the pair (hi, lo) carries ~48 bits.
+// Ogita, Rump, Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 2005.
+struct df64 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+// acc += a*b, error-free product, compensated sum (Dot2 step).
+__device__ __forceinline__ void df64_fma(df64& acc, float a, float b) {
+  float p = a * b;
+  float pe = fmaf(a, b, -p);
+  float s, se;
+  two_sum(acc.hi, p, s, se);
+  acc.hi = s;
+  acc.lo += se + pe;
+}
+
+__device__ __forceinline__ double df64_to_double(df64 v) { return (double)v.hi + (double)v.lo; }
+
+// ---------------------------------------------------------------- warp helpers
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3",
+// SC 2011.  Round: (c0,c1,c2,c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2),
+// hi(M0 c0) ^ c3 ^ k1, lo(M0 c0)); the key advances by (W0, W1) between rounds.
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    uint32_t lo0 = M0 * c.x, hi0 = __umulhi(M0, c.x);
+    uint32_t lo1 = M1 * c.z, hi1 = __umulhi(M1, c.z);
+    U4 n;
+    n.x = hi1 ^ c.y ^ k0;
+    n.y = lo1;
+    n.z = hi0 ^ c.w ^ k1;
+    n.w = lo0;
+    c = n;
+  }
+  return c;
+}
+
+// Box-Muller (1958) on 24-bit uniforms: u1 = (a+1) 2^-24 in (0,1], u2 = b 2^-24.
+__device__ __forceinline__ void box_muller24(uint32_t wa, uint32_t wb, float& z0, float& z1) {
+  float u1 = (float)((wa >> 8) + 1u) * 5.9604644775390625e-8f;   // exact
+  float u2 = (float)(wb >> 8) * 5.9604644775390625e-8f;           // exact
+  float r = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  z0 = r * c;
+  z1 = r * s;
+}
+
+// Omega(j, k) of (seed, stream): four normals per counter (j, k/4).
+__device__ __forceinline__ void omega_quad(uint64_t seed, uint32_t stream, uint64_t j, uint32_t kq,
+                                           float out[4]) {
+  U4 c{(uint32_t)j, (uint32_t)(j >> 32), kq, stream};
+  U4 w = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  box_muller24(w.x, w.y, out[0], out[1]);
+  box_muller24(w.z, w.w, out[2], out[3]);
+}
+
+}  // namespace rhosvd

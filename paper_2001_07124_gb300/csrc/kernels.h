@@ -1,0 +1,86 @@
+// Host-side launchers of the device kernels (one translation unit each family).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rhosvd.h"
+
+namespace rhosvd {
+
+struct DevStatus;
+
+// Raise a kernel's dynamic shared memory limit to `bytes`, once per device and
+// kernel (the attribute is process-wide; setting it on every launch costs host time).
+cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes);
+
+// Strided view of a contraction operand: entry (i, j) with j = l + L*r lives at
+// base[l + i*s_i + r*s_r]; l in [0,L), r in [0,Rt), i in [0,I).
+struct View {
+  const float* p;
+  int64_t L, I, Rt;
+  int64_t s_i, s_r;
+};
+
+// Tall operand W(j, k) = base[l + r*w_r + k*w_k] with the same j = l + L*r split.
+struct WView {
+  const float* p;
+  int64_t w_r, w_k;
+};
+
+// Output of a TTM: Out(j, k) at base[l + k*o_k + r*o_r].
+struct OView {
+  float* p;
+  int64_t o_k, o_r;
+};
+
+// ---- sketch.cu
+// Split plan of a sketch Y(i,k) = sum_j X(i,j) W(j,k).
+struct SketchPlan {
+  int tiles_i, tiles_k, splits;
+  int64_t jchunk;
+};
+SketchPlan plan_sketch(int64_t I, int K, int64_t J);
+size_t sketch_partial_floats(const SketchPlan& pl, int64_t I, int K);
+
+// Y = X_(n) W in FP32 (partials in ws_part, deterministic fixed-order reduction).
+cudaError_t launch_sketch(const View& x, const WView& w, int K, float* Y, int64_t ldy,
+                          float* ws_part, cudaStream_t st);
+// G = X_(n) W accumulated in double-float, reduced in FP64 to Gd (K x I... as I x K, ld = I).
+cudaError_t launch_sketch_df(const View& x, const WView& w, int K, double* Gd, int64_t ldg,
+                             double* ws_part, cudaStream_t st);
+
+// Out(j,k) = sum_i X(i,j) M(i,k), M(i,k) = Mp[i*m_i + k*m_k].  In-place on the
+// X buffer is allowed when Out addresses only rows j of X's own columns.
+cudaError_t launch_ttm(const View& x, const float* Mp, int64_t m_i, int64_t m_k, int K,
+                       const OView& out, const DevStatus* skip_if_orth_fail, cudaStream_t st);
+
+// ---- omega.cu
+cudaError_t launch_omega(uint64_t seed, uint32_t stream_id, int64_t rows, int cols, float* out,
+                         int64_t ld, cudaStream_t st);
+
+// ---- orth.cu
+// Cholesky of the K x K FP64 Gram G (ld K) into Rinv = R^{-1} (upper, FP32,
+// K x K column-major) with R^T R = G.  pass 0 writes orth_fail; pass 1 runs
+// only if orth_fail is clear.  Breakdown sets orth_fail and, if fail_code is
+// non-zero, records fail_code as the device error.
+cudaError_t launch_chol_inv(const double* G, int K, float* Rinv, int pass, int fail_code, DevStatus* st,
+                            cudaStream_t stream);
+// Householder QR of A (m x K, ld) into its Q factor, in place; runs only when
+// orth_fail is set (or always if force).
+cudaError_t launch_householder(float* A, int64_t m, int K, int64_t ld, DevStatus* st, bool force,
+                               cudaStream_t stream);
+// Fixed-order sum of FP64 partials: out[e] = sum_s part[s*n + e], e < n.
+cudaError_t launch_reduce_d(const double* part, int splits, int64_t n, double* out, cudaStream_t st);
+
+// ---- eig.cu
+// Leading R eigenvectors (descending) of the symmetric PSD K x K FP64 matrix
+// G: semidefinite Cholesky G = L L^T (FP64), then one-sided Jacobi on L^T in
+// FP32.  Ub is K x R (ld K); sv (nullable) receives sqrt(eigenvalues), K entries.
+cudaError_t launch_small_eig(const double* G, int K, int R, float* Ub, float* sv, DevStatus* st,
+                             cudaStream_t stream);
+
+// ---- misc
+cudaError_t launch_fill_identity(float* U, int64_t I, int R, cudaStream_t st);
+
+}  // namespace rhosvd

@@ -1,0 +1,50 @@
+// Gaussian test matrices Omega (Alg. 1 step 1) drawn from a counter-based
+// generator: entry (j, k) depends only on (seed, stream_id, j, k), so any
+// block of Omega can be produced by any thread in any order.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rhosvd {
+
+namespace {
+
+// One thread per (row j, group of four columns); rows are contiguous in memory.
+__global__ void omega_kernel(uint64_t seed, uint32_t stream_id, int64_t rows, int cols,
+                             float* __restrict__ out, int64_t ld) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.y;
+  if (j >= rows) return;
+  float z[4];
+  omega_quad(seed, stream_id, (uint64_t)j, (uint32_t)g, z);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int k = 4 * g + t;
+    if (k < cols) out[j + (int64_t)k * ld] = z[t];
+  }
+}
+
+__global__ void fill_identity_kernel(float* U, int64_t I, int R) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= I * R) return;
+  const int64_t c = e / I, r = e - c * I;
+  U[e] = (r == c) ? 1.f : 0.f;
+}
+
+}  // namespace
+
+cudaError_t launch_omega(uint64_t seed, uint32_t stream_id, int64_t rows, int cols, float* out, int64_t ld,
+                         cudaStream_t st) {
+  if (rows == 0 || cols == 0) return cudaSuccess;
+  dim3 grid((unsigned)((rows + 255) / 256), (unsigned)((cols + 3) / 4));
+  omega_kernel<<<grid, 256, 0, st>>>(seed, stream_id, rows, cols, out, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_identity(float* U, int64_t I, int R, cudaStream_t st) {
+  const int64_t n = I * R;
+  if (n == 0) return cudaSuccess;
+  fill_identity_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, I, R);
+  return cudaGetLastError();
+}
+
+}  // namespace rhosvd

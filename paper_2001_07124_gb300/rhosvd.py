@@ -1,0 +1,364 @@
+"""Python binding of librhosvd (argument marshalling only).
+
+Every step of the decomposition runs in the CUDA library; this module turns
+torch tensors into device pointers, sizes and the caller's CUDA stream, and
+checks status codes.  PyTorch provides device memory and streams only.
+
+Layout: a tensor of sizes (I_1..I_N) is column-major, i_1 fastest.  The
+functions accept a float32 CUDA tensor that is either contiguous (any shape
+with the right number of elements; a (I_N, ..., I_1) tensor is the natural
+one) or a Fortran-strided view of shape (I_1..I_N).  Matrices returned to the
+caller (factors U_n, sketches Y_n) are column-major I x K blocks exposed as
+(I, K) views; the core G is exposed as an (R_1..R_N) view of its column-major
+buffer.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Sequence
+
+import numpy as np
+
+from . import _build
+
+MAX_MODES = 8
+MAX_K = 128
+ALGOS = {"rhosvd": 0, "rsthosvd": 1, "rpet": 2}
+STATUS = {0: "RHOSVD_OK", 1: "RHOSVD_EINVAL", 2: "RHOSVD_ENOMEM", 3: "RHOSVD_ECUDA", 4: "RHOSVD_ENONFINITE",
+          5: "RHOSVD_EBREAKDOWN", 6: "RHOSVD_ETIMEOUT", 7: "RHOSVD_EUNSUPPORTED"}
+FLAG_FALLBACK = 1
+
+
+class RhosvdError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = int(code)
+        msg = lib().rhosvd_status_string(self.code).decode() if _LIB is not None else STATUS.get(code, "?")
+        super().__init__(f"{where}: {STATUS.get(self.code, self.code)} ({msg})")
+
+
+class Shape(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int32), ("dims", ctypes.c_int64 * MAX_MODES)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("algo", ctypes.c_int32), ("p", ctypes.c_int32), ("q", ctypes.c_int32),
+                ("flags", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("K", ctypes.c_int32 * MAX_MODES), ("S", ctypes.c_int32 * MAX_MODES)]
+
+
+_LIB = None
+_P = ctypes.c_void_p
+_PP = ctypes.POINTER(ctypes.c_void_p)
+_I32P = ctypes.POINTER(ctypes.c_int32)
+_I64P = ctypes.POINTER(ctypes.c_int64)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load librhosvd.so; raise if it has not been built (there is no fallback)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"librhosvd.so is not built ({path}); call paper_2001_07124_gb300.build() first")
+    L = ctypes.CDLL(path)
+    st = ctypes.c_int
+    sig = {
+        "rhosvd_plan": (st, [ctypes.POINTER(Shape), _I32P, ctypes.POINTER(Opts), _I32P, _I32P, _I64P]),
+        "rhosvd_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(Shape), _I32P, ctypes.POINTER(Opts)]),
+        "rhosvd_primitive_workspace_size": (ctypes.c_size_t, [ctypes.POINTER(Shape), ctypes.c_int32]),
+        "rhosvd_launch_count": (ctypes.c_int64, [ctypes.POINTER(Shape), _I32P, ctypes.POINTER(Opts)]),
+        "rhosvd_omega": (st, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int64, ctypes.c_int32, _P,
+                              ctypes.c_int64, _P]),
+        "rhosvd_sketch": (st, [_P, ctypes.POINTER(Shape), ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P,
+                               _P, _P, ctypes.c_size_t, _P]),
+        "rhosvd_sketch_all": (st, [_P, ctypes.POINTER(Shape), _I32P, _I32P, ctypes.c_uint64, _PP, _PP, _PP,
+                                   _P, _P, ctypes.c_size_t, _P]),
+        "rhosvd_power": (st, [_P, ctypes.POINTER(Shape), ctypes.c_int32, ctypes.c_int32, _P, _P,
+                              ctypes.c_size_t, _P]),
+        "rhosvd_orth": (st, [_P, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, _I32P, _P, ctypes.c_size_t,
+                             _P]),
+        "rhosvd_core": (st, [_P, ctypes.POINTER(Shape), _PP, _I32P, _P, _P, ctypes.c_size_t, _P]),
+        "rhosvd_decompose": (st, [_P, ctypes.POINTER(Shape), _I32P, ctypes.POINTER(Opts), _PP, _PP, _PP, _P,
+                                  _P, ctypes.c_size_t, _P]),
+        "rhosvd_device_status": (st, [_P, ctypes.c_size_t, _P, _I32P]),
+        "rhosvd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = L
+    return L
+
+
+def declared_symbols() -> list[str]:
+    """Entry points declared in include/rhosvd.h, parsed from the header text."""
+    import re
+    hdr = os.path.join(_build.INCLUDE, "rhosvd.h")
+    text = open(hdr).read()
+    return sorted(set(re.findall(r"\b(rhosvd_[a-z_]+)\s*\(", text)))
+
+
+# ------------------------------------------------------------------ marshalling helpers
+
+def make_shape(dims: Sequence[int]) -> Shape:
+    dims = [int(d) for d in dims]
+    if not 1 <= len(dims) <= MAX_MODES:
+        raise ValueError("between 1 and 8 modes")
+    sh = Shape()
+    sh.N = len(dims)
+    for n, d in enumerate(dims):
+        sh.dims[n] = d
+    return sh
+
+
+def make_opts(algo: str = "rsthosvd", p: int = 10, q: int = 1, seed: int = 0,
+              K: Sequence[int] | None = None, S: Sequence[int] | None = None) -> Opts:
+    o = Opts()
+    o.algo = ALGOS[algo]
+    o.p, o.q, o.flags, o.seed = int(p), int(q), 0, int(seed) & 0xFFFFFFFFFFFFFFFF
+    for n in range(MAX_MODES):
+        o.K[n] = int(K[n]) if K is not None and n < len(K) else 0
+        o.S[n] = int(S[n]) if S is not None and n < len(S) else 0
+    return o
+
+
+def _i32(vals: Sequence[int]):
+    arr = (ctypes.c_int32 * max(1, len(vals)))(*[int(v) for v in vals])
+    return arr
+
+
+def _ptrs(tensors):
+    if tensors is None:
+        return None
+    arr = (ctypes.c_void_p * MAX_MODES)()
+    for n, t in enumerate(tensors):
+        arr[n] = None if t is None else _dptr(t)
+    return arr
+
+
+def _dptr(t) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise RhosvdError(code, where)
+
+
+def colmajor(x, dims: Sequence[int]):
+    """Validate that x holds a column-major FP32 CUDA tensor of sizes dims."""
+    import torch
+    n = int(np.prod(dims))
+    if x.dtype != torch.float32 or not x.is_cuda or x.numel() != n:
+        raise ValueError(f"expected a float32 CUDA tensor with {n} elements")
+    if x.is_contiguous():
+        return x
+    if tuple(x.shape) == tuple(dims) and x.permute(*reversed(range(x.dim()))).is_contiguous():
+        return x
+    raise ValueError("tensor is neither contiguous nor a Fortran-ordered view of dims")
+
+
+def fortran_view(buf, dims: Sequence[int]):
+    """(I_1..I_N) view of a column-major buffer."""
+    return buf.reshape(tuple(reversed([int(d) for d in dims]))).permute(*reversed(range(len(dims))))
+
+
+def empty_colmajor(dims: Sequence[int], device=None):
+    import torch
+    return torch.empty(int(np.prod(dims)), dtype=torch.float32, device=device or "cuda")
+
+
+def matrix(buf, rows: int, cols: int):
+    """(rows, cols) view of a column-major rows x cols buffer."""
+    return buf.reshape(int(cols), int(rows)).t()
+
+
+class Workspace:
+    """Caller-owned device workspace (the library itself never allocates)."""
+
+    def __init__(self, nbytes: int, device=None):
+        import torch
+        self.nbytes = int(max(nbytes, 256))
+        self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=device or "cuda")
+
+    @property
+    def ptr(self) -> int:
+        return self.buf.data_ptr()
+
+    def ensure(self, nbytes: int):
+        if nbytes > self.nbytes:
+            self.__init__(nbytes, self.buf.device)
+        return self
+
+
+# ------------------------------------------------------------------ entry points
+
+def rhosvd_plan(dims, ranks, algo="rsthosvd", p=10, q=1, K=None, S=None):
+    """(K_n, S_n, J_n) lists a decomposition uses."""
+    N = len(dims)
+    Ko, So, Jo = (ctypes.c_int32 * N)(), (ctypes.c_int32 * N)(), (ctypes.c_int64 * N)()
+    _check(lib().rhosvd_plan(ctypes.byref(make_shape(dims)), _i32(ranks),
+                             ctypes.byref(make_opts(algo, p, q, 0, K, S)), Ko, So, Jo), "rhosvd_plan")
+    return list(Ko), list(So), list(Jo)
+
+
+def rhosvd_workspace_size(dims, ranks, algo="rsthosvd", p=10, q=1, K=None, S=None) -> int:
+    return int(lib().rhosvd_workspace_size(ctypes.byref(make_shape(dims)), _i32(ranks),
+                                           ctypes.byref(make_opts(algo, p, q, 0, K, S))))
+
+
+def rhosvd_launch_count(dims, ranks, algo="rsthosvd", p=10, q=1, K=None, S=None) -> int:
+    return int(lib().rhosvd_launch_count(ctypes.byref(make_shape(dims)), _i32(ranks),
+                                         ctypes.byref(make_opts(algo, p, q, 0, K, S))))
+
+
+def rhosvd_primitive_workspace_size(dims, Kmax) -> int:
+    return int(lib().rhosvd_primitive_workspace_size(ctypes.byref(make_shape(dims)), int(Kmax)))
+
+
+def rhosvd_omega(seed: int, stream_id: int, rows: int, cols: int, out=None, stream=None):
+    """rows x cols Gaussian test matrix; returns the (rows, cols) column-major view."""
+    import torch
+    if out is None:
+        out = torch.empty(int(rows) * int(cols), dtype=torch.float32, device="cuda")
+    _check(lib().rhosvd_omega(int(seed), int(stream_id), int(rows), int(cols), _dptr(out), int(rows),
+                              _stream(stream)), "rhosvd_omega")
+    return matrix(out, rows, cols)
+
+
+def _ws_for(ws, nbytes):
+    if ws is None:
+        return Workspace(nbytes)
+    return ws.ensure(nbytes)
+
+
+def rhosvd_sketch(X, dims, mode: int, K: int, seed: int = 0, Omega=None, Y=None, ws=None, stream=None):
+    """Y = X_(mode) Omega (I_mode x K)."""
+    X = colmajor(X, dims)
+    I = int(dims[mode])
+    Y = empty_colmajor((I, K)) if Y is None else Y
+    ws = _ws_for(ws, rhosvd_primitive_workspace_size(dims, K))
+    om = None if Omega is None else _dptr(Omega)
+    _check(lib().rhosvd_sketch(_dptr(X), ctypes.byref(make_shape(dims)), int(mode), int(K), int(seed), om,
+                               _dptr(Y), ws.ptr, ws.nbytes, _stream(stream)), "rhosvd_sketch")
+    return matrix(Y, I, K)
+
+
+def rhosvd_sketch_all(X, dims, K, S=None, seed: int = 0, Omega=None, Omega_tilde=None, want_H=True,
+                      ws=None, stream=None):
+    """All mode sketches Y_n and (optionally) the core sketch H of R-PET."""
+    X = colmajor(X, dims)
+    N = len(dims)
+    Ys = [empty_colmajor((dims[n], K[n])) for n in range(N)]
+    H = empty_colmajor(S) if (want_H and S is not None) else None
+    need = rhosvd_primitive_workspace_size(dims, max(K))
+    if H is not None:
+        t = list(dims)
+        mt = 1
+        om = 0
+        for n in range(N):
+            t[n] = S[n]
+            mt = max(mt, int(np.prod(t)))
+            om += S[n] * dims[n] * 4 + 256
+        need += 2 * (mt * 4 + 256) + om
+    ws = _ws_for(ws, need)
+    _check(lib().rhosvd_sketch_all(_dptr(X), ctypes.byref(make_shape(dims)), _i32(K),
+                                   _i32(S) if S is not None else None, int(seed), _ptrs(Omega),
+                                   _ptrs(Omega_tilde), _ptrs(Ys), None if H is None else _dptr(H), ws.ptr,
+                                   ws.nbytes, _stream(stream)), "rhosvd_sketch_all")
+    Ys = [matrix(Ys[n], dims[n], K[n]) for n in range(N)]
+    return Ys, (None if H is None else fortran_view(H, S))
+
+
+def rhosvd_power(X, dims, mode: int, Q, ws=None, stream=None):
+    """One stable power step: returns X_(n) orth(X_(n)^T Q) (I x K)."""
+    X = colmajor(X, dims)
+    I, K = int(Q.shape[0]), int(Q.shape[1])
+    buf = Q.t().contiguous().reshape(-1).clone()
+    ws = _ws_for(ws, rhosvd_primitive_workspace_size(dims, K))
+    _check(lib().rhosvd_power(_dptr(X), ctypes.byref(make_shape(dims)), int(mode), K, _dptr(buf), ws.ptr,
+                              ws.nbytes, _stream(stream)), "rhosvd_power")
+    return matrix(buf, I, K)
+
+
+def rhosvd_orth(Y, ws=None, stream=None, report_fallback=False):
+    """Orthonormalise the columns of Y (m x K, given as an (m, K) tensor); returns (Q, fallback)."""
+    m, K = int(Y.shape[0]), int(Y.shape[1])
+    buf = Y.t().contiguous().reshape(-1).clone()
+    ws = _ws_for(ws, rhosvd_primitive_workspace_size((m, K), K))
+    fb = ctypes.c_int32(0)
+    _check(lib().rhosvd_orth(_dptr(buf), m, K, m, ctypes.byref(fb) if report_fallback else None, ws.ptr,
+                             ws.nbytes, _stream(stream)), "rhosvd_orth")
+    return matrix(buf, m, K), (bool(fb.value) if report_fallback else None)
+
+
+def rhosvd_core(X, dims, Qs, ws=None, stream=None):
+    """G = X x_1 Q_1^T ... x_N Q_N^T; Qs[n] is (I_n, K_n) or None to skip the mode."""
+    X = colmajor(X, dims)
+    N = len(dims)
+    K = [int(dims[n]) if Qs[n] is None else int(Qs[n].shape[1]) for n in range(N)]
+    qbufs = [None if q is None else q.t().contiguous().reshape(-1) for q in Qs]
+    G = empty_colmajor(K)
+    t = list(dims)
+    mt = 1
+    for n in range(N):
+        t[n] = K[n]
+        mt = max(mt, int(np.prod(t)))
+    ws = _ws_for(ws, 256 + 2 * (mt * 4 + 256))
+    _check(lib().rhosvd_core(_dptr(X), ctypes.byref(make_shape(dims)), _ptrs(qbufs), _i32(K), _dptr(G),
+                             ws.ptr, ws.nbytes, _stream(stream)), "rhosvd_core")
+    return fortran_view(G, K)
+
+
+def rhosvd_decompose(X, dims, ranks, algo="rsthosvd", p=10, q=1, seed=0, Omega=None, Omega_tilde=None,
+                     K=None, S=None, ws=None, out=None, stream=None, check=True):
+    """Randomized Tucker decomposition; returns (G as an (R_1..R_N) view, [U_n as (I_n, R_n) views]).
+
+    Omega / Omega_tilde: optional lists of explicit test matrices as column-major
+    buffers (rows x cols) with the sizes rhosvd_plan reports.  ``out``: optional
+    (G_buf, [U_bufs]) preallocated buffers.  ``check``: synchronise and raise on
+    a device-detected error."""
+    X = colmajor(X, dims)
+    N = len(dims)
+    shape, opts = make_shape(dims), make_opts(algo, p, q, seed, K, S)
+    r = _i32(ranks)
+    if out is None:
+        G = empty_colmajor(ranks)
+        Us = [empty_colmajor((dims[n], ranks[n])) for n in range(N)]
+    else:
+        G, Us = out
+    need = int(lib().rhosvd_workspace_size(ctypes.byref(shape), r, ctypes.byref(opts)))
+    if need == 0:
+        _check(1, "rhosvd_workspace_size")
+    ws = _ws_for(ws, need)
+    code = lib().rhosvd_decompose(_dptr(X), ctypes.byref(shape), r, ctypes.byref(opts), _ptrs(Omega),
+                                  _ptrs(Omega_tilde), _ptrs(Us), _dptr(G), ws.ptr, ws.nbytes, _stream(stream))
+    _check(code, "rhosvd_decompose")
+    if check:
+        dev, _ = rhosvd_device_status(ws, stream)
+        _check(dev, "rhosvd_decompose (device)")
+    return fortran_view(G, ranks), [matrix(Us[n], dims[n], ranks[n]) for n in range(N)]
+
+
+def rhosvd_device_status(ws, stream=None):
+    flags = ctypes.c_int32(0)
+    code = lib().rhosvd_device_status(ws.ptr, ws.nbytes, _stream(stream), ctypes.byref(flags))
+    return int(code), int(flags.value)

@@ -1,0 +1,346 @@
+"""CUDA path vs the FP64 oracle, element by element or by subspace, through the C ABI.
+
+Tolerances (derived in the design doc):
+* sketches / TTMs (FP32 arithmetic, long sums): |gpu - oracle| <= 1e-5 * (|A| |B|)
+  elementwise, i.e. relative to the sum of absolute products;
+* Gaussian test matrices: |gpu - oracle| <= 2^-21 max(1, |z|) (FP32 logf/sincospi
+  against an FP64 evaluation rounded once);
+* decompositions (factors are defined only up to rotations): per mode the
+  largest principal-angle sine between GPU and oracle factors <= 1e-4, and
+  |E_gpu - E_oracle| <= 1e-5 with E the explicit FP64 relative error on the
+  same FP32-rounded input; factors orthonormal to 1e-5.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import algorithms as A  # noqa: E402
+from oracle import metrics as M  # noqa: E402
+from oracle import philox  # noqa: E402
+from oracle import tensor as T  # noqa: E402
+from workloads import WORKLOADS, device_layout, gaussian_matrix, lowrank_tensor, random_tensor  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2001_07124_gb300 as pkg
+    pkg.build()
+    pkg.rhosvd.lib()
+    torch.cuda.set_device(0)
+
+
+def R():
+    from paper_2001_07124_gb300 import rhosvd
+    return rhosvd
+
+
+def dev(x):
+    return torch.from_numpy(device_layout(np.asarray(x))).cuda()
+
+
+def dev_mat(m):
+    return torch.from_numpy(np.asfortranarray(m, dtype=np.float32).ravel(order="F")).cuda()
+
+
+def f32(x):
+    return np.asfortranarray(np.asarray(x).astype(np.float32).astype(np.float64))
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def assert_close_abs(got, want, bound, rel=1e-5):
+    err = np.abs(got - want)
+    lim = rel * bound + 1e-30
+    bad = err > lim
+    assert not bad.any(), f"{bad.sum()} entries off, worst ratio {np.max(err / lim):.3g}"
+
+
+# ------------------------------------------------------------------ a1: Omega generator
+
+@pytest.mark.parametrize("seed,stream,rows,cols", [(0, 0, 5000, 13), (0x1234_5678_9ABC_DEF0, 7, 3001, 4),
+                                                   (42, 3, 777, 42)])
+def test_omega_matches_oracle_generator(seed, stream, rows, cols):
+    got = host(R().rhosvd_omega(seed, stream, rows, cols))
+    want = philox.omega(seed, stream, rows, cols).astype(np.float64)
+    assert got.shape == want.shape
+    err = np.abs(got - want) / np.maximum(1.0, np.abs(want))
+    assert err.max() <= 2.0 ** -21, err.max()
+
+
+# ------------------------------------------------------------------ a2: sketch
+
+SKETCH_CASES = [((67, 45, 83), 17), ((9, 10, 11, 12), 5), ((130, 70), 64), ((3, 70, 5), 3),
+                ((100, 20, 30), 70), ((50, 1, 40), 1)]
+
+
+@pytest.mark.parametrize("dims,K", SKETCH_CASES)
+def test_sketch_parity_explicit_omega(dims, K):
+    x = random_tensor(dims, 1)
+    X = dev(x)
+    x32 = f32(x)
+    for n in range(len(dims)):
+        J = int(np.prod(dims)) // dims[n]
+        Kn = min(K, dims[n])
+        om = gaussian_matrix(10 + n, J, Kn)
+        Y = host(R().rhosvd_sketch(X, dims, n, Kn, Omega=dev_mat(om)))
+        a = T.unfold(x32, n)
+        want = a @ om.astype(np.float64)
+        assert_close_abs(Y, want, np.abs(a) @ np.abs(om.astype(np.float64)))
+
+
+def test_sketch_seeded_omega_vs_oracle_generator():
+    dims = (40, 33, 29)
+    x = random_tensor(dims, 2)
+    X = dev(x)
+    x32 = f32(x)
+    for n in range(3):
+        J = int(np.prod(dims)) // dims[n]
+        om = philox.omega(99, n, J, 11).astype(np.float64)
+        Y = host(R().rhosvd_sketch(X, dims, n, 11, seed=99))
+        a = T.unfold(x32, n)
+        assert_close_abs(Y, a @ om, np.abs(a) @ np.abs(om))
+
+
+# ------------------------------------------------------------------ TTM / core projection
+
+@pytest.mark.parametrize("dims,K", [((67, 45, 83), (7, 45, 12)), ((9, 10, 11, 12), (3, 4, 5, 6)),
+                                    ((200, 3, 150), (70, 3, 65))])
+def test_core_projection_parity(dims, K):
+    x = random_tensor(dims, 3)
+    x32 = f32(x)
+    rng = np.random.default_rng(4)
+    qs = [None if K[n] == dims[n] else rng.standard_normal((dims[n], K[n])).astype(np.float32)
+          for n in range(len(dims))]
+    Qd = [None if q is None else torch.from_numpy(q).cuda() for q in qs]
+    G = host(R().rhosvd_core(dev(x), dims, Qd))
+    mats = [None if q is None else q.astype(np.float64).T for q in qs]
+    want = T.multi_ttm(x32, mats)
+    bound = T.multi_ttm(np.abs(x32), [None if m is None else np.abs(m) for m in mats])
+    assert G.shape == want.shape
+    assert_close_abs(G, want, bound)
+
+
+# ------------------------------------------------------------------ a3: orthonormalisation
+
+def _orth_checks(Y, Q, fb_expected=None, fb=None):
+    q = host(Q)
+    assert M.orthonormality(q) <= 1e-5
+    resid = Y - q @ (q.T @ Y)
+    assert np.linalg.norm(resid) <= 1e-5 * np.linalg.norm(Y)
+    if fb_expected is not None:
+        assert fb == fb_expected
+
+
+@pytest.mark.parametrize("m,K", [(1000, 37), (512, 42), (262144, 42), (300, 128), (65, 64)])
+def test_orth_well_conditioned(m, K):
+    y = np.random.default_rng(m + K).standard_normal((m, K)).astype(np.float32)
+    Q, fb = R().rhosvd_orth(torch.from_numpy(y).cuda(), report_fallback=True)
+    _orth_checks(y.astype(np.float64), Q, False, fb)
+    # same subspace as the oracle's Householder QR
+    assert M.max_principal_sine(host(Q), A.orth(y.astype(np.float64))) <= 1e-5
+
+
+def test_orth_ill_conditioned_cond_1e5():
+    rng = np.random.default_rng(5)
+    u, _ = np.linalg.qr(rng.standard_normal((4000, 40)))
+    v, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    y = ((u * np.logspace(0, -5, 40)) @ v.T).astype(np.float32)
+    Q, fb = R().rhosvd_orth(torch.from_numpy(y).cuda(), report_fallback=True)
+    _orth_checks(y.astype(np.float64), Q)
+    assert fb is False
+
+
+@pytest.mark.parametrize("m,K,rank", [(300, 20, 5), (20000, 24, 10)])
+def test_orth_rank_deficient_uses_householder(m, K, rank):
+    rng = np.random.default_rng(6)
+    y = (rng.standard_normal((m, rank)) @ rng.standard_normal((rank, K))).astype(np.float32)
+    Q, fb = R().rhosvd_orth(torch.from_numpy(y).cuda(), report_fallback=True)
+    _orth_checks(y.astype(np.float64), Q, True, fb)
+    # the oracle's basis of range(Y) is contained in the GPU basis
+    qo = A.orth(y.astype(np.float64))[:, :rank]
+    qg = host(Q)
+    assert np.linalg.norm(qo - qg @ (qg.T @ qo)) <= 1e-4
+
+
+# ------------------------------------------------------------------ a4: power iteration
+
+def test_power_step_parity():
+    dims = (60, 50, 40)
+    x = lowrank_tensor(dims, (8, 8, 8), 8, noise=0.05)
+    x32 = f32(x)
+    for n in range(3):
+        a = T.unfold(x32, n)
+        q = A.orth(np.random.default_rng(9 + n).standard_normal((dims[n], 12)))
+        Y = host(R().rhosvd_power(dev(x), dims, n, torch.from_numpy(q.astype(np.float32)).cuda()))
+        want = a @ A.orth(a.T @ q.astype(np.float32).astype(np.float64))
+        # Z is unique up to a K x K rotation, so compare ranges and singular values
+        assert M.max_principal_sine(Y, want) <= 1e-4
+        np.testing.assert_allclose(np.linalg.svd(Y, compute_uv=False), np.linalg.svd(want, compute_uv=False),
+                                   rtol=1e-4)
+
+
+# ------------------------------------------------------------------ decompositions
+
+def _compare(x32, g_gpu, u_gpu, g_or, u_or, sine_tol=1e-4, e_tol=1e-5):
+    e_gpu = M.rel_error(x32, g_gpu, u_gpu)
+    e_or = M.rel_error(x32, g_or, u_or)
+    sines = [M.max_principal_sine(a, b) for a, b in zip(u_gpu, u_or)]
+    orth = [M.orthonormality(u) for u in u_gpu]
+    assert max(sines) <= sine_tol, sines
+    assert abs(e_gpu - e_or) <= e_tol, (e_gpu, e_or)
+    assert max(orth) <= 1e-5, orth
+    return e_gpu, e_or, max(sines)
+
+
+def _run(x, dims, ranks, algo, p, q, Omega=None, Omega_tilde=None, K=None, S=None, seed=0):
+    om = None if Omega is None else [dev_mat(o) for o in Omega]
+    ot = None if Omega_tilde is None else [dev_mat(o) for o in Omega_tilde]
+    G, U = R().rhosvd_decompose(dev(x), dims, ranks, algo=algo, p=p, q=q, seed=seed, Omega=om,
+                                Omega_tilde=ot, K=K, S=S)
+    return host(G), [host(u) for u in U]
+
+
+DEC_CASES = [((40, 50, 60), (5, 6, 7)), ((12, 13, 14, 15), (3, 3, 4, 4)), ((130, 70, 33), (20, 9, 4)),
+             ((7, 90, 65), (7, 10, 3))]
+
+
+@pytest.mark.parametrize("dims,ranks", DEC_CASES)
+@pytest.mark.parametrize("algo,q", [("rhosvd", 0), ("rhosvd", 1), ("rsthosvd", 1), ("rsthosvd", 2)])
+def test_decompose_parity_explicit_omega(dims, ranks, algo, q):
+    p = 5
+    x = lowrank_tensor(dims, ranks, 11, noise=1e-3)
+    x32 = f32(x)
+    shapes = A.omega_shapes(algo, dims, ranks, p)
+    om = [gaussian_matrix(200 + n, r, c) for n, (r, c) in enumerate(shapes)]
+    g, u = _run(x, dims, ranks, algo, p, q, Omega=om)
+    g_or, u_or = getattr(A, algo)(x32, ranks, q, [o.astype(np.float64) for o in om])
+    _compare(x32, g, u, g_or, u_or)
+
+
+@pytest.mark.parametrize("dims,ranks", DEC_CASES[:3])
+def test_rpet_parity_explicit_omega(dims, ranks):
+    x = lowrank_tensor(dims, ranks, 12, noise=1e-3)
+    x32 = f32(x)
+    K = tuple(min(r + 4, d) for r, d in zip(ranks, dims))
+    S = tuple(2 * k + 1 for k in K)
+    fs, ts = A.omega_shapes("rpet", dims, ranks, 0, K=K, S=S)
+    om = [gaussian_matrix(300 + n, r, c) for n, (r, c) in enumerate(fs)]
+    ot = [gaussian_matrix(400 + n, r, c) for n, (r, c) in enumerate(ts)]
+    g, u = _run(x, dims, ranks, "rpet", 0, 0, Omega=om, Omega_tilde=ot, K=K, S=S)
+    g_or, u_or, _ = A.rpet(x32, ranks, [o.astype(np.float64) for o in om], [o.astype(np.float64) for o in ot])
+    _compare(x32, g, u, g_or, u_or)
+
+
+def _oracle_seeded(algo, x32, dims, ranks, p, q, seed, K=None, S=None):
+    """The oracle on test matrices from its own Philox implementation (the GPU draws its own)."""
+    if algo == "rpet":
+        fs, ts = A.omega_shapes("rpet", dims, ranks, p, K=K, S=S)
+        N = len(dims)
+        om = [philox.omega(seed, n, r, c).astype(np.float64) for n, (r, c) in enumerate(fs)]
+        ot = [philox.omega(seed, N + n, r, c).astype(np.float64) for n, (r, c) in enumerate(ts)]
+        g, u, _ = A.rpet(x32, ranks, om, ot)
+        return g, u
+    shapes = A.omega_shapes(algo, dims, ranks, p)
+    om = [philox.omega(seed, n, r, c).astype(np.float64) for n, (r, c) in enumerate(shapes)]
+    return getattr(A, algo)(x32, ranks, q, om)
+
+
+@pytest.mark.parametrize("algo", ["rhosvd", "rsthosvd", "rpet"])
+def test_decompose_seeded_vs_oracle_generator(algo):
+    dims, ranks = (48, 52, 44), (6, 5, 7)
+    x = lowrank_tensor(dims, ranks, 13, noise=1e-3)
+    x32 = f32(x)
+    K = (10, 9, 11) if algo == "rpet" else None
+    S = (21, 19, 23) if algo == "rpet" else None
+    g, u = _run(x, dims, ranks, algo, 4, 1, K=K, S=S, seed=2024)
+    g_or, u_or = _oracle_seeded(algo, x32, dims, ranks, 4, 1, 2024, K=K, S=S)
+    _compare(x32, g, u, g_or, u_or)
+
+
+def test_rank_equal_to_mode_size_skips_mode():
+    dims, ranks = (6, 40, 50), (6, 5, 4)
+    x = lowrank_tensor(dims, (6, 5, 4), 14, noise=1e-3)
+    x32 = f32(x)
+    for algo in ("rhosvd", "rsthosvd"):
+        g, u = _run(x, dims, ranks, algo, 3, 1, seed=5)
+        np.testing.assert_array_equal(u[0], np.eye(6))
+        g_or, u_or = _oracle_seeded(algo, x32, dims, ranks, 3, 1, 5)
+        _compare(x32, g, u, g_or, u_or)
+
+
+def test_noise_free_low_rank_recovery():
+    """Noise-free exact multilinear rank: the FP32 path recovers X to FP32 accuracy."""
+    dims, ranks = (60, 70, 80), (5, 6, 7)
+    x = lowrank_tensor(dims, ranks, 15, noise=0.0, factors="gaussian")
+    x32 = f32(x)
+    for algo in ("rhosvd", "rsthosvd", "rpet"):
+        K = tuple(r + 3 for r in ranks) if algo == "rpet" else None
+        S = tuple(2 * k + 1 for k in K) if algo == "rpet" else None
+        g, u = _run(x, dims, ranks, algo, 3, 1, K=K, S=S, seed=6)
+        g_or, u_or = _oracle_seeded(algo, x32, dims, ranks, 3, 1, 6, K=K, S=S)
+        e_or = M.rel_error(x32, g_or, u_or)
+        # rounding X to FP32 adds relative noise <= 2^-24 per entry, which bounds the best
+        # approximation error; the oracle stays within the sqrt(N) quasi-optimality factor
+        assert e_or <= 3 ** 0.5 * 2.0 ** -24
+        assert M.rel_error(x32, g, u) - e_or <= 1e-5  # the FP32 path, within the stated tolerance
+        assert max(M.orthonormality(v) for v in u) <= 1e-5
+        assert max(M.max_principal_sine(a, b) for a, b in zip(u, u_or)) <= 1e-4
+
+
+def test_nonfinite_input_is_reported():
+    dims, ranks = (30, 31, 32), (4, 4, 4)
+    x = lowrank_tensor(dims, ranks, 16, noise=1e-3)
+    x[3, 4, 5] = np.nan
+    rh = R()
+    with pytest.raises(rh.RhosvdError) as ei:
+        rh.rhosvd_decompose(dev(x), dims, ranks, algo="rsthosvd", p=4, q=1)
+    assert ei.value.code == 4   # RHOSVD_ENONFINITE
+
+
+def test_bitwise_deterministic():
+    dims, ranks = (64, 64, 64), (8, 8, 8)
+    x = lowrank_tensor(dims, ranks, 17, noise=1e-3)
+    X = dev(x)
+    outs = []
+    for _ in range(2):
+        G, U = R().rhosvd_decompose(X, dims, ranks, algo="rsthosvd", p=6, q=1, seed=3)
+        outs.append((host(G), [host(u) for u in U]))
+    np.testing.assert_array_equal(outs[0][0], outs[1][0])
+    for a, b in zip(outs[0][1], outs[1][1]):
+        np.testing.assert_array_equal(a, b)
+
+
+def test_device_status_cleared_between_calls():
+    rh = R()
+    dims, ranks = (20, 21, 22), (3, 3, 3)
+    bad = lowrank_tensor(dims, ranks, 18, noise=1e-3)
+    bad[0, 0, 0] = np.inf
+    ws = rh.Workspace(rh.rhosvd_workspace_size(dims, ranks, "rsthosvd", 3, 1))
+    rh.rhosvd_decompose(dev(bad), dims, ranks, algo="rsthosvd", p=3, q=1, ws=ws, check=False)
+    assert rh.rhosvd_device_status(ws)[0] == 4
+    good = lowrank_tensor(dims, ranks, 18, noise=1e-3)
+    rh.rhosvd_decompose(dev(good), dims, ranks, algo="rsthosvd", p=3, q=1, ws=ws, check=False)
+    assert rh.rhosvd_device_status(ws)[0] == 0
+
+
+# ------------------------------------------------------------------ full-size workloads
+
+@pytest.mark.parametrize("name", ["lowrank100_rhosvd", "decay512_rsthosvd", "lowrank128x4_rpet"])
+def test_workload_full_size_parity(name):
+    """The benchmark configurations at full size, seed-drawn test matrices on both sides."""
+    w = WORKLOADS[name]
+    x = w.tensor()
+    x32 = f32(x)
+    g, u = _run(x, w.dims, w.ranks, w.algo, w.p, w.q, K=w.K, S=w.S, seed=w.omega_seed)
+    del x
+    g_or, u_or = _oracle_seeded(w.algo, x32, w.dims, w.ranks, w.p, w.q, w.omega_seed, K=w.K, S=w.S)
+    e_gpu, e_or, s = _compare(x32, g, u, g_or, u_or)
+    print(f"{name}: E_gpu={e_gpu:.6e} E_oracle={e_or:.6e} max_sine={s:.2e}")
