@@ -126,6 +126,26 @@ rhosvd_status rhosvd_sketch(const float* X, const rhosvd_shape* shape, int32_t m
                             uint64_t seed, const float* Omega, float* Y,
                             void* ws, size_t ws_bytes, void* stream);
 
+/* Mode-n sketch without a workspace (the paper has no counterpart; this is a
+ * deployment variant of rhosvd_sketch).  For callers that cannot allocate
+ * device memory where they need the sketch -- code inside another framework's
+ * memory pool, plug-ins handed only their input and output buffers, loops
+ * where a cudaMalloc and its implicit synchronisation are not allowed.
+ * Computes Y = X_(n) Omega exactly like rhosvd_sketch with an explicit Omega
+ * (J_n x K, ld J_n; must not be NULL -- there is nowhere to draw it) and Y
+ * (I_mode x K, ld I_mode).  The split-K partial sums live in a fixed 4 MiB
+ * device array (2^20 floats) that every GPU which loads the library holds
+ * until the process exits; the call allocates nothing.  Requests with
+ * I_mode * K > 2^20 return RHOSVD_EINVAL before anything is enqueued.
+ * The first call on a device looks up that array's device address (a
+ * cudaGetSymbolAddress on the current device), so make the first call on each
+ * device before any stream capture.  All calls on a device share the one
+ * array and each call overwrites it: calls whose work may overlap on the GPU
+ * (different streams, no ordering between them) race and give wrong results;
+ * order them on one stream or with events. */
+rhosvd_status rhosvd_sketch_noalloc(const float* X, const rhosvd_shape* shape, int32_t mode, int32_t K,
+                                    const float* Omega, float* Y, void* stream);
+
 /* Every sketch R-PET needs (Alg. 9 lines 1 and 3): Y[n] = X_(n) Omega_n
  * (I_n x K[n], ld = I_n) for all n, and, if H is not NULL, the core sketch
  * H = X x_1 Omega~_1 ... x_N Omega~_N (S[0] x ... x S[N-1], column-major) with

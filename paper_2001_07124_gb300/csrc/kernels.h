@@ -46,6 +46,10 @@ size_t sketch_partial_floats(const SketchPlan& pl, int64_t I, int K);
 // Y = X_(n) W in FP32 (partials in ws_part, deterministic fixed-order reduction).
 cudaError_t launch_sketch(const View& x, const WView& w, int K, float* Y, int64_t ldy,
                           float* ws_part, cudaStream_t st);
+// Same computation with the contraction split into at most max_splits parts, so
+// that the partial sums fit a caller-provided scratch of max_splits * I * K floats.
+cudaError_t launch_sketch_capped(const View& x, const WView& w, int K, float* Y, int64_t ldy,
+                                 float* part, int max_splits, cudaStream_t st);
 // G = X_(n) W accumulated in double-float, reduced in FP64 to Gd (K x I... as I x K, ld = I).
 cudaError_t launch_sketch_df(const View& x, const WView& w, int K, double* Gd, int64_t ldg,
                              double* ws_part, cudaStream_t st);

@@ -295,6 +295,24 @@ cudaError_t launch_sketch(const View& x, const WView& w, int K, float* Y, int64_
   return cudaGetLastError();
 }
 
+cudaError_t launch_sketch_capped(const View& x, const WView& w, int K, float* Y, int64_t ldy, float* part,
+                                 int max_splits, cudaStream_t st) {
+  const int64_t J = x.L * x.Rt;
+  SketchPlan pl = plan_sketch(x.I, K, J);
+  if (pl.splits > max_splits) {
+    // widen the per-CTA contraction chunk until the partial sums fit
+    int64_t chunk = (J + max_splits - 1) / max_splits;
+    pl.jchunk = ((chunk + SK_BJ - 1) / SK_BJ) * SK_BJ;
+    pl.splits = (int)std::max<int64_t>(1, (J + pl.jchunk - 1) / pl.jchunk);
+  }
+  dim3 grid(pl.tiles_i, pl.tiles_k, pl.splits);
+  sketch_partial_kernel<false, float><<<grid, SK_THREADS, 0, st>>>(x, w, K, pl.jchunk, part);
+  const int64_t n = x.I * K;
+  reduce_partials_kernel<float, float><<<(unsigned)((n + 31) / 32), 32 * RD_ROWS, 0, st>>>(
+      part, pl.splits, x.I, K, Y, ldy);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sketch_df(const View& x, const WView& w, int K, double* Gd, int64_t ldg,
                              double* ws_part, cudaStream_t st) {
   const int64_t J = x.L * x.Rt;

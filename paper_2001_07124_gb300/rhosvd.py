@@ -77,6 +77,7 @@ def lib() -> ctypes.CDLL:
                               ctypes.c_int64, _P]),
         "rhosvd_sketch": (st, [_P, ctypes.POINTER(Shape), ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P,
                                _P, _P, ctypes.c_size_t, _P]),
+        "rhosvd_sketch_noalloc": (st, [_P, ctypes.POINTER(Shape), ctypes.c_int32, ctypes.c_int32, _P, _P, _P]),
         "rhosvd_sketch_all": (st, [_P, ctypes.POINTER(Shape), _I32P, _I32P, ctypes.c_uint64, _PP, _PP, _PP,
                                    _P, _P, ctypes.c_size_t, _P]),
         "rhosvd_power": (st, [_P, ctypes.POINTER(Shape), ctypes.c_int32, ctypes.c_int32, _P, _P,
@@ -259,6 +260,19 @@ def rhosvd_sketch(X, dims, mode: int, K: int, seed: int = 0, Omega=None, Y=None,
     om = None if Omega is None else _dptr(Omega)
     _check(lib().rhosvd_sketch(_dptr(X), ctypes.byref(make_shape(dims)), int(mode), int(K), int(seed), om,
                                _dptr(Y), ws.ptr, ws.nbytes, _stream(stream)), "rhosvd_sketch")
+    return matrix(Y, I, K)
+
+
+def rhosvd_sketch_noalloc(X, dims, mode: int, K: int, Omega, Y=None, stream=None):
+    """Y = X_(mode) Omega without a workspace, for callers that cannot allocate
+    device memory at the call site (the partial sums live in a fixed 4 MiB
+    device array owned by the library; Y may be passed in preallocated).
+    Calls that overlap on the GPU share that array and race; order them."""
+    X = colmajor(X, dims)
+    I = int(dims[mode])
+    Y = empty_colmajor((I, K)) if Y is None else Y
+    _check(lib().rhosvd_sketch_noalloc(_dptr(X), ctypes.byref(make_shape(dims)), int(mode), int(K), _dptr(Omega),
+                                       _dptr(Y), _stream(stream)), "rhosvd_sketch_noalloc")
     return matrix(Y, I, K)
 
 
