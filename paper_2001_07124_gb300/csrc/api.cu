@@ -98,9 +98,13 @@ void op_gram_df(Ctx& c, const View& x, const WView& w, int K, double* Gd) {
   if (!c.dry) c.check(launch_sketch_df(x, w, K, Gd, x.I, part, c.s));
 }
 
-void op_gram_matrix(Ctx& c, const float* A, int64_t m, int K, int64_t ld, double* Gd) {
-  WView w{A, 0, ld};
-  op_gram_df(c, matrix_view(A, m, K, ld), w, K, Gd);
+// Gd (K x K, FP64) = A^T A for a tall matrix; exact = FP64-accurate products
+void op_gram_matrix(Ctx& c, const float* A, int64_t m, int K, int64_t ld, double* Gd, bool exact = true) {
+  Scope sc(c);
+  GramPlan pl = plan_gram(m, K);
+  double* part = c.take<double>((size_t)pl.ctas * K * K);
+  c.launches += 2;
+  if (!c.dry) c.check(launch_gram(A, m, K, ld, Gd, part, exact, c.s));
 }
 
 void op_ttm(Ctx& c, const View& x, const float* M, int64_t m_i, int64_t m_k, int K, const OView& out,
@@ -113,14 +117,12 @@ void op_ttm(Ctx& c, const View& x, const float* M, int64_t m_i, int64_t m_k, int
 void op_orth(Ctx& c, float* Y, int64_t m, int K, int64_t ld) {
   Scope sc(c);
   double* G = c.take<double>((size_t)K * K);
-  float* Rinv = c.take<float>((size_t)K * K);
-  const View yv = matrix_view(Y, m, K, ld);
-  const OView yo{Y, ld, 0};
+  float* L = c.take<float>((size_t)K * K);
   for (int pass = 0; pass < 2; ++pass) {
-    op_gram_matrix(c, Y, m, K, ld, G);
-    c.launches += 1;
-    if (!c.dry) c.check(launch_chol_inv(G, K, Rinv, pass, 0, c.st, c.s));
-    op_ttm(c, yv, Rinv, 1, K, K, yo, c.st);
+    op_gram_matrix(c, Y, m, K, ld, G, pass == 0);
+    c.launches += 2;
+    if (!c.dry) c.check(launch_chol(G, K, L, pass, 0, c.st, c.s));
+    if (!c.dry) c.check(launch_trsm_rows(Y, m, K, ld, L, 0, c.st, c.s));
   }
   c.launches += 1;
   if (!c.dry) c.check(launch_householder(Y, m, K, ld, c.st, false, c.s));
@@ -425,7 +427,7 @@ void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const
   }
   float* Cb[2] = {c.take<float>(max_c), c.take<float>(max_c)};
   double* Gd = c.take<double>(max_kk);
-  float* Rinv = c.take<float>(max_kk);
+  float* Lf = c.take<float>(max_kk);
 
   // lines 1-2: factor sketches and their orthonormal bases
   for (int n = 0; n < N; ++n) {
@@ -464,15 +466,9 @@ void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const
       op_ttm(c, qv, om, S, 1, S, OView{A, 1, S});
     }
     op_gram_matrix(c, A, S, K, S, Gd);
-    c.launches += 1;
-    if (!c.dry) c.check(launch_chol_inv(Gd, K, Rinv, 0, RHOSVD_EBREAKDOWN, c.st, c.s));
-    op_ttm(c, matrix_view(A, S, K, S), Rinv, 1, K, K, OView{A, S, 0});     // A R^-1, in place
-    {
-      Scope sc(c);
-      float* T1 = c.take<float>((size_t)S * K);
-      if (!c.dry) c.check(cudaMemcpyAsync(T1, A, sizeof(float) * S * K, cudaMemcpyDeviceToDevice, c.s));
-      op_ttm(c, matrix_view(T1, S, K, S), Rinv, K, 1, K, OView{A, S, 0}); // (A R^-1) R^-T
-    }
+    c.launches += 2;
+    if (!c.dry) c.check(launch_chol(Gd, K, Lf, 0, RHOSVD_EBREAKDOWN, c.st, c.s));
+    if (!c.dry) c.check(launch_trsm_rows(A, S, K, S, Lf, 1, c.st, c.s));   // A (A^T A)^-1, in place
     float* dst = Cb[ping];
     ttm_mode(c, cur, t, n, A, 1, S, K, dst);   // M(s, k) = P^T(s, k)
     t.d[n] = K;

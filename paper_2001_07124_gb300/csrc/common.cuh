@@ -18,7 +18,8 @@ struct DevStatus {
   int32_t orth_fail;      // set by a Cholesky pass that broke down, cleared per orth call
   int32_t fallbacks;      // number of Householder fallbacks that ran
   int32_t fallback_rows;  // rows m of the last matrix that needed the fallback
-  int32_t pad[59];
+  int32_t eig_sweeps;     // largest number of Jacobi sweeps a truncation needed
+  int32_t pad[58];
 };
 static_assert(sizeof(DevStatus) == 256, "status block is 256 bytes");
 
@@ -61,6 +62,18 @@ __device__ __forceinline__ void df64_fma(df64& acc, float a, float b) {
 }
 
 __device__ __forceinline__ double df64_to_double(df64 v) { return (double)v.hi + (double)v.lo; }
+
+// 1/sqrt(d) in FP64: the FP32 hardware estimate refined by two Newton steps
+// y <- y (3 - d y^2) / 2 (each step doubles the correct bits: ~2^-22 -> 2^-44
+// -> full precision).  Callers pass pivots of Gram matrices scaled to max
+// diagonal 1, well inside the FP32 exponent range.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  double y = (double)rsqrtf((float)d);
+  y = y * (1.5 - 0.5 * d * y * y);
+  y = y * (1.5 - 0.5 * d * y * y);
+  return y;
+}
+__device__ __forceinline__ float rsqrt_newton(float d) { return rsqrtf(d); }
 
 // ---------------------------------------------------------------- warp helpers
 __device__ __forceinline__ float warp_sum(float v) {

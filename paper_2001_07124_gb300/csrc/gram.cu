@@ -1,0 +1,125 @@
+// Gram matrix G = A^T A of a tall column-major matrix A (m x K, leading
+// dimension ld), reduced to FP64: the "small Gram" of CholeskyQR2 (Alg. 1
+// step 3) and of the truncation step (B B^T, Alg. 1 step 5).
+//
+// Only the upper triangle a <= b is accumulated (K(K+1)/2 pairs per row); each
+// CTA owns a contiguous block of rows, stages 64-row tiles in shared memory and
+// writes its partial K x K Gram (both triangles) in FP64; partials are summed in
+// a fixed order (reduce_d_kernel), so results are bitwise reproducible.
+//
+// Two accumulation modes:
+//  * EXACT: every product a*b is split exactly by an FMA (TwoProd) and added
+//    with TwoSum into a double-float accumulator (Ogita, Rump, Oishi 2005,
+//    "Accurate sum and dot product"), so the Gram is FP64-accurate even when
+//    cond(A) is ~1e6 (first CholeskyQR pass).
+//  * CHUNKED: products are summed in FP32 over one 64-row tile and the tile sums
+//    are added in FP64; enough when A is close to orthonormal (second pass).
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace rhosvd {
+namespace {
+
+constexpr int GR_THREADS = 256;
+constexpr int GR_TILE = 64;                      // rows per shared-memory tile
+constexpr int GR_TARGET_CTAS = 296;              // 2 per SM on 148-152 SMs
+
+template <bool EXACT, int PT>                    // PT = max pairs per thread
+__global__ void __launch_bounds__(GR_THREADS)
+gram_kernel(const float* __restrict__ A, int64_t m, int K, int64_t ld, int64_t rows_per_cta,
+            double* __restrict__ part) {
+  extern __shared__ float tile[];                // [K][GR_TILE + 1]
+  const int tid = threadIdx.x;
+  const int P = K * (K + 1) / 2;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r1 = min(m, r0 + rows_per_cta);
+  constexpr int LD = GR_TILE + 1;
+
+  int pab[PT];                                    // a | b << 16
+  double dacc[PT];
+  df64 xacc[PT];
+#pragma unroll
+  for (int t = 0; t < PT; ++t) {
+    const int p = tid + t * GR_THREADS;
+    int b = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+    while (b > 0 && b * (b + 1) / 2 > p) --b;
+    while ((b + 1) * (b + 2) / 2 <= p) ++b;
+    pab[t] = (p < P) ? ((p - b * (b + 1) / 2) | (b << 16)) : 0;
+    dacc[t] = 0.0;
+    xacc[t] = df64{0.f, 0.f};
+  }
+  for (int64_t rt = r0; rt < r1; rt += GR_TILE) {
+    const int nrow = (r1 - rt < GR_TILE) ? (int)(r1 - rt) : GR_TILE;
+    __syncthreads();
+    for (int e = tid; e < K * GR_TILE; e += GR_THREADS) {
+      const int c = e / GR_TILE, r = e % GR_TILE;
+      tile[c * LD + r] = (r < nrow) ? __ldg(A + (rt + r) + (int64_t)c * ld) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int t = 0; t < PT; ++t) {
+      if (tid + t * GR_THREADS >= P) break;
+      const float* ca = tile + (pab[t] & 0xffff) * LD;
+      const float* cb = tile + (pab[t] >> 16) * LD;
+      if (EXACT) {
+        df64 acc = xacc[t];
+#pragma unroll 8
+        for (int r = 0; r < GR_TILE; ++r) df64_fma(acc, ca[r], cb[r]);
+        xacc[t] = acc;
+      } else {
+        float s = 0.f;
+#pragma unroll 8
+        for (int r = 0; r < GR_TILE; ++r) s = fmaf(ca[r], cb[r], s);
+        dacc[t] += (double)s;
+      }
+    }
+  }
+  double* dst = part + (int64_t)blockIdx.x * K * K;
+#pragma unroll
+  for (int t = 0; t < PT; ++t) {
+    if (tid + t * GR_THREADS >= P) break;
+    const double v = EXACT ? df64_to_double(xacc[t]) : dacc[t];
+    const int a = pab[t] & 0xffff, b = pab[t] >> 16;
+    dst[a + b * K] = v;
+    dst[b + a * K] = v;
+  }
+}
+
+template <bool EXACT>
+cudaError_t launch_gram_t(const float* A, int64_t m, int K, int64_t ld, double* G, double* part, int ctas,
+                          int64_t rows, cudaStream_t st) {
+  const int P = K * (K + 1) / 2;
+  const int pt = (P + GR_THREADS - 1) / GR_THREADS;
+  const size_t smem = (size_t)K * (GR_TILE + 1) * sizeof(float);
+  if (pt <= 4) gram_kernel<EXACT, 4><<<ctas, GR_THREADS, smem, st>>>(A, m, K, ld, rows, part);
+  else if (pt <= 8) gram_kernel<EXACT, 8><<<ctas, GR_THREADS, smem, st>>>(A, m, K, ld, rows, part);
+  else if (pt <= 16) gram_kernel<EXACT, 16><<<ctas, GR_THREADS, smem, st>>>(A, m, K, ld, rows, part);
+  else gram_kernel<EXACT, 33><<<ctas, GR_THREADS, smem, st>>>(A, m, K, ld, rows, part);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_reduce_d(part, ctas, (int64_t)K * K, G, st);
+}
+
+}  // namespace
+
+GramPlan plan_gram(int64_t m, int K) {
+  GramPlan pl;
+  // enough rows per CTA that the pair bookkeeping amortises, at most ~2 CTAs per SM
+  int64_t rows = (m + GR_TARGET_CTAS - 1) / GR_TARGET_CTAS;
+  rows = std::max<int64_t>(GR_TILE, ((rows + GR_TILE - 1) / GR_TILE) * GR_TILE);
+  pl.rows_per_cta = rows;
+  pl.ctas = (int)std::max<int64_t>(1, (m + rows - 1) / rows);
+  (void)K;
+  return pl;
+}
+
+cudaError_t launch_gram(const float* A, int64_t m, int K, int64_t ld, double* G, double* part, bool exact,
+                        cudaStream_t st) {
+  GramPlan pl = plan_gram(m, K);
+  return exact ? launch_gram_t<true>(A, m, K, ld, G, part, pl.ctas, pl.rows_per_cta, st)
+               : launch_gram_t<false>(A, m, K, ld, G, part, pl.ctas, pl.rows_per_cta, st);
+}
+
+}  // namespace rhosvd

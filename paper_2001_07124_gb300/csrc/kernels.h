@@ -59,17 +59,34 @@ cudaError_t launch_sketch_df(const View& x, const WView& w, int K, double* Gd, i
 cudaError_t launch_ttm(const View& x, const float* Mp, int64_t m_i, int64_t m_k, int K,
                        const OView& out, const DevStatus* skip_if_orth_fail, cudaStream_t st);
 
+// ---- gram.cu
+// G (K x K, FP64) = A^T A for A m x K (ld).  exact: double-float products
+// (FP64-accurate for ill-conditioned A); otherwise FP32 within 64-row tiles and
+// FP64 across them (for nearly orthonormal A).  part: ctas * K * K doubles.
+struct GramPlan {
+  int ctas;
+  int64_t rows_per_cta;
+};
+GramPlan plan_gram(int64_t m, int K);
+cudaError_t launch_gram(const float* A, int64_t m, int K, int64_t ld, double* G, double* part, bool exact,
+                        cudaStream_t st);
+
 // ---- omega.cu
 cudaError_t launch_omega(uint64_t seed, uint32_t stream_id, int64_t rows, int cols, float* out,
                          int64_t ld, cudaStream_t st);
 
 // ---- orth.cu
-// Cholesky of the K x K FP64 Gram G (ld K) into Rinv = R^{-1} (upper, FP32,
-// K x K column-major) with R^T R = G.  pass 0 writes orth_fail; pass 1 runs
-// only if orth_fail is clear.  Breakdown sets orth_fail and, if fail_code is
-// non-zero, records fail_code as the device error.
-cudaError_t launch_chol_inv(const double* G, int K, float* Rinv, int pass, int fail_code, DevStatus* st,
-                            cudaStream_t stream);
+// Cholesky factor L (K x K, FP32, column-major lower, zero above) of the FP64
+// Gram G = L L^T.  pass 0 writes orth_fail; pass 1 runs only if orth_fail is
+// clear.  Breakdown sets orth_fail and, if fail_code is non-zero, records
+// fail_code as the device error.
+cudaError_t launch_chol(const double* G, int K, float* L, int pass, int fail_code, DevStatus* st,
+                        cudaStream_t stream);
+// Row-parallel triangular solves with L: mode 0 replaces every row y^T of Y
+// (m x K, ld) by y^T L^-T (= Y R^-1 with R = L^T); mode 1 by y^T (L L^T)^-1.
+// Skipped when skip is non-NULL and orth_fail is set.
+cudaError_t launch_trsm_rows(float* Y, int64_t m, int K, int64_t ld, const float* L, int mode,
+                             const DevStatus* skip, cudaStream_t stream);
 // Householder QR of A (m x K, ld) into its Q factor, in place; runs only when
 // orth_fail is set (or always if force).
 cudaError_t launch_householder(float* A, int64_t m, int K, int64_t ld, DevStatus* st, bool force,

@@ -3,8 +3,9 @@
 //
 // CholeskyQR2 (Fukaya, Nakatsukasa, Yanagisawa, Yamamoto 2014; Yamamoto et al.
 // 2015): G = Y^T Y, R = chol(G), Q1 = Y R^-1, repeated once on Q1.  The Gram is
-// accumulated in double-float (FP64-accurate, see sketch.cu) and the Cholesky
-// and triangular inverse run in FP64 on one CTA; the apply is the TTM kernel.
+// accumulated in double-float (FP64-accurate, see gram.cu); the first pass's
+// Cholesky runs in FP64 on one CTA, the second pass's in FP32 when its Gram is
+// close to I; Y R^-1 is applied by row-parallel forward substitution.
 // The first pass only rejects pivots that are numerically non-positive
 // (<= K * 1e-15 * max diag): for larger condition numbers Q1 = Y R^-1 is still
 // formed and the second pass judges it; a second-pass pivot below 1e-4 * max
@@ -24,56 +25,107 @@ namespace {
 
 constexpr int CH_THREADS = 256;
 
-__global__ void __launch_bounds__(CH_THREADS)
-chol_inv_kernel(const double* __restrict__ G, int K, float* __restrict__ Rinv, int pass, int fail_code,
-                DevStatus* st) {
-  if (pass == 1 && st->orth_fail) return;
-  extern __shared__ double A[];          // K x K, A[i + j*K]
-  double* diag = A + (size_t)K * K;      // K entries: diagonal of L^-1
-  __shared__ int fail;
-  __shared__ int nonfinite;
-  __shared__ double maxdiag;
-  const int tid = threadIdx.x;
+// Right-looking Cholesky G/g = L' L'^T of the Gram scaled by g = max diag, on a
+// 16 x 16 thread grid: step j writes column j of L' = A(:,j)/sqrt(d) to Lout
+// and updates the trailing lower triangle with the unscaled column,
+// A(i,k) -= A(i,j) A(k,j) / d.  The GPU's FP64 pipe is narrow, so the per-step
+// scalar 1/sqrt(d) is computed once, by the thread that finalises the next
+// pivot (it updates A(j+1,j+1) last in step j), and broadcast through shared
+// memory; each step needs one barrier.  Lout receives L = sqrt(g) L'
+// (K x K column-major, zero above the diagonal).  Returns false (uniformly)
+// when a scaled pivot is at or below tol.
+template <typename T>
+__device__ bool chol_body(const double* __restrict__ G, int K, float* __restrict__ Lout, T* A, double g,
+                          double tol) {
+  __shared__ T rs_s[RHOSVD_MAX_K];
+  __shared__ int bad;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const T ginv = (T)(1.0 / g);
+  for (int c = ty; c < K; c += 16)
+    for (int r = tx; r < K; r += 16) A[r + c * K] = (r >= c) ? (T)G[r + c * K] * ginv : (T)0;
+  __syncthreads();
   if (tid == 0) {
-    fail = 0;
-    nonfinite = 0;
-    maxdiag = 0.0;
+    const T d0 = A[0];
+    bad = !(d0 > (T)tol);
+    rs_s[0] = bad ? (T)0 : rsqrt_newton(d0);
   }
   __syncthreads();
+  const float sg = (float)sqrt(g);
+  for (int j = 0; j < K; ++j) {
+    if (bad) return false;                  // uniform: set before the last barrier
+    const T rs = rs_s[j];
+    const T r2 = rs * rs;
+    for (int i = j + tid; i < K; i += CH_THREADS) Lout[i + j * K] = (float)(A[i + j * K] * rs) * sg;
+    for (int i = j + 1 + ty; i < K; i += 16) {
+      const T aij = A[i + j * K] * r2;
+      for (int k = j + 1 + tx; k <= i; k += 16) A[i + k * K] -= aij * A[k + j * K];
+    }
+    if (tid == 0 && j + 1 < K) {            // thread (0,0) owns A(j+1, j+1)
+      const T dn = A[(j + 1) + (j + 1) * K];
+      if (!(dn > (T)tol)) bad = 1;
+      else rs_s[j + 1] = rsqrt_newton(dn);
+    }
+    __syncthreads();
+  }
+  for (int c = ty; c < K; c += 16)
+    for (int r = tx; r < c; r += 16) Lout[r + c * K] = 0.f;
+  return true;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Cholesky factor L (G = L L^T) of one CholeskyQR pass.  The first pass's Gram
+// can have condition ~1e12 and is factored in FP64; the second pass's in FP32
+// when every off-diagonal cosine G_ij / sqrt(G_ii G_jj) is at most 1e-2 (then
+// cond(G) < 1.5 and FP32 adds O(K u) to the orthogonality of Q2), in FP64
+// otherwise.  Pivot thresholds (relative to max diag): K * 1e-15 for the first
+// pass (numerically non-positive), 1e-4 for the second (cond(Q1) > 100).
+__global__ void __launch_bounds__(CH_THREADS)
+chol_kernel(const double* __restrict__ G, int K, float* __restrict__ Lout, int pass, int fail_code,
+            DevStatus* st) {
+  if (pass == 1 && st->orth_fail) return;
+  extern __shared__ __align__(16) unsigned char ch_smem[];
+  __shared__ int nonfinite;
+  __shared__ float wmax[CH_THREADS / 32];
+  __shared__ double maxdiag;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) nonfinite = 0;
+  if (warp == 0) {
+    double m = 0.0;
+    for (int i = lane; i < K; i += 32) m = fmax(m, G[i + i * K]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) maxdiag = m;
+  }
+  __syncthreads();
+  float cmax = 0.f;                          // largest off-diagonal cosine, in FP32
   for (int e = tid; e < K * K; e += CH_THREADS) {
     const double v = G[e];
-    A[e] = v;
     if (!isfinite(v)) nonfinite = 1;
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double m = 0.0;
-    for (int i = 0; i < K; ++i) m = fmax(m, A[i + i * K]);
-    maxdiag = m;
-    if (nonfinite || !(m > 0.0)) fail = 1;
-  }
-  __syncthreads();
-  const double tol = (pass == 0 ? (double)K * 1e-15 : 1e-4) * maxdiag;
-  for (int j = 0; j < K && !fail; ++j) {
-    if (tid == 0) {
-      const double d = A[j + j * K];
-      if (!(d > tol)) fail = 1;
-      else A[j + j * K] = sqrt(d);
+    const int c = e / K, r = e - c * K;
+    if (r > c) {
+      const float grr = (float)G[r + r * K], gcc = (float)G[c + c * K];
+      const float cs = (grr > 0.f && gcc > 0.f) ? fabsf((float)v) * rsqrtf(grr) * rsqrtf(gcc) : 1.f;
+      cmax = fmaxf(cmax, fminf(cs, 1.f));
     }
-    __syncthreads();
-    if (fail) break;
-    const double ljj = A[j + j * K];
-    for (int i = j + 1 + tid; i < K; i += CH_THREADS) A[i + j * K] /= ljj;
-    __syncthreads();
-    // trailing update of the lower triangle: A[i,k] -= L[i,j] L[k,j], j < k <= i
-    const int n = K - j - 1;
-    for (int e = tid; e < n * n; e += CH_THREADS) {
-      const int k = j + 1 + e / n, i = j + 1 + e % n;
-      if (i >= k) A[i + k * K] -= A[i + j * K] * A[k + j * K];
-    }
-    __syncthreads();
   }
-  if (fail) {
+  cmax = warp_max(cmax);
+  if (lane == 0) wmax[warp] = cmax;
+  __syncthreads();
+  float allmax = 0.f;
+#pragma unroll
+  for (int w = 0; w < CH_THREADS / 32; ++w) allmax = fmaxf(allmax, wmax[w]);
+  bool ok = !nonfinite && maxdiag > 0.0 && isfinite(maxdiag);
+  if (ok) {
+    const double tol = (pass == 0) ? (double)K * 1e-15 : 1e-4;
+    if (pass == 1 && allmax <= 1e-2f) ok = chol_body<float>(G, K, Lout, reinterpret_cast<float*>(ch_smem), maxdiag, tol);
+    else ok = chol_body<double>(G, K, Lout, reinterpret_cast<double*>(ch_smem), maxdiag, tol);
+  }
+  if (!ok) {
     if (tid == 0) {
       st->orth_fail = 1;
       if (nonfinite) set_error(st, RHOSVD_ENONFINITE);
@@ -81,26 +133,78 @@ chol_inv_kernel(const double* __restrict__ G, int K, float* __restrict__ Rinv, i
     }
     return;
   }
-  // L^-1 column c by thread c (forward substitution); L^-1(i,c), i > c, is kept
-  // in the unused strict upper triangle at A[c + i*K], its diagonal in diag[].
-  for (int c = tid; c < K; c += CH_THREADS) {
-    diag[c] = 1.0 / A[c + c * K];
-    for (int i = c + 1; i < K; ++i) {
-      double s = A[i + c * K] * diag[c];
-      for (int k = c + 1; k < i; ++k) s += A[i + k * K] * A[c + k * K];
-      A[c + i * K] = -s / A[i + i * K];
-    }
+  if (pass == 0 && tid == 0) st->orth_fail = 0;
+}
+
+// Row-parallel triangular solves with the Cholesky factor L (K x K, lower):
+// for every row y^T of Y (m x K, ld), mode 0 overwrites it with q^T where
+// L q = y, i.e. Q = Y L^-T = Y R^-1 (the CholeskyQR apply); mode 1 then also
+// solves L^T x = q, i.e. Y (L L^T)^-1 = Y G^-1 (normal-equation pseudo-inverse).
+// One thread per row, the row in registers (KB >= K, fully unrolled), L in
+// shared memory row-major for the forward sweep and column-major for the
+// backward sweep; the row tile is staged through shared memory so that global
+// loads and stores are coalesced.
+constexpr int TR_ROWS = 128;
+
+template <int KB>
+__global__ void __launch_bounds__(TR_ROWS)
+trsm_rows_kernel(float* __restrict__ Y, int64_t m, int K, int64_t ld, const float* __restrict__ L, int mode,
+                 const DevStatus* skip) {
+  if (skip != nullptr && skip->orth_fail) return;
+  extern __shared__ __align__(16) float tr_smem[];
+  float* Lr = tr_smem;                 // K x KB row-major: Lr[c*KB + k] = L(c,k)
+  float* Lc = Lr + KB * KB;            // KB x K column-major: Lc[k + c*KB] = L(k,c)
+  float* dinv = Lc + KB * KB;          // 1 / L(c,c)
+  float* tile = dinv + KB;             // TR_ROWS x pitch
+  const int pitch = K | 1;             // odd pitch: conflict-free per-thread rows
+  const int tid = threadIdx.x;
+  for (int e = tid; e < KB * KB; e += TR_ROWS) {
+    const int c = e / KB, k = e - c * KB;
+    const float v = (c < K && k < K) ? L[c + k * K] : 0.f;     // L(c,k)
+    Lr[c * KB + k] = v;
+    Lc[c + k * KB] = v;                                         // L(c,k) at column k
+  }
+  for (int c = tid; c < KB; c += TR_ROWS) dinv[c] = (c < K) ? 1.f / L[c + c * K] : 0.f;
+  const int64_t r0 = (int64_t)blockIdx.x * TR_ROWS;
+  const int nrow = (int)((m - r0) < TR_ROWS ? (m - r0) : TR_ROWS);
+  for (int e = tid; e < TR_ROWS * K; e += TR_ROWS) {
+    const int t = e % TR_ROWS, c = e / TR_ROWS;
+    if (t < nrow) tile[t * pitch + c] = Y[(r0 + t) + (int64_t)c * ld];
   }
   __syncthreads();
-  // R^-1 = (L^T)^-1 = (L^-1)^T: R^-1(r, c) = L^-1(c, r), upper triangular
-  for (int e = tid; e < K * K; e += CH_THREADS) {
-    const int c = e / K, r = e % K;
-    float v = 0.f;
-    if (r < c) v = (float)A[r + c * K];
-    else if (r == c) v = (float)diag[r];
-    Rinv[e] = v;
+  if (tid < nrow) {
+    float q[KB];
+#pragma unroll
+    for (int c = 0; c < KB; ++c) q[c] = (c < K) ? tile[tid * pitch + c] : 0.f;
+    // forward: q_c = (y_c - sum_{k<c} L(c,k) q_k) / L(c,c)
+#pragma unroll
+    for (int c = 0; c < KB; ++c) {
+      float s = q[c];
+      const float* lrow = Lr + c * KB;
+#pragma unroll
+      for (int k = 0; k < c; ++k) s = fmaf(-lrow[k], q[k], s);
+      q[c] = s * dinv[c];
+    }
+    if (mode == 1) {
+      // backward: x_c = (q_c - sum_{k>c} L(k,c) x_k) / L(c,c)
+#pragma unroll
+      for (int c = KB - 1; c >= 0; --c) {
+        float s = q[c];
+        const float* lcol = Lc + c * KB;
+#pragma unroll
+        for (int k = c + 1; k < KB; ++k) s = fmaf(-lcol[k], q[k], s);
+        q[c] = s * dinv[c];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < KB; ++c)
+      if (c < K) tile[tid * pitch + c] = q[c];
   }
-  if (pass == 0 && tid == 0) st->orth_fail = 0;
+  __syncthreads();
+  for (int e = tid; e < TR_ROWS * K; e += TR_ROWS) {
+    const int t = e % TR_ROWS, c = e / TR_ROWS;
+    if (t < nrow) Y[(r0 + t) + (int64_t)c * ld] = tile[t * pitch + c];
+  }
 }
 
 constexpr int HH_THREADS = 1024;
@@ -208,14 +312,37 @@ householder_kernel(float* A, int64_t m, int K, int64_t ld, DevStatus* st, int fo
 
 }  // namespace
 
-cudaError_t launch_chol_inv(const double* G, int K, float* Rinv, int pass, int fail_code, DevStatus* st,
-                            cudaStream_t stream) {
-  const size_t smem = ((size_t)K * K + K) * sizeof(double);
-  static const size_t kMax = ((size_t)RHOSVD_MAX_K * RHOSVD_MAX_K + RHOSVD_MAX_K) * sizeof(double);
-  cudaError_t e = allow_dynamic_smem((const void*)chol_inv_kernel, kMax);
+cudaError_t launch_chol(const double* G, int K, float* L, int pass, int fail_code, DevStatus* st,
+                        cudaStream_t stream) {
+  const size_t smem = (size_t)K * K * sizeof(double);
+  cudaError_t e = allow_dynamic_smem((const void*)chol_kernel,
+                                     (size_t)RHOSVD_MAX_K * RHOSVD_MAX_K * sizeof(double));
   if (e != cudaSuccess) return e;
-  chol_inv_kernel<<<1, CH_THREADS, smem, stream>>>(G, K, Rinv, pass, fail_code, st);
+  chol_kernel<<<1, CH_THREADS, smem, stream>>>(G, K, L, pass, fail_code, st);
   return cudaGetLastError();
+}
+
+template <int KB>
+static cudaError_t launch_trsm_kb(float* Y, int64_t m, int K, int64_t ld, const float* L, int mode,
+                                  const DevStatus* skip, cudaStream_t stream) {
+  const size_t smem = (2 * (size_t)KB * KB + KB + (size_t)TR_ROWS * (K | 1)) * sizeof(float);
+  cudaError_t e = allow_dynamic_smem((const void*)trsm_rows_kernel<KB>,
+                                     (2 * (size_t)KB * KB + KB + (size_t)TR_ROWS * (KB | 1)) * sizeof(float));
+  if (e != cudaSuccess) return e;
+  const unsigned grid = (unsigned)((m + TR_ROWS - 1) / TR_ROWS);
+  trsm_rows_kernel<KB><<<grid, TR_ROWS, smem, stream>>>(Y, m, K, ld, L, mode, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trsm_rows(float* Y, int64_t m, int K, int64_t ld, const float* L, int mode,
+                             const DevStatus* skip, cudaStream_t stream) {
+  if (m == 0) return cudaSuccess;
+  if (K <= 16) return launch_trsm_kb<16>(Y, m, K, ld, L, mode, skip, stream);
+  if (K <= 32) return launch_trsm_kb<32>(Y, m, K, ld, L, mode, skip, stream);
+  if (K <= 48) return launch_trsm_kb<48>(Y, m, K, ld, L, mode, skip, stream);
+  if (K <= 64) return launch_trsm_kb<64>(Y, m, K, ld, L, mode, skip, stream);
+  if (K <= 96) return launch_trsm_kb<96>(Y, m, K, ld, L, mode, skip, stream);
+  return launch_trsm_kb<128>(Y, m, K, ld, L, mode, skip, stream);
 }
 
 cudaError_t launch_householder(float* A, int64_t m, int K, int64_t ld, DevStatus* st, bool force,

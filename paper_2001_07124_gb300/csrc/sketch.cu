@@ -157,16 +157,17 @@ reduce_d_kernel(const double* __restrict__ part, int splits, int64_t n, double* 
 }
 
 // ---------------------------------------------------------------- TTM
-constexpr int TT_BJ = 128;
+constexpr int TT_MAX_BJ = 128;
 constexpr int TT_BI = 16;
 constexpr int TT_THREADS = 256;
 
-template <int KT>   // output columns per CTA = 16*KT
+template <int UJ, int KT>   // rows per CTA = 16*UJ, output columns per CTA = 16*KT
 __global__ void __launch_bounds__(TT_THREADS)
 ttm_kernel(View x, const float* __restrict__ M, int64_t m_i, int64_t m_k, int K, OView out,
            const DevStatus* skip) {
   if (skip != nullptr && skip->orth_fail) return;
   constexpr int BK = 16 * KT;
+  constexpr int TT_BJ = 16 * UJ;
   __shared__ float Xs[TT_BI][TT_BJ + 1];
   __shared__ float Ms[TT_BI][BK + 1];
   __shared__ int64_t xoff[TT_BJ];
@@ -191,9 +192,9 @@ ttm_kernel(View x, const float* __restrict__ M, int64_t m_i, int64_t m_k, int K,
   }
   __syncthreads();
 
-  float acc[8][KT];
+  float acc[UJ][KT];
 #pragma unroll
-  for (int u = 0; u < 8; ++u)
+  for (int u = 0; u < UJ; ++u)
 #pragma unroll
     for (int v = 0; v < KT; ++v) acc[u][v] = 0.f;
 
@@ -217,20 +218,20 @@ ttm_kernel(View x, const float* __restrict__ M, int64_t m_i, int64_t m_k, int K,
     __syncthreads();
 #pragma unroll
     for (int ii = 0; ii < TT_BI; ++ii) {
-      float a[8], b[KT];
+      float a[UJ], b[KT];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) a[u] = Xs[ii][tj + 16 * u];
+      for (int u = 0; u < UJ; ++u) a[u] = Xs[ii][tj + 16 * u];
 #pragma unroll
       for (int v = 0; v < KT; ++v) b[v] = Ms[ii][tk + 16 * v];
 #pragma unroll
-      for (int u = 0; u < 8; ++u)
+      for (int u = 0; u < UJ; ++u)
 #pragma unroll
         for (int v = 0; v < KT; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int u = 0; u < 8; ++u) {
+  for (int u = 0; u < UJ; ++u) {
     const int64_t off = ooff[tj + 16 * u];
     if (off < 0) continue;
 #pragma unroll
@@ -334,12 +335,17 @@ cudaError_t launch_ttm(const View& x, const float* Mp, int64_t m_i, int64_t m_k,
                        const DevStatus* skip, cudaStream_t st) {
   const int64_t J = x.L * x.Rt;
   if (J == 0 || K == 0) return cudaSuccess;
-  const unsigned gx = (unsigned)((J + TT_BJ - 1) / TT_BJ);
+  // 128-row tiles when there are enough of them to fill the GPU, 32-row tiles otherwise
+  const bool wide = (J + TT_MAX_BJ - 1) / TT_MAX_BJ >= 296;
+  const int bj = wide ? 128 : 32;
+  const unsigned gx = (unsigned)((J + bj - 1) / bj);
   if (K <= 64) {
-    ttm_kernel<4><<<dim3(gx, 1), TT_THREADS, 0, st>>>(x, Mp, m_i, m_k, K, out, skip);
+    if (wide) ttm_kernel<8, 4><<<dim3(gx, 1), TT_THREADS, 0, st>>>(x, Mp, m_i, m_k, K, out, skip);
+    else ttm_kernel<2, 4><<<dim3(gx, 1), TT_THREADS, 0, st>>>(x, Mp, m_i, m_k, K, out, skip);
   } else {
-    ttm_kernel<8><<<dim3(gx, (unsigned)((K + 127) / 128)), TT_THREADS, 0, st>>>(x, Mp, m_i, m_k, K, out,
-                                                                                skip);
+    const dim3 grid(gx, (unsigned)((K + 127) / 128));
+    if (wide) ttm_kernel<8, 8><<<grid, TT_THREADS, 0, st>>>(x, Mp, m_i, m_k, K, out, skip);
+    else ttm_kernel<2, 8><<<grid, TT_THREADS, 0, st>>>(x, Mp, m_i, m_k, K, out, skip);
   }
   return cudaGetLastError();
 }
