@@ -83,10 +83,9 @@ View matrix_view(const float* p, int64_t m, int K, int64_t ld) {
 // Y (I x K, ld) = X_(n) W with W(j,k) = w.p[l + r*w_r + k*w_k]
 void op_sketch(Ctx& c, const View& x, const WView& w, int K, float* Y, int64_t ldy) {
   Scope sc(c);
-  SketchPlan pl = plan_sketch(x.I, K, x.L * x.Rt);
-  float* part = c.take<float>(sketch_partial_floats(pl, x.I, K));
+  float* part = c.take<float>(sketch_scratch_floats(x.I, K, x.L * x.Rt));
   c.launches += 2;
-  if (!c.dry) c.check(launch_sketch(x, w, K, Y, ldy, part, c.s));
+  if (!c.dry) c.check(launch_sketch_auto(x, w, K, Y, ldy, part, c.st, c.s));
 }
 
 // Gd (I x I, FP64) = X_(n) W accumulated in double-float
@@ -540,8 +539,7 @@ size_t primitive_ws(const Geom& g, int Kmax) {
   size_t fixed = c.off;
   size_t extra = 0;
   for (int n = 0; n < g.N; ++n) {
-    SketchPlan pl = plan_sketch(g.d[n], Kmax, g.J(n));
-    extra = std::max(extra, sketch_partial_floats(pl, g.d[n], Kmax) * sizeof(double));
+    extra = std::max(extra, sketch_scratch_floats(g.d[n], Kmax, g.J(n)) * sizeof(double));
     SketchPlan pz = plan_sketch(Kmax, Kmax, g.J(n));
     extra = std::max(extra, sketch_partial_floats(pz, Kmax, Kmax) * sizeof(double));
   }

@@ -50,6 +50,25 @@ cudaError_t launch_sketch(const View& x, const WView& w, int K, float* Y, int64_
 // that the partial sums fit a caller-provided scratch of max_splits * I * K floats.
 cudaError_t launch_sketch_capped(const View& x, const WView& w, int K, float* Y, int64_t ldy,
                                  float* part, int max_splits, cudaStream_t st);
+// Fixed-order FP32 reduction of sketch partials part[s][k][i] into Y (ld ldy).
+cudaError_t launch_reduce_partials_f(const float* part, int splits, int64_t I, int K, float* Y, int64_t ldy,
+                                     cudaStream_t st);
+
+// ---- tc_sketch.cu: tcgen05 (3xTF32) sketch for mode-1 layouts
+struct TcSketchPlan {
+  int splits, mgroups;
+  int64_t jchunk;
+};
+bool tc_sketch_supported(const View& x, const WView& w, int K);
+TcSketchPlan plan_tc_sketch(int64_t I, int K, int64_t J);
+cudaError_t launch_tc_sketch(const View& x, const WView& w, int K, float* Y, int64_t ldy, float* part,
+                             DevStatus* st, cudaStream_t stream);
+
+// Sketch with the fastest kernel that supports the layout; part must hold
+// sketch_scratch_floats(x.I, K, J) floats.
+size_t sketch_scratch_floats(int64_t I, int K, int64_t J);
+cudaError_t launch_sketch_auto(const View& x, const WView& w, int K, float* Y, int64_t ldy, float* part,
+                               DevStatus* st, cudaStream_t stream);
 // G = X_(n) W accumulated in double-float, reduced in FP64 to Gd (K x I... as I x K, ld = I).
 cudaError_t launch_sketch_df(const View& x, const WView& w, int K, double* Gd, int64_t ldg,
                              double* ws_part, cudaStream_t st);

@@ -296,6 +296,29 @@ cudaError_t launch_sketch(const View& x, const WView& w, int K, float* Y, int64_
   return cudaGetLastError();
 }
 
+cudaError_t launch_reduce_partials_f(const float* part, int splits, int64_t I, int K, float* Y, int64_t ldy,
+                                     cudaStream_t st) {
+  const int64_t n = I * K;
+  reduce_partials_kernel<float, float><<<(unsigned)((n + 31) / 32), 32 * RD_ROWS, 0, st>>>(part, splits, I, K, Y,
+                                                                                          ldy);
+  return cudaGetLastError();
+}
+
+size_t sketch_scratch_floats(int64_t I, int K, int64_t J) {
+  const size_t simt = sketch_partial_floats(plan_sketch(I, K, J), I, K);
+  const TcSketchPlan tp = plan_tc_sketch(I, K, J);
+  return std::max(simt, (size_t)tp.splits * (size_t)I * (size_t)K);
+}
+
+cudaError_t launch_sketch_auto(const View& x, const WView& w, int K, float* Y, int64_t ldy, float* part,
+                               DevStatus* st, cudaStream_t stream) {
+  if (st != nullptr && tc_sketch_supported(x, w, K)) {
+    cudaError_t e = launch_tc_sketch(x, w, K, Y, ldy, part, st, stream);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  return launch_sketch(x, w, K, Y, ldy, part, stream);
+}
+
 cudaError_t launch_sketch_capped(const View& x, const WView& w, int K, float* Y, int64_t ldy, float* part,
                                  int max_splits, cudaStream_t st) {
   const int64_t J = x.L * x.Rt;

@@ -109,6 +109,42 @@ def test_sketch_seeded_omega_vs_oracle_generator():
         assert_close_abs(Y, a @ om, np.abs(a) @ np.abs(om))
 
 
+# Mode-1 layouts with I and J multiples of 4 run on the tcgen05 (3xTF32) sketch
+# kernel: N padded to 16/32/48/64, partial last 8-column blocks (J % 8 == 4),
+# one or several 512-row groups, 1-4 MMA tiles per group.
+TC_CASES = [((512, 64, 64), 42), ((256, 40, 52), 16), ((100, 48, 50), 33), ((1024, 32, 40), 64),
+            ((772, 36, 36), 20), ((128, 36, 111), 7), ((4, 300, 20), 4)]
+
+
+@pytest.mark.parametrize("dims,K", TC_CASES)
+def test_tc_sketch_mode1_parity(dims, K):
+    x = random_tensor(dims, 21)
+    X = dev(x)
+    a = T.unfold(f32(x), 0)
+    J = int(np.prod(dims[1:]))
+    om = gaussian_matrix(22, J, K)
+    om64 = om.astype(np.float64)
+    bound = np.abs(a) @ np.abs(om64)
+    Y = host(R().rhosvd_sketch(X, dims, 0, K, Omega=dev_mat(om)))
+    assert_close_abs(Y, a @ om64, bound)
+    # the workspace-free entry point keeps the SIMT kernel: both must agree
+    Y2 = host(R().rhosvd_sketch_noalloc(X, dims, 0, K, dev_mat(om)))
+    assert_close_abs(Y, Y2, bound, rel=2e-5)
+    # seeded test matrix on the device vs the oracle's generator
+    Y3 = host(R().rhosvd_sketch(X, dims, 0, K, seed=77))
+    om3 = philox.omega(77, 0, J, K).astype(np.float64)
+    assert_close_abs(Y3, a @ om3, np.abs(a) @ np.abs(om3))
+
+
+def test_tc_sketch_is_deterministic():
+    dims, K = (512, 64, 64), 42
+    X = dev(random_tensor(dims, 23))
+    om = dev_mat(gaussian_matrix(24, 64 * 64, K))
+    y1 = host(R().rhosvd_sketch(X, dims, 0, K, Omega=om))
+    y2 = host(R().rhosvd_sketch(X, dims, 0, K, Omega=om))
+    np.testing.assert_array_equal(y1, y2)
+
+
 # ------------------------------------------------------------------ TTM / core projection
 
 @pytest.mark.parametrize("dims,K", [((67, 45, 83), (7, 45, 12)), ((9, 10, 11, 12), (3, 4, 5, 6)),
