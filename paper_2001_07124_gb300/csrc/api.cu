@@ -109,7 +109,7 @@ void op_gram_matrix(Ctx& c, const float* A, int64_t m, int K, int64_t ld, double
 void op_ttm(Ctx& c, const View& x, const float* M, int64_t m_i, int64_t m_k, int K, const OView& out,
             const DevStatus* skip = nullptr) {
   if (x.L * x.Rt > 0 && K > 0) c.launches += 1;
-  if (!c.dry) c.check(launch_ttm(x, M, m_i, m_k, K, out, skip, c.s));
+  if (!c.dry) c.check(launch_ttm_auto(x, M, m_i, m_k, K, out, skip, c.st, c.s));
 }
 
 // CholeskyQR2 with device-side Householder fallback, in place on Y (m x K, ld)

@@ -78,6 +78,14 @@ cudaError_t launch_sketch_df(const View& x, const WView& w, int K, double* Gd, i
 cudaError_t launch_ttm(const View& x, const float* Mp, int64_t m_i, int64_t m_k, int K,
                        const OView& out, const DevStatus* skip_if_orth_fail, cudaStream_t st);
 
+// ---- tc_ttm.cu: tcgen05 (3xTF32) n-mode product for mode-1 layouts
+bool tc_ttm_supported(const View& x, int64_t m_i, int64_t m_k, int K, const OView& out);
+cudaError_t launch_tc_ttm(const View& x, const float* Mp, int64_t m_k, int K, const OView& out,
+                          const DevStatus* skip, DevStatus* st, cudaStream_t stream);
+// TTM with the fastest kernel that supports the layout (st receives device errors).
+cudaError_t launch_ttm_auto(const View& x, const float* Mp, int64_t m_i, int64_t m_k, int K, const OView& out,
+                            const DevStatus* skip, DevStatus* st, cudaStream_t stream);
+
 // ---- gram.cu
 // G (K x K, FP64) = A^T A for A m x K (ld).  exact: double-float products
 // (FP64-accurate for ill-conditioned A); otherwise FP32 within 64-row tiles and

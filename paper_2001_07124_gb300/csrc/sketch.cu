@@ -319,6 +319,15 @@ cudaError_t launch_sketch_auto(const View& x, const WView& w, int K, float* Y, i
   return launch_sketch(x, w, K, Y, ldy, part, stream);
 }
 
+cudaError_t launch_ttm_auto(const View& x, const float* Mp, int64_t m_i, int64_t m_k, int K, const OView& out,
+                            const DevStatus* skip, DevStatus* st, cudaStream_t stream) {
+  if (st != nullptr && tc_ttm_supported(x, m_i, m_k, K, out)) {
+    cudaError_t e = launch_tc_ttm(x, Mp, m_k, K, out, skip, st, stream);
+    if (e != cudaErrorNotSupported) return e;
+  }
+  return launch_ttm(x, Mp, m_i, m_k, K, out, skip, stream);
+}
+
 cudaError_t launch_sketch_capped(const View& x, const WView& w, int K, float* Y, int64_t ldy, float* part,
                                  int max_splits, cudaStream_t st) {
   const int64_t J = x.L * x.Rt;

@@ -6,15 +6,16 @@
 // CTA owns up to 512 rows i (four 128-row MMA tiles) and a contiguous range of
 // j, and writes its partial I x K block for the fixed-order reducer.
 //
-// Data path per 8-column block of j (one MMA K step of kind::tf32):
-//   * TMA copies the X tile (8 x 512 FP32, two 256-wide boxes) and the raw W
-//     tile (8 x NPAD) into a 6-stage shared-memory ring (producer warp 4).
-//   * Four transform warps (0-3, one TMEM lane quadrant each) read X rows from
+// Data path per 16-column block of j (two MMA K steps of kind::tf32):
+//   * TMA copies the X tile (16 x 512 FP32, two 256-wide boxes) and the raw W
+//     tile (16 x 64) into a 4-stage shared-memory ring (producer warp 8).
+//   * Eight transform warps (two warpgroups; warp w owns TMEM lane quadrant
+//     w % 4, warpgroup g the 128-row tiles 2g and 2g+1) read X rows from
 //     shared memory, split every value into TF32 hi + lo (3xTF32) and store
 //     both into tensor memory as the A operand (tcgen05.st), so the skinny
 //     N <= 64 GEMM never re-reads A from shared memory; they also split the W
 //     tile into hi/lo B tiles in the canonical no-swizzle K-major layout.
-//   * One thread of warp 5 issues, per 128-row tile, the three MMAs
+//   * One thread of warp 9 issues, per 128-row tile and K step, the three MMAs
 //     A_hi*B_hi + A_hi*B_lo + A_lo*B_hi into FP32 accumulators in TMEM.
 //   * At the end the transform warps read the accumulators (tcgen05.ld) and
 //     write the partial sums.
@@ -31,20 +32,23 @@ namespace {
 
 using namespace tc;
 
-constexpr int BJ = 8;                     // j per k-block (one tf32 MMA K)
-constexpr int X_STAGES = 6;
-constexpr int A_STAGES = 4;
+constexpr int BJ = 16;                    // j per stage (two tf32 MMA K steps of 8)
+constexpr int X_STAGES = 5;
+constexpr int A_STAGES = 2;
 constexpr int ROWS = 512;                 // rows i per CTA (4 MMA tiles)
 constexpr int BOXW = 256;                 // TMA box width in i
-constexpr int NUM_THREADS = 192;          // warps 0-3 transform/epilogue, 4 producer, 5 MMA
+constexpr int NUM_XFORM = 256;            // warps 0-7
+constexpr int NUM_THREADS = NUM_XFORM + 64;   // + warp 8 producer, warp 9 MMA issuer
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int D_COLS = 64;                // accumulator columns reserved per tile
 constexpr int A_COL0 = 4 * D_COLS;        // first TMEM column of the A stages
+constexpr int A_STAGE_COLS = 128;         // per stage: 4 tiles x (16 hi + 16 lo)
+constexpr int B_TILE = 64 * BJ;           // floats per B tile (N <= 64)
 
 struct __align__(1024) SketchSmem {
   float x[X_STAGES][ROWS / BOXW][BJ * BOXW];   // TMA boxes: [box][jj][256]
-  float wraw[X_STAGES][64 * BJ];               // TMA box [n][jj], rows n >= K are zero-filled
-  float b[A_STAGES][2][64 * BJ];               // hi / lo B tiles, canonical K-major layout
+  float wraw[X_STAGES][B_TILE];                // TMA box [n][jj], rows n >= K are zero-filled
+  float b[A_STAGES][2][B_TILE];                // hi / lo B tiles, canonical K-major layout
   uint64_t full_x[X_STAGES], empty_x[X_STAGES];
   uint64_t full_a[A_STAGES], empty_a[A_STAGES];
   uint64_t done;
@@ -52,11 +56,10 @@ struct __align__(1024) SketchSmem {
   int abort_flag;
 };
 
-// byte offset of element (n, kk) in a K-major no-swizzle B tile: 8x16B core
-// matrices, LBO = 128 (K direction), SBO = 256 (N direction)
-__device__ __forceinline__ int b_off(int n, int kk) {
-  return (n >> 3) * 256 + (kk >> 2) * 128 + (n & 7) * 16 + (kk & 3) * 4;
-}
+// B tiles (N x 16 K elements, K-major, no swizzle): element (n, kk) sits at
+// byte (n >> 3) * 512 + (kk >> 2) * 128 + (n & 7) * 16 + (kk & 3) * 4, i.e.
+// 8-row x 16-byte core matrices with LBO = 128 (K direction) and SBO = 512
+// (N direction); the second MMA K step starts 256 bytes in.
 
 template <int NPAD>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
@@ -79,17 +82,17 @@ tc_sketch_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
   if (tid == 0) {
     for (int s = 0; s < X_STAGES; ++s) {
       mbar_init(&sm.full_x[s], 1);
-      mbar_init(&sm.empty_x[s], 128);
+      mbar_init(&sm.empty_x[s], NUM_XFORM);
     }
     for (int a = 0; a < A_STAGES; ++a) {
-      mbar_init(&sm.full_a[a], 128);
+      mbar_init(&sm.full_a[a], NUM_XFORM);
       mbar_init(&sm.empty_a[a], 1);
     }
     mbar_init(&sm.done, 1);
     sm.abort_flag = 0;
     mbar_fence_init();
   }
-  if (warp == 5) {
+  if (warp == 9) {
     tmem_alloc(&sm.tmem_base, TMEM_COLS);
     tmem_relinquish();
   }
@@ -100,10 +103,10 @@ tc_sketch_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
   volatile int* abort_flag = &sm.abort_flag;
   bool ok = true;
 
-  if (warp == 4) {
+  if (warp == 8) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      const uint32_t bytes = (uint32_t)(nbox * BJ * BOXW * 4 + 64 * BJ * 4);
+      const uint32_t bytes = (uint32_t)(nbox * BJ * BOXW * 4 + B_TILE * 4);
       for (int kb = 0; kb < nkb && ok; ++kb) {
         const int s = kb % X_STAGES;
         const uint32_t ph = (uint32_t)(kb / X_STAGES) & 1u;
@@ -114,7 +117,7 @@ tc_sketch_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
         tma_load_2d(sm.wraw[s], &tmW, jt, 0, &sm.full_x[s]);
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == 9) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       for (int kb = 0; kb < nkb && ok; ++kb) {
@@ -122,22 +125,28 @@ tc_sketch_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
         const uint32_t ph = (uint32_t)(kb / A_STAGES) & 1u;
         if (!mbar_wait(&sm.full_a[a], ph, abort_flag)) { ok = false; break; }
         tc_fence_after();
-        const uint64_t bhi = smem_desc_kmajor_nosw(smem_u32(sm.b[a][0]), 128, 256);
-        const uint64_t blo = smem_desc_kmajor_nosw(smem_u32(sm.b[a][1]), 128, 256);
+        const uint32_t bhi = smem_u32(sm.b[a][0]), blo = smem_u32(sm.b[a][1]);
         for (int t = 0; t < mt; ++t) {
           const uint32_t d = tmem + (uint32_t)(t * D_COLS);
-          const uint32_t ahi = tmem + (uint32_t)(A_COL0 + a * 64 + t * 16);
-          mma_tf32_ts(d, ahi, bhi, idesc, kb > 0 ? 1u : 0u);
-          mma_tf32_ts(d, ahi, blo, idesc, 1u);
-          mma_tf32_ts(d, ahi + 8, bhi, idesc, 1u);
+          const uint32_t ahi = tmem + (uint32_t)(A_COL0 + a * A_STAGE_COLS + t * 32);
+#pragma unroll
+          for (int ks = 0; ks < 2; ++ks) {
+            const uint64_t dbh = smem_desc_kmajor_nosw(bhi + ks * 256, 128, 512);
+            const uint64_t dbl = smem_desc_kmajor_nosw(blo + ks * 256, 128, 512);
+            mma_tf32_ts(d, ahi + ks * 8, dbh, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+            mma_tf32_ts(d, ahi + ks * 8, dbl, idesc, 1u);
+            mma_tf32_ts(d, ahi + 16 + ks * 8, dbh, idesc, 1u);
+          }
         }
         mma_commit(&sm.empty_a[a]);
       }
       mma_commit(&sm.done);
     }
   } else {
-    // ------------------------------------------------------------ transform (warps 0-3)
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+    // ------------------------------------------------------------ transform (warps 0-7)
+    const int quad = warp & 3, wg = warp >> 2;
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    const int row_in_tile = quad * 32 + lane;
     for (int kb = 0; kb < nkb && ok; ++kb) {
       const int s = kb % X_STAGES, a = kb % A_STAGES;
       const uint32_t phx = (uint32_t)(kb / X_STAGES) & 1u, pha = (uint32_t)(kb / A_STAGES) & 1u;
@@ -146,28 +155,35 @@ tc_sketch_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
       if (!mbar_wait(&sm.full_x[s], phx, abort_flag)) { ok = false; break; }
       if (!mbar_wait(&sm.empty_a[a], pha ^ 1u, abort_flag)) { ok = false; break; }
       tc_fence_after();
-      for (int t = 0; t < mt; ++t) {
-        const int r = t * 128 + tid;                 // row within the CTA's block
-        const float* xb = sm.x[s][r / BOXW] + (r % BOXW);
-        uint32_t hi[8], lo[8];
 #pragma unroll
-        for (int jj = 0; jj < BJ; ++jj) {
-          const float v = (jj < valid && r < rows) ? xb[jj * BOXW] : 0.f;
-          split_tf32(v, hi[jj], lo[jj]);
+      for (int tt = 0; tt < 2; ++tt) {
+        const int t = 2 * wg + tt;
+        if (t < mt) {
+          const int r = t * 128 + row_in_tile;       // row within the CTA's block
+          const float* xb = sm.x[s][r / BOXW] + (r % BOXW);
+          uint32_t hi[16], lo[16];
+#pragma unroll
+          for (int jj = 0; jj < BJ; ++jj) {
+            const float v = (jj < valid && r < rows) ? xb[jj * BOXW] : 0.f;
+            split_tf32(v, hi[jj], lo[jj]);
+          }
+          const uint32_t col = tmem + (uint32_t)(A_COL0 + a * A_STAGE_COLS + t * 32);
+          tmem_st_x16(col + lane_base, hi);
+          tmem_st_x16(col + 16 + lane_base, lo);
         }
-        const uint32_t col = tmem + (uint32_t)(A_COL0 + a * 64 + t * 16);
-        tmem_st_x8(col + lane_base, hi);
-        tmem_st_x8(col + 8 + lane_base, lo);
       }
-      // B tiles: element (n, jj) of W, split into hi / lo
-      for (int e = tid; e < NPAD * BJ; e += 128) {
-        const int n = e / BJ, jj = e % BJ;
+      // B tiles: element (n, jj) of W, split into hi / lo.  Threads walk the
+      // canonical layout word by word (conflict-free stores): word w holds
+      // n = 8 (w >> 7) + ((w >> 2) & 7), jj = 4 ((w >> 5) & 3) + (w & 3).
+#pragma unroll
+      for (int u = 0; u < NPAD * BJ / NUM_XFORM; ++u) {
+        const int w = tid + u * NUM_XFORM;
+        const int n = 8 * (w >> 7) + ((w >> 2) & 7), jj = 4 * ((w >> 5) & 3) + (w & 3);
         const float v = (jj < valid && n < K) ? sm.wraw[s][n * BJ + jj] : 0.f;
         uint32_t h, l;
         split_tf32(v, h, l);
-        const int off = b_off(n, jj) >> 2;
-        reinterpret_cast<uint32_t*>(sm.b[a][0])[off] = h;
-        reinterpret_cast<uint32_t*>(sm.b[a][1])[off] = l;
+        reinterpret_cast<uint32_t*>(sm.b[a][0])[w] = h;
+        reinterpret_cast<uint32_t*>(sm.b[a][1])[w] = l;
       }
       fence_proxy_async_smem();
       tmem_wait_st();
@@ -179,8 +195,11 @@ tc_sketch_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
     if (ok && nkb > 0) ok = mbar_wait(&sm.done, 0, abort_flag);
     if (ok) {
       tc_fence_after();
-      for (int t = 0; t < mt; ++t) {
-        const int64_t i = i0 + t * 128 + tid;
+#pragma unroll
+      for (int tt = 0; tt < 2; ++tt) {
+        const int t = 2 * wg + tt;
+        if (t >= mt) continue;
+        const int64_t i = i0 + t * 128 + row_in_tile;
 #pragma unroll
         for (int c0 = 0; c0 < NPAD; c0 += 16) {
           uint32_t v[16];
@@ -202,9 +221,8 @@ tc_sketch_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
   // teardown: every role is past its last wait (all waits are bounded); let
   // in-flight MMAs drain before TMEM is released
   __syncthreads();
-  if (warp == 5) {
+  if (warp == 9) {
     if (sm.abort_flag && lane == 0) {
-      // best effort: wait (bounded) for the last commit so no MMA still writes TMEM
       const uint64_t t0 = globaltimer_ns();
       while (!mbar_try_wait(&sm.done, 0) && globaltimer_ns() - t0 < kWaitLimitNs) {
       }

@@ -1,0 +1,316 @@
+// Tensor-core (tcgen05) n-mode product for a mode-1 layout:
+//   Out(j, k) = sum_i X[i + I*j] M(i, k),   M(i, k) = Mp[i + ldm*k]
+// i.e. Z = X_(1)^T Q (the power-iteration TTM of Alg. 1 step 2) and
+// B^T = X_(1)^T Q (the projection B = Q^T X_(1), Alg. 1 step 4), with Out
+// written at Out[j*o_r + k*o_k] (o_r = 1, o_k = J for the J x K "Z layout").
+//
+// Persistent, warp-specialised: each CTA takes 128-row tiles of j in turn and
+// contracts over all of i in stages of 32:
+//   * warp 12 (producer): TMA copies the X tile (128 rows j x 32 floats i, 128B
+//     swizzle) and the raw M tile (64 x 32) of a stage into a 6-stage ring;
+//   * warps 0-7 (two transform warpgroups, alternating stages): split X into
+//     TF32 hi/lo and store it in tensor memory as the A operand (thread = row j
+//     = TMEM lane), split M into hi/lo B tiles in the canonical K-major layout;
+//   * warp 13 (one thread): per stage, four K steps of the three MMAs
+//     A_hi*B_hi + A_hi*B_lo + A_lo*B_hi into a double-buffered FP32 TMEM
+//     accumulator, committing the tile when its last stage is issued;
+//   * warps 8-11 (epilogue): read a finished accumulator (tcgen05.ld), write
+//     the rows of Out, and hand the buffer back while the next tile computes.
+// Requirements (checked by the launcher): I % 4 == 0, ldm % 4 == 0, K <= 64.
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_common.cuh"
+
+namespace rhosvd {
+namespace {
+
+using namespace tc;
+
+constexpr int BI = 32;                    // contraction elements per stage (4 MMA K steps)
+constexpr int TILE_J = 128;               // rows j per tile (one MMA M)
+constexpr int X_STAGES = 6;
+constexpr int A_STAGES = 4;
+constexpr int NUM_XFORM = 256;            // warps 0-7
+constexpr int NUM_EPI = 128;              // warps 8-11
+constexpr int PRODUCER_WARP = 12, MMA_WARP = 13;
+constexpr int NUM_THREADS = 448;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int D_COLS = 64;                // per accumulator buffer
+constexpr int A_COL0 = 2 * D_COLS;        // A stages after the two accumulators
+constexpr int A_STAGE_COLS = 2 * BI;      // 32 hi + 32 lo columns
+constexpr int M_TILE = 64 * BI;           // floats per B tile (N <= 64)
+
+struct __align__(1024) TtmSmem {
+  float x[X_STAGES][TILE_J * BI];          // TMA tile [j][i], 128B rows, 128B swizzle
+  float mraw[X_STAGES][M_TILE];            // TMA tile [k][i], rows k >= K zero-filled
+  float b[A_STAGES][2][M_TILE];            // hi / lo B tiles, canonical K-major layout
+  uint64_t full_x[X_STAGES], empty_x[X_STAGES];
+  uint64_t full_a[A_STAGES], empty_a[A_STAGES];
+  uint64_t d_full[2], d_empty[2];
+  uint32_t tmem_base;
+  int abort_flag;
+};
+
+// B tile with 32 K elements: element (n, kk) at byte (n >> 3) * 1024 +
+// (kk >> 2) * 128 + (n & 7) * 16 + (kk & 3) * 4 (LBO = 128, SBO = 1024); MMA
+// K step ks starts 256 * ks bytes in.  Word w of the tile holds
+// n = 8 (w >> 8) + ((w >> 2) & 7), kk = 4 ((w >> 5) & 7) + (w & 3).
+
+template <int NPAD>
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+tc_ttm_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmM, int I,
+                 int64_t J, int K, float* __restrict__ out, int64_t o_k, int64_t o_r,
+                 const DevStatus* skip, DevStatus* st) {
+  if (skip != nullptr && skip->orth_fail) return;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  TtmSmem& sm = *reinterpret_cast<TtmSmem*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = (int)((J + TILE_J - 1) / TILE_J);
+  const int nst = (I + BI - 1) / BI;                  // stages per tile
+  constexpr uint32_t idesc = idesc_tf32(128, NPAD);
+
+  if (tid == 0) {
+    for (int s = 0; s < X_STAGES; ++s) {
+      mbar_init(&sm.full_x[s], 1);
+      mbar_init(&sm.empty_x[s], 128);
+    }
+    for (int a = 0; a < A_STAGES; ++a) {
+      mbar_init(&sm.full_a[a], 128);
+      mbar_init(&sm.empty_a[a], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&sm.d_full[b], 1);
+      mbar_init(&sm.d_empty[b], NUM_EPI);
+    }
+    sm.abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == MMA_WARP) {
+    tmem_alloc(&sm.tmem_base, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = sm.tmem_base;
+  volatile int* abort_flag = &sm.abort_flag;
+  bool ok = true;
+  // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
+  const int my_tiles = (ntiles > (int)blockIdx.x) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const int total = my_tiles * nst;                   // stages of this CTA
+
+  if (warp == PRODUCER_WARP) {
+    if (lane == 0) {
+      const uint32_t bytes = (uint32_t)(TILE_J * BI * 4 + M_TILE * 4);
+      for (int g = 0; g < total && ok; ++g) {
+        const int s = g % X_STAGES;
+        const uint32_t ph = (uint32_t)(g / X_STAGES) & 1u;
+        if (!mbar_wait(&sm.empty_x[s], ph ^ 1u, abort_flag)) { ok = false; break; }
+        const int tile = (int)blockIdx.x + (g / nst) * (int)gridDim.x;
+        const int ib = (g % nst) * BI;
+        mbar_arrive_expect_tx(&sm.full_x[s], bytes);
+        tma_load_2d(sm.x[s], &tmX, ib, tile * TILE_J, &sm.full_x[s]);
+        tma_load_2d(sm.mraw[s], &tmM, ib, 0, &sm.full_x[s]);
+      }
+    }
+  } else if (warp == MMA_WARP) {
+    if (lane == 0) {
+      for (int g = 0; g < total && ok; ++g) {
+        const int tl = g / nst, ks0 = g % nst;
+        const int buf = tl & 1;
+        if (ks0 == 0) {                                // accumulator buffer must be drained
+          if (!mbar_wait(&sm.d_empty[buf], ((uint32_t)(tl >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+        }
+        const int a = g % A_STAGES;
+        if (!mbar_wait(&sm.full_a[a], (uint32_t)(g / A_STAGES) & 1u, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * D_COLS);
+        const uint32_t ahi = tmem + (uint32_t)(A_COL0 + a * A_STAGE_COLS);
+        const uint32_t bhi = smem_u32(sm.b[a][0]), blo = smem_u32(sm.b[a][1]);
+#pragma unroll
+        for (int ks = 0; ks < BI / 8; ++ks) {
+          const uint64_t dbh = smem_desc_kmajor_nosw(bhi + ks * 256, 128, 1024);
+          const uint64_t dbl = smem_desc_kmajor_nosw(blo + ks * 256, 128, 1024);
+          mma_tf32_ts(d, ahi + ks * 8, dbh, idesc, (ks0 > 0 || ks > 0) ? 1u : 0u);
+          mma_tf32_ts(d, ahi + ks * 8, dbl, idesc, 1u);
+          mma_tf32_ts(d, ahi + BI + ks * 8, dbh, idesc, 1u);
+        }
+        mma_commit(&sm.empty_a[a]);
+        if (ks0 == nst - 1) mma_commit(&sm.d_full[buf]);
+      }
+    }
+  } else if (warp < 8) {
+    // ------------------------------------------------------------ transform
+    const int wg = warp >> 2, quad = warp & 3;
+    const int row = quad * 32 + lane;                 // j within the tile = TMEM lane
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    const int xt = tid & 127;                         // thread index within the warpgroup
+    for (int g = wg; g < total && ok; g += 2) {
+      const int s = g % X_STAGES, a = g % A_STAGES;
+      if (!mbar_wait(&sm.full_x[s], (uint32_t)(g / X_STAGES) & 1u, abort_flag)) { ok = false; break; }
+      if (!mbar_wait(&sm.empty_a[a], ((uint32_t)(g / A_STAGES) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+      tc_fence_after();
+      // row `row` of the swizzled X tile: logical 16-byte chunk c sits at chunk c ^ (row & 7)
+      const float4* xr = reinterpret_cast<const float4*>(sm.x[s] + row * BI);
+      uint32_t hi[32], lo[32];
+#pragma unroll
+      for (int c = 0; c < BI / 4; ++c) {
+        const float4 v = xr[c ^ (row & 7)];
+        split_tf32(v.x, hi[4 * c + 0], lo[4 * c + 0]);
+        split_tf32(v.y, hi[4 * c + 1], lo[4 * c + 1]);
+        split_tf32(v.z, hi[4 * c + 2], lo[4 * c + 2]);
+        split_tf32(v.w, hi[4 * c + 3], lo[4 * c + 3]);
+      }
+      const uint32_t col = tmem + (uint32_t)(A_COL0 + a * A_STAGE_COLS) + lane_base;
+      uint32_t h16[16], l16[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) { h16[q] = hi[q]; l16[q] = lo[q]; }
+      tmem_st_x16(col, h16);
+      tmem_st_x16(col + BI, l16);
+#pragma unroll
+      for (int q = 0; q < 16; ++q) { h16[q] = hi[16 + q]; l16[q] = lo[16 + q]; }
+      tmem_st_x16(col + 16, h16);
+      tmem_st_x16(col + BI + 16, l16);
+      // B tiles: M(i, k) for the stage, element (n = k, kk = i offset)
+#pragma unroll
+      for (int u = 0; u < NPAD * BI / 128; ++u) {
+        const int w = xt + u * 128;
+        const int n = 8 * (w >> 8) + ((w >> 2) & 7), kk = 4 * ((w >> 5) & 7) + (w & 3);
+        const float v = (n < K) ? sm.mraw[s][n * BI + kk] : 0.f;
+        uint32_t h, l;
+        split_tf32(v, h, l);
+        reinterpret_cast<uint32_t*>(sm.b[a][0])[w] = h;
+        reinterpret_cast<uint32_t*>(sm.b[a][1])[w] = l;
+      }
+      fence_proxy_async_smem();
+      tmem_wait_st();
+      tc_fence_before();
+      mbar_arrive(&sm.full_a[a]);
+      mbar_arrive(&sm.empty_x[s]);
+    }
+  } else if (warp < 12) {
+    // ------------------------------------------------------------ epilogue
+    const int quad = warp & 3;
+    const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
+    for (int tl = 0; tl < my_tiles && ok; ++tl) {
+      const int buf = tl & 1;
+      if (!mbar_wait(&sm.d_full[buf], (uint32_t)(tl >> 1) & 1u, abort_flag)) { ok = false; break; }
+      tc_fence_after();
+      const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
+      const int64_t j = (int64_t)tile * TILE_J + quad * 32 + lane;
+#pragma unroll
+      for (int c0 = 0; c0 < NPAD; c0 += 16) {
+        uint32_t v[16];
+        tmem_ld_x16(tmem + lane_base + (uint32_t)(buf * D_COLS + c0), v);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int k = c0 + c;
+          if (k < K && j < J) out[j * o_r + (int64_t)k * o_k] = __uint_as_float(v[c]);
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&sm.d_empty[buf]);
+    }
+  }
+  if (!ok) {
+    *abort_flag = 1;
+    set_error(st, RHOSVD_ETIMEOUT);
+  }
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------- host side
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn_ttm() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+bool tmap2d(CUtensorMap* m, const float* base, uint64_t inner, uint64_t outer, uint64_t outer_stride,
+            uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle sw) {
+  EncodeTiledFn fn = encode_fn_ttm();
+  if (fn == nullptr) return false;
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {outer_stride * sizeof(float)};
+  cuuint32_t box[2] = {box_inner, box_outer};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int sms_ttm() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (n <= 0) n = 148;
+  }
+  return n;
+}
+
+template <int NPAD>
+cudaError_t launch_npad(const CUtensorMap& tmX, const CUtensorMap& tmM, int I, int64_t J, int K, const OView& out,
+                        const DevStatus* skip, DevStatus* st, cudaStream_t stream) {
+  const size_t smem = sizeof(TtmSmem) + 1024;
+  cudaError_t e = allow_dynamic_smem((const void*)tc_ttm_m1_kernel<NPAD>, smem);
+  if (e != cudaSuccess) return e;
+  const int ntiles = (int)((J + TILE_J - 1) / TILE_J);
+  const int grid = std::min(ntiles, sms_ttm());
+  tc_ttm_m1_kernel<NPAD><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmM, I, J, K, out.p, out.o_k, out.o_r, skip,
+                                                                st);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_ttm_supported(const View& x, int64_t m_i, int64_t m_k, int K, const OView& out) {
+  if (x.L != 1 || x.s_i != 1 || x.s_r != x.I) return false;   // X(i, j) = X[i + I*j]
+  if (m_i != 1 || m_k < x.I || m_k % 4 != 0) return false;     // M column-major, ld multiple of 4
+  if (K < 1 || K > 64 || x.I % 4 != 0 || x.I > (int64_t(1) << 30) || x.Rt < TILE_J) return false;
+  (void)out;
+  return encode_fn_ttm() != nullptr;
+}
+
+cudaError_t launch_tc_ttm(const View& x, const float* Mp, int64_t m_k, int K, const OView& out,
+                          const DevStatus* skip, DevStatus* st, cudaStream_t stream) {
+  if ((reinterpret_cast<uintptr_t>(x.p) & 15) || (reinterpret_cast<uintptr_t>(Mp) & 15)) return cudaErrorNotSupported;
+  const int64_t I = x.I, J = x.Rt;
+  CUtensorMap tmX, tmM;
+  if (!tmap2d(&tmX, x.p, (uint64_t)I, (uint64_t)J, (uint64_t)I, BI, TILE_J, CU_TENSOR_MAP_SWIZZLE_128B))
+    return cudaErrorNotSupported;
+  if (!tmap2d(&tmM, Mp, (uint64_t)I, (uint64_t)K, (uint64_t)m_k, BI, 64, CU_TENSOR_MAP_SWIZZLE_NONE))
+    return cudaErrorNotSupported;
+  const int npad = ((K + 15) / 16) * 16;
+  switch (npad) {
+    case 16: return launch_npad<16>(tmX, tmM, (int)I, J, K, out, skip, st, stream);
+    case 32: return launch_npad<32>(tmX, tmM, (int)I, J, K, out, skip, st, stream);
+    case 48: return launch_npad<48>(tmX, tmM, (int)I, J, K, out, skip, st, stream);
+    default: return launch_npad<64>(tmX, tmM, (int)I, J, K, out, skip, st, stream);
+  }
+}
+
+}  // namespace rhosvd

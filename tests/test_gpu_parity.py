@@ -147,6 +147,37 @@ def test_tc_sketch_is_deterministic():
 
 # ------------------------------------------------------------------ TTM / core projection
 
+# Mode-1 n-mode products with I % 4 == 0, K <= 64 and at least 128 columns
+# run on the tcgen05 TTM kernel: partial last 32-wide stage (I % 32 != 0),
+# I < 32, partial last 128-row tile, every N padding.
+TC_TTM_CASES = [((512, 64, 64), 42), ((100, 48, 50), 16), ((256, 33, 17), 64), ((36, 128, 9), 5),
+                ((20, 300, 7), 20), ((128, 40, 40), 33)]
+
+
+@pytest.mark.parametrize("dims,K", TC_TTM_CASES)
+def test_tc_ttm_mode1_parity(dims, K):
+    x = random_tensor(dims, 31)
+    x32 = f32(x)
+    q = np.random.default_rng(32).standard_normal((dims[0], K)).astype(np.float32)
+    G = host(R().rhosvd_core(dev(x), dims, [torch.from_numpy(q).cuda()] + [None] * (len(dims) - 1)))
+    want = T.ttm(x32, q.astype(np.float64).T, 0)
+    bound = T.ttm(np.abs(x32), np.abs(q.astype(np.float64)).T, 0)
+    assert_close_abs(G, want, bound)
+
+
+def test_tc_ttm_power_step_z_layout():
+    """rhosvd_power's Z = X_(1)^T Q is written in the J x K layout by the same kernel."""
+    dims = (512, 40, 30)
+    x = lowrank_tensor(dims, (10, 10, 10), 33, noise=0.05)
+    a = T.unfold(f32(x), 0)
+    q = A.orth(np.random.default_rng(34).standard_normal((512, 42)))
+    Y = host(R().rhosvd_power(dev(x), dims, 0, torch.from_numpy(q.astype(np.float32)).cuda()))
+    want = a @ A.orth(a.T @ q.astype(np.float32).astype(np.float64))
+    assert M.max_principal_sine(Y, want) <= 1e-4
+    np.testing.assert_allclose(np.linalg.svd(Y, compute_uv=False), np.linalg.svd(want, compute_uv=False),
+                               rtol=1e-4)
+
+
 @pytest.mark.parametrize("dims,K", [((67, 45, 83), (7, 45, 12)), ((9, 10, 11, 12), (3, 4, 5, 6)),
                                     ((200, 3, 150), (70, 3, 65))])
 def test_core_projection_parity(dims, K):
