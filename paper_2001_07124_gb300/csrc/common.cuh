@@ -63,6 +63,54 @@ __device__ __forceinline__ void df64_fma(df64& acc, float a, float b) {
 
 __device__ __forceinline__ double df64_to_double(df64 v) { return (double)v.hi + (double)v.lo; }
 
+// Double-word ("double-float") arithmetic on FP32 pairs, hi + lo with
+// |lo| <= ulp(hi)/2: the FMA-based algorithms of Joldes, Muller, Popescu,
+// "Tight and rigorous error bounds for basic building blocks of double-word
+// arithmetic", ACM TOMS 2017 (relative errors ~2^-44..2^-46).  Used where a
+// short sequential chain needs more than FP32 precision and GB300's narrow
+// FP64 pipe would dominate the latency.
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {   // |a| >= |b|
+  s = a + b;
+  e = b - (s - a);
+}
+__device__ __forceinline__ df64 dw_from_double(double v) {
+  const float hi = __double2float_rn(v);
+  return df64{hi, __double2float_rn(v - (double)hi)};
+}
+// DW + DW, the accurate algorithm (two TwoSums and two renormalisations)
+__device__ __forceinline__ df64 dw_add(df64 x, df64 y) {
+  float s, t, e, f;
+  two_sum(x.hi, y.hi, s, t);
+  two_sum(x.lo, y.lo, e, f);
+  t += e;
+  fast_two_sum(s, t, s, t);
+  t += f;
+  fast_two_sum(s, t, s, t);
+  return df64{s, t};
+}
+__device__ __forceinline__ df64 dw_neg(df64 x) { return df64{-x.hi, -x.lo}; }
+// DW x DW with FMA
+__device__ __forceinline__ df64 dw_mul(df64 x, df64 y) {
+  const float ch = x.hi * y.hi;
+  float cl = fmaf(x.hi, y.hi, -ch);
+  const float tl = fmaf(x.lo, y.hi, x.hi * y.lo);
+  cl += tl;
+  float s, e;
+  fast_two_sum(ch, cl, s, e);
+  return df64{s, e};
+}
+// 1/sqrt(d) for a positive double-word d: the FP32 estimate plus one Newton
+// correction r = r0 + r0 (1 - d r0^2) / 2 evaluated in double-word arithmetic.
+__device__ __forceinline__ df64 dw_rsqrt(df64 d) {
+  const float r0 = rsqrtf(d.hi);
+  const df64 r = df64{r0, 0.f};
+  const df64 q = dw_mul(dw_mul(d, r), r);
+  const df64 e = dw_add(df64{1.f, 0.f}, dw_neg(q));
+  float s, t;
+  fast_two_sum(r0, 0.5f * r0 * e.hi, s, t);
+  return df64{s, t};
+}
+
 // 1/sqrt(d) in FP64: the FP32 hardware estimate refined by two Newton steps
 // y <- y (3 - d y^2) / 2 (each step doubles the correct bits: ~2^-22 -> 2^-44
 // -> full precision).  Callers pass pivots of Gram matrices scaled to max

@@ -18,6 +18,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "small_la.cuh"
 
 namespace rhosvd {
 
@@ -25,92 +26,55 @@ namespace {
 
 constexpr int CH_THREADS = 256;
 
-// Right-looking Cholesky G/g = L' L'^T of the Gram scaled by g = max diag, on a
-// 16 x 16 thread grid: step j writes column j of L' = A(:,j)/sqrt(d) to Lout
-// and updates the trailing lower triangle with the unscaled column,
-// A(i,k) -= A(i,j) A(k,j) / d.  The GPU's FP64 pipe is narrow, so the per-step
-// scalar 1/sqrt(d) is computed once, by the thread that finalises the next
-// pivot (it updates A(j+1,j+1) last in step j), and broadcast through shared
-// memory; each step needs one barrier.  Lout receives L = sqrt(g) L'
-// (K x K column-major, zero above the diagonal).  Returns false (uniformly)
-// when a scaled pivot is at or below tol.
-template <typename T>
-__device__ bool chol_body(const double* __restrict__ G, int K, float* __restrict__ Lout, T* A, double g,
-                          double tol) {
-  __shared__ T rs_s[RHOSVD_MAX_K];
-  __shared__ int bad;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const T ginv = (T)(1.0 / g);
-  for (int c = ty; c < K; c += 16)
-    for (int r = tx; r < K; r += 16) A[r + c * K] = (r >= c) ? (T)G[r + c * K] * ginv : (T)0;
-  __syncthreads();
-  if (tid == 0) {
-    const T d0 = A[0];
-    bad = !(d0 > (T)tol);
-    rs_s[0] = bad ? (T)0 : rsqrt_newton(d0);
-  }
-  __syncthreads();
-  const float sg = (float)sqrt(g);
-  for (int j = 0; j < K; ++j) {
-    if (bad) return false;                  // uniform: set before the last barrier
-    const T rs = rs_s[j];
-    const T r2 = rs * rs;
-    for (int i = j + tid; i < K; i += CH_THREADS) Lout[i + j * K] = (float)(A[i + j * K] * rs) * sg;
-    for (int i = j + 1 + ty; i < K; i += 16) {
-      const T aij = A[i + j * K] * r2;
-      for (int k = j + 1 + tx; k <= i; k += 16) A[i + k * K] -= aij * A[k + j * K];
-    }
-    if (tid == 0 && j + 1 < K) {            // thread (0,0) owns A(j+1, j+1)
-      const T dn = A[(j + 1) + (j + 1) * K];
-      if (!(dn > (T)tol)) bad = 1;
-      else rs_s[j + 1] = rsqrt_newton(dn);
-    }
-    __syncthreads();
-  }
-  for (int c = ty; c < K; c += 16)
-    for (int r = tx; r < c; r += 16) Lout[r + c * K] = 0.f;
-  return true;
-}
-
 __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
-// Cholesky factor L (G = L L^T) of one CholeskyQR pass.  The first pass's Gram
-// can have condition ~1e12 and is factored in FP64; the second pass's in FP32
-// when every off-diagonal cosine G_ij / sqrt(G_ii G_jj) is at most 1e-2 (then
-// cond(G) < 1.5 and FP32 adds O(K u) to the orthogonality of Q2), in FP64
-// otherwise.  Pivot thresholds (relative to max diag): K * 1e-15 for the first
-// pass (numerically non-positive), 1e-4 for the second (cond(Q1) > 100).
+// Cholesky factor L (G = L L^T) of one CholeskyQR pass.  G is first copied to
+// shared memory with independent loads (one memory latency, not one per loop
+// trip).  The first pass's Gram can have condition ~1e12 and is factored in
+// double-word arithmetic; the second pass's in FP32 when every off-diagonal
+// cosine G_ij / sqrt(G_ii G_jj) is at most 1e-2 (then cond(G) < 1.5 and FP32
+// adds O(K u) to the orthogonality of Q2), in double-word otherwise.  Pivot
+// thresholds relative to max diag: K * 1e-14 for the first pass (numerically
+// non-positive at double-word precision), 1e-4 for the second (cond(Q1) > 100).
 __global__ void __launch_bounds__(CH_THREADS)
 chol_kernel(const double* __restrict__ G, int K, float* __restrict__ Lout, int pass, int fail_code,
             DevStatus* st) {
   if (pass == 1 && st->orth_fail) return;
   extern __shared__ __align__(16) unsigned char ch_smem[];
-  __shared__ int nonfinite;
+  double* Gs = reinterpret_cast<double*>(ch_smem);                 // K x K FP64
+  unsigned char* work = ch_smem + (size_t)K * K * sizeof(double);  // FP32 factorisation storage
+  __shared__ int nonfinite, flag;
   __shared__ float wmax[CH_THREADS / 32];
   __shared__ double maxdiag;
+  __shared__ df64 rs_dw[RHOSVD_MAX_K];
+  __shared__ float rs_f[RHOSVD_MAX_K];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) nonfinite = 0;
+  __syncthreads();
+  for (int e = tid; e < K * K; e += CH_THREADS) {
+    const double v = G[e];
+    Gs[e] = v;
+    if (!isfinite(v)) nonfinite = 1;
+  }
+  __syncthreads();
   if (warp == 0) {
     double m = 0.0;
-    for (int i = lane; i < K; i += 32) m = fmax(m, G[i + i * K]);
+    for (int i = lane; i < K; i += 32) m = fmax(m, Gs[i + i * K]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) maxdiag = m;
   }
-  __syncthreads();
   float cmax = 0.f;                          // largest off-diagonal cosine, in FP32
   for (int e = tid; e < K * K; e += CH_THREADS) {
-    const double v = G[e];
-    if (!isfinite(v)) nonfinite = 1;
     const int c = e / K, r = e - c * K;
     if (r > c) {
-      const float grr = (float)G[r + r * K], gcc = (float)G[c + c * K];
-      const float cs = (grr > 0.f && gcc > 0.f) ? fabsf((float)v) * rsqrtf(grr) * rsqrtf(gcc) : 1.f;
-      cmax = fmaxf(cmax, fminf(cs, 1.f));
+      const float grr = (float)Gs[r + r * K], gcc = (float)Gs[c + c * K];
+      const float cs = (grr > 0.f && gcc > 0.f) ? fabsf((float)Gs[e]) * rsqrtf(grr) * rsqrtf(gcc) : 1.f;
+      cmax = fminf(fmaxf(cmax, cs), 1.f);
     }
   }
   cmax = warp_max(cmax);
@@ -121,9 +85,14 @@ chol_kernel(const double* __restrict__ G, int K, float* __restrict__ Lout, int p
   for (int w = 0; w < CH_THREADS / 32; ++w) allmax = fmaxf(allmax, wmax[w]);
   bool ok = !nonfinite && maxdiag > 0.0 && isfinite(maxdiag);
   if (ok) {
-    const double tol = (pass == 0) ? (double)K * 1e-15 : 1e-4;
-    if (pass == 1 && allmax <= 1e-2f) ok = chol_body<float>(G, K, Lout, reinterpret_cast<float*>(ch_smem), maxdiag, tol);
-    else ok = chol_body<double>(G, K, Lout, reinterpret_cast<double*>(ch_smem), maxdiag, tol);
+    const int e = 2 * (ilogb(maxdiag) / 2);  // even power of two: exact scaling and unscaling
+    const double tol = ((pass == 0) ? (double)K * 1e-14 : 1e-4) * ldexp(maxdiag, -e);
+    if (pass == 1 && allmax <= 1e-2f)
+      ok = chol_grid<F32Ops>(Gs, K, e, tol, false, Lout, reinterpret_cast<float*>(work), rs_f, &flag);
+    else
+      // the double-word factor overwrites Gs in place: same element size, and each
+      // element is read and rewritten by the same thread
+      ok = chol_grid<DWOps>(Gs, K, e, tol, false, Lout, reinterpret_cast<df64*>(Gs), rs_dw, &flag);
   }
   if (!ok) {
     if (tid == 0) {
@@ -314,9 +283,9 @@ householder_kernel(float* A, int64_t m, int K, int64_t ld, DevStatus* st, int fo
 
 cudaError_t launch_chol(const double* G, int K, float* L, int pass, int fail_code, DevStatus* st,
                         cudaStream_t stream) {
-  const size_t smem = (size_t)K * K * sizeof(double);
+  const size_t smem = (size_t)K * K * (sizeof(double) + sizeof(float));
   cudaError_t e = allow_dynamic_smem((const void*)chol_kernel,
-                                     (size_t)RHOSVD_MAX_K * RHOSVD_MAX_K * sizeof(double));
+                                     (size_t)RHOSVD_MAX_K * RHOSVD_MAX_K * (sizeof(double) + sizeof(float)));
   if (e != cudaSuccess) return e;
   chol_kernel<<<1, CH_THREADS, smem, stream>>>(G, K, L, pass, fail_code, st);
   return cudaGetLastError();
