@@ -112,16 +112,31 @@ void op_ttm(Ctx& c, const View& x, const float* M, int64_t m_i, int64_t m_k, int
   if (!c.dry) c.check(launch_ttm_auto(x, M, m_i, m_k, K, out, skip, c.st, c.s));
 }
 
-// CholeskyQR2 with device-side Householder fallback, in place on Y (m x K, ld)
-void op_orth(Ctx& c, float* Y, int64_t m, int K, int64_t ld) {
+// CholeskyQR with device-side Householder fallback, in place on Y (m x K, ld).
+// passes = 2 is CholeskyQR2 (Q orthonormal to FP32 accuracy); passes = 1 is
+// used for the intermediate bases of the power iteration (Alg. 1 step 2),
+// where only range(Q) matters: a second pass would re-orthonormalise Q1 within
+// range(Q1) without changing it, and Q1 from the FP64-accurate first pass is
+// well conditioned whenever that pass succeeds.  The apply Y R^-1 runs as a
+// tensor-core GEMM with the explicit R^-1 when the tall matrix allows it,
+// otherwise as a row-wise triangular solve.
+void op_orth(Ctx& c, float* Y, int64_t m, int K, int64_t ld, int passes = 2) {
   Scope sc(c);
   double* G = c.take<double>((size_t)K * K);
   float* L = c.take<float>((size_t)K * K);
-  for (int pass = 0; pass < 2; ++pass) {
+  const int ldm = (K + 3) & ~3;
+  float* Minv = c.take<float>((size_t)ldm * K);
+  const View yv = matrix_view(Y, m, K, ld);
+  const bool gemm = c.st != nullptr && tc_ttm_supported(yv, 1, ldm, K, OView{Y, ld, 0});
+  for (int pass = 0; pass < passes; ++pass) {
     op_gram_matrix(c, Y, m, K, ld, G, pass == 0);
     c.launches += 2;
-    if (!c.dry) c.check(launch_chol(G, K, L, pass, 0, c.st, c.s));
-    if (!c.dry) c.check(launch_trsm_rows(Y, m, K, ld, L, 0, c.st, c.s));
+    if (!c.dry) c.check(launch_chol(G, K, L, gemm ? Minv : nullptr, ldm, pass, 0, c.st, c.s));
+    if (gemm) {
+      if (!c.dry) c.check(launch_tc_ttm(yv, Minv, ldm, K, OView{Y, ld, 0}, c.st, c.st, c.s));
+    } else {
+      if (!c.dry) c.check(launch_trsm_rows(Y, m, K, ld, L, 0, c.st, c.s));
+    }
   }
   c.launches += 1;
   if (!c.dry) c.check(launch_householder(Y, m, K, ld, c.st, false, c.s));
@@ -163,13 +178,13 @@ void alg1_mode(Ctx& c, const float* x, const Geom& g, int n, int K, int R, int q
     W = Om;
   }
   op_sketch(c, xv, WView{W, L, J}, K, Yb, I);            // Y = X_(n) Omega
-  op_orth(c, Yb, I, K, I);                               // Q = orth(Y)
+  op_orth(c, Yb, I, K, I, q > 0 ? 1 : 2);               // Q = orth(Y)
   const OView zo{Zb, J, L};                              // Z(j,k) at j + k*J
   for (int it = 0; it < q; ++it) {
     op_ttm(c, xv, Yb, 1, I, K, zo);                      // Z = X_(n)^T Q
-    op_orth(c, Zb, J, K, J);                             // Z = orth(Z)
+    op_orth(c, Zb, J, K, J, 1);                          // Z = orth(Z)
     op_sketch(c, xv, WView{Zb, L, J}, K, Yb, I);         // Y = X_(n) Z
-    op_orth(c, Yb, I, K, I);                             // Q = orth(Y)
+    op_orth(c, Yb, I, K, I, it + 1 < q ? 1 : 2);         // Q = orth(Y)
   }
   op_ttm(c, xv, Yb, 1, I, K, zo);                        // B^T = X_(n)^T Q
   op_truncate(c, Zb, J, K, J, R, Ub);                    // Ubar_R of B
@@ -466,7 +481,7 @@ void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const
     }
     op_gram_matrix(c, A, S, K, S, Gd);
     c.launches += 2;
-    if (!c.dry) c.check(launch_chol(Gd, K, Lf, 0, RHOSVD_EBREAKDOWN, c.st, c.s));
+    if (!c.dry) c.check(launch_chol(Gd, K, Lf, nullptr, 0, 0, RHOSVD_EBREAKDOWN, c.st, c.s));
     if (!c.dry) c.check(launch_trsm_rows(A, S, K, S, Lf, 1, c.st, c.s));   // A (A^T A)^-1, in place
     float* dst = Cb[ping];
     ttm_mode(c, cur, t, n, A, 1, S, K, dst);   // M(s, k) = P^T(s, k)
@@ -543,7 +558,8 @@ size_t primitive_ws(const Geom& g, int Kmax) {
     SketchPlan pz = plan_sketch(Kmax, Kmax, g.J(n));
     extra = std::max(extra, sketch_partial_floats(pz, Kmax, Kmax) * sizeof(double));
   }
-  extra += 4 * (size_t)RHOSVD_MAX_K * RHOSVD_MAX_K * sizeof(double) + 8 * ALIGN;
+  extra += 4 * (size_t)RHOSVD_MAX_K * RHOSVD_MAX_K * sizeof(double) +
+           (size_t)RHOSVD_MAX_K * RHOSVD_MAX_K * sizeof(float) + 8 * ALIGN;
   return fixed + extra;
 }
 

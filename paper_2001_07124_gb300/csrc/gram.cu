@@ -12,8 +12,10 @@
 //    with TwoSum into a double-float accumulator (Ogita, Rump, Oishi 2005,
 //    "Accurate sum and dot product"), so the Gram is FP64-accurate even when
 //    cond(A) is ~1e6 (first CholeskyQR pass).
-//  * CHUNKED: products are summed in FP32 over one 64-row tile and the tile sums
+//  * CHUNKED: products are summed in FP32 over four 64-row tiles and those sums
 //    are added in FP64; enough when A is close to orthonormal (second pass).
+//    Register-blocked: a thread owns a 4 x 4 block of column pairs and reads
+//    the tile as float4 row quads, 2 shared loads per 16 FMAs per row.
 #include <algorithm>
 
 #include "common.cuh"
@@ -87,6 +89,139 @@ gram_kernel(const float* __restrict__ A, int64_t m, int K, int64_t ld, int64_t r
   }
 }
 
+// ---------------------------------------------------------------- chunked, register-blocked
+constexpr int GF_LD = GR_TILE + 4;               // column pitch of the tile (== 4 mod 32)
+constexpr int GF_FLUSH = 4;                      // tiles summed in FP32 before the FP64 add
+
+__device__ __forceinline__ void pair_blocks(int p, int& bi, int& bj) {   // p -> (bi <= bj), column-major upper
+  int b = (int)((sqrtf(8.f * (float)p + 1.f) - 1.f) * 0.5f);
+  while (b > 0 && b * (b + 1) / 2 > p) --b;
+  while ((b + 1) * (b + 2) / 2 <= p) ++b;
+  bi = p - b * (b + 1) / 2;
+  bj = b;
+}
+
+template <int PT>                                // block pairs per thread (npairs <= PT * GR_THREADS)
+__global__ void __launch_bounds__(GR_THREADS)
+gram_f32_kernel(const float* __restrict__ A, int64_t m, int K, int64_t ld, int64_t rows_per_cta,
+                double* __restrict__ part) {
+  extern __shared__ __align__(16) float gf_smem[];   // tile [4*nb][GF_LD]; later the phase partials
+  const int tid = threadIdx.x;
+  const int nb = (K + 3) / 4, npairs = nb * (nb + 1) / 2;
+  const int phases = npairs >= GR_THREADS ? 1 : GR_THREADS / npairs;
+  const int phase = npairs >= GR_THREADS ? 0 : tid / npairs;
+  const bool active = npairs >= GR_THREADS ? true : tid < phases * npairs;
+  const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r1 = min(m, r0 + rows_per_cta);
+
+  int bi[PT], bj[PT];
+  bool own[PT];
+  float acc[PT][16];
+  double dacc[PT][16];
+#pragma unroll
+  for (int t = 0; t < PT; ++t) {
+    const int p = (npairs >= GR_THREADS) ? tid + t * GR_THREADS : (t == 0 ? tid % npairs : npairs);
+    own[t] = active && p < npairs;
+    pair_blocks(own[t] ? p : 0, bi[t], bj[t]);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) { acc[t][e] = 0.f; dacc[t][e] = 0.0; }
+  }
+  int ntile = 0;
+  for (int64_t rt = r0; rt < r1; rt += GR_TILE, ++ntile) {
+    const int nrow = (r1 - rt < GR_TILE) ? (int)(r1 - rt) : GR_TILE;
+    __syncthreads();
+    for (int e = tid; e < 4 * nb * GR_TILE; e += GR_THREADS) {
+      const int c = e / GR_TILE, r = e % GR_TILE;
+      gf_smem[c * GF_LD + r] = (r < nrow && c < K) ? __ldg(A + (rt + r) + (int64_t)c * ld) : 0.f;
+    }
+    __syncthreads();
+    for (int q = phase; q < GR_TILE / 4; q += phases) {
+#pragma unroll
+      for (int t = 0; t < PT; ++t) {
+        if (!own[t]) continue;
+        float4 a[4], b[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a[u] = *reinterpret_cast<const float4*>(gf_smem + (4 * bi[t] + u) * GF_LD + 4 * q);
+          b[u] = *reinterpret_cast<const float4*>(gf_smem + (4 * bj[t] + u) * GF_LD + 4 * q);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            float x = acc[t][4 * u + v];
+            x = fmaf(a[u].x, b[v].x, x);
+            x = fmaf(a[u].y, b[v].y, x);
+            x = fmaf(a[u].z, b[v].z, x);
+            x = fmaf(a[u].w, b[v].w, x);
+            acc[t][4 * u + v] = x;
+          }
+      }
+    }
+    if ((ntile + 1) % GF_FLUSH == 0) {
+#pragma unroll
+      for (int t = 0; t < PT; ++t)
+#pragma unroll
+        for (int e = 0; e < 16; ++e) { dacc[t][e] += (double)acc[t][e]; acc[t][e] = 0.f; }
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < PT; ++t)
+#pragma unroll
+    for (int e = 0; e < 16; ++e) dacc[t][e] += (double)acc[t][e];
+  double* dst = part + (int64_t)blockIdx.x * K * K;
+  if (phases == 1) {
+#pragma unroll
+    for (int t = 0; t < PT; ++t) {
+      if (!own[t]) continue;
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int a = 4 * bi[t] + e / 4, b = 4 * bj[t] + e % 4;
+        if (a < K && b < K) { dst[a + b * K] = dacc[t][e]; dst[b + a * K] = dacc[t][e]; }
+      }
+    }
+    return;
+  }
+  // several row phases per pair block: sum them in a fixed order through shared memory
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(gf_smem);   // [phase][pair][16]
+  if (own[0])
+#pragma unroll
+    for (int e = 0; e < 16; ++e) red[((size_t)phase * npairs + tid % npairs) * 16 + e] = dacc[0][e];
+  __syncthreads();
+  for (int w = tid; w < npairs * 16; w += GR_THREADS) {
+    const int p = w / 16, e = w % 16;
+    double v = 0.0;
+    for (int ph = 0; ph < phases; ++ph) v += red[((size_t)ph * npairs + p) * 16 + e];
+    int pi, pj;
+    pair_blocks(p, pi, pj);
+    const int a = 4 * pi + e / 4, b = 4 * pj + e % 4;
+    if (a < K && b < K) { dst[a + b * K] = v; dst[b + a * K] = v; }
+  }
+}
+
+cudaError_t launch_gram_f32(const float* A, int64_t m, int K, int64_t ld, double* G, double* part, int ctas,
+                            int64_t rows, cudaStream_t st) {
+  const int nb = (K + 3) / 4, npairs = nb * (nb + 1) / 2;
+  const int phases = npairs >= GR_THREADS ? 1 : GR_THREADS / npairs;
+  const size_t tile = (size_t)4 * nb * GF_LD * sizeof(float);
+  const size_t red = phases > 1 ? (size_t)phases * npairs * 16 * sizeof(double) : 0;   // <= 32 KB
+  const size_t smem = tile > red ? tile : red;
+  cudaError_t e;
+  if (npairs <= GR_THREADS) {
+    if ((e = allow_dynamic_smem((const void*)gram_f32_kernel<1>, 64 * 1024)) != cudaSuccess) return e;
+    gram_f32_kernel<1><<<ctas, GR_THREADS, smem, st>>>(A, m, K, ld, rows, part);
+  } else if (npairs <= 2 * GR_THREADS) {
+    if ((e = allow_dynamic_smem((const void*)gram_f32_kernel<2>, 64 * 1024)) != cudaSuccess) return e;
+    gram_f32_kernel<2><<<ctas, GR_THREADS, smem, st>>>(A, m, K, ld, rows, part);
+  } else {
+    if ((e = allow_dynamic_smem((const void*)gram_f32_kernel<3>, 64 * 1024)) != cudaSuccess) return e;
+    gram_f32_kernel<3><<<ctas, GR_THREADS, smem, st>>>(A, m, K, ld, rows, part);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  return launch_reduce_d(part, ctas, (int64_t)K * K, G, st);
+}
+
 template <bool EXACT>
 cudaError_t launch_gram_t(const float* A, int64_t m, int K, int64_t ld, double* G, double* part, int ctas,
                           int64_t rows, cudaStream_t st) {
@@ -119,7 +254,7 @@ cudaError_t launch_gram(const float* A, int64_t m, int K, int64_t ld, double* G,
                         cudaStream_t st) {
   GramPlan pl = plan_gram(m, K);
   return exact ? launch_gram_t<true>(A, m, K, ld, G, part, pl.ctas, pl.rows_per_cta, st)
-               : launch_gram_t<false>(A, m, K, ld, G, part, pl.ctas, pl.rows_per_cta, st);
+               : launch_gram_f32(A, m, K, ld, G, part, pl.ctas, pl.rows_per_cta, st);
 }
 
 }  // namespace rhosvd

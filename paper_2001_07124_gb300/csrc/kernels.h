@@ -106,9 +106,10 @@ cudaError_t launch_omega(uint64_t seed, uint32_t stream_id, int64_t rows, int co
 // Cholesky factor L (K x K, FP32, column-major lower, zero above) of the FP64
 // Gram G = L L^T.  pass 0 writes orth_fail; pass 1 runs only if orth_fail is
 // clear.  Breakdown sets orth_fail and, if fail_code is non-zero, records
-// fail_code as the device error.
-cudaError_t launch_chol(const double* G, int K, float* L, int pass, int fail_code, DevStatus* st,
-                        cudaStream_t stream);
+// fail_code as the device error.  Minv (nullable) receives R^-1 = L^-T (K x K,
+// column-major, leading dimension ldm) for the GEMM form of the apply.
+cudaError_t launch_chol(const double* G, int K, float* L, float* Minv, int ldm, int pass, int fail_code,
+                        DevStatus* st, cudaStream_t stream);
 // Row-parallel triangular solves with L: mode 0 replaces every row y^T of Y
 // (m x K, ld) by y^T L^-T (= Y R^-1 with R = L^T); mode 1 by y^T (L L^T)^-1.
 // Skipped when skip is non-NULL and orth_fail is set.

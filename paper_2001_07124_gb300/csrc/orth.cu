@@ -40,9 +40,14 @@ __device__ __forceinline__ float warp_max(float v) {
 // adds O(K u) to the orthogonality of Q2), in double-word otherwise.  Pivot
 // thresholds relative to max diag: K * 1e-14 for the first pass (numerically
 // non-positive at double-word precision), 1e-4 for the second (cond(Q1) > 100).
+//
+// With Minv != nullptr the kernel also writes R^-1 = L^-T (FP32, K x K,
+// column-major, leading dimension ldm), so that the apply Q = Y R^-1 is a
+// plain GEMM: column c of L^-1 by forward substitution (one thread per
+// column), from the same FP32 factor the row-wise solve would use.
 __global__ void __launch_bounds__(CH_THREADS)
-chol_kernel(const double* __restrict__ G, int K, float* __restrict__ Lout, int pass, int fail_code,
-            DevStatus* st) {
+chol_kernel(const double* __restrict__ G, int K, float* __restrict__ Lout, float* __restrict__ Minv, int ldm,
+            int pass, int fail_code, DevStatus* st) {
   if (pass == 1 && st->orth_fail) return;
   extern __shared__ __align__(16) unsigned char ch_smem[];
   double* Gs = reinterpret_cast<double*>(ch_smem);                 // K x K FP64
@@ -103,6 +108,29 @@ chol_kernel(const double* __restrict__ G, int K, float* __restrict__ Lout, int p
     return;
   }
   if (pass == 0 && tid == 0) st->orth_fail = 0;
+  if (Minv == nullptr) return;
+  // L (FP32) was written to Lout by this block; stage it and L^-1 over the Gram storage
+  float* Ls = reinterpret_cast<float*>(ch_smem);     // K x K, column-major
+  float* Li = Ls + K * K;                            // K x K: Li[i + c*K] = (L^-1)(i, c)
+  __syncthreads();
+  for (int e = tid; e < K * K; e += CH_THREADS) Ls[e] = Lout[e];
+  __syncthreads();
+  if (tid < K) {
+    const int c = tid;
+    float* x = Li + c * K;
+    for (int i = 0; i < c; ++i) x[i] = 0.f;
+    x[c] = 1.f / Ls[c + c * K];
+    for (int i = c + 1; i < K; ++i) {
+      float s = 0.f;
+      for (int k = c; k < i; ++k) s = fmaf(Ls[i + k * K], x[k], s);
+      x[i] = -s / Ls[i + i * K];
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < K * K; e += CH_THREADS) {     // Minv(i, c) = (L^-1)(c, i)
+    const int c = e / K, i = e - c * K;
+    Minv[i + (int64_t)c * ldm] = Li[c + i * K];
+  }
 }
 
 // Row-parallel triangular solves with the Cholesky factor L (K x K, lower):
@@ -281,13 +309,13 @@ householder_kernel(float* A, int64_t m, int K, int64_t ld, DevStatus* st, int fo
 
 }  // namespace
 
-cudaError_t launch_chol(const double* G, int K, float* L, int pass, int fail_code, DevStatus* st,
-                        cudaStream_t stream) {
+cudaError_t launch_chol(const double* G, int K, float* L, float* Minv, int ldm, int pass, int fail_code,
+                        DevStatus* st, cudaStream_t stream) {
   const size_t smem = (size_t)K * K * (sizeof(double) + sizeof(float));
   cudaError_t e = allow_dynamic_smem((const void*)chol_kernel,
                                      (size_t)RHOSVD_MAX_K * RHOSVD_MAX_K * (sizeof(double) + sizeof(float)));
   if (e != cudaSuccess) return e;
-  chol_kernel<<<1, CH_THREADS, smem, stream>>>(G, K, L, pass, fail_code, st);
+  chol_kernel<<<1, CH_THREADS, smem, stream>>>(G, K, L, Minv, ldm, pass, fail_code, st);
   return cudaGetLastError();
 }
 

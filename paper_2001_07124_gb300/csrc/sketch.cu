@@ -246,7 +246,7 @@ ttm_kernel(View x, const float* __restrict__ M, int64_t m_i, int64_t m_k, int K,
 
 cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes) {
   // one flag per (device, kernel) pair; a handful of kernels use this
-  constexpr int kMaxDev = 64, kMaxKern = 8;
+  constexpr int kMaxDev = 64, kMaxKern = 64;
   static const void* kernels[kMaxKern] = {nullptr};
   static bool done[kMaxKern][kMaxDev] = {{false}};
   static int nk = 0;

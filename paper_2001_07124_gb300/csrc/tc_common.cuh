@@ -64,6 +64,14 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tmap, 
       "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tmap, int x, int y, int z,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ---------------------------------------------------------------- TMEM
@@ -153,6 +161,17 @@ __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) 
   hi = h;
   lo = __float_as_uint(x - __uint_as_float(h));
 }
+
+// ---------------------------------------------------------------- host: tensor maps
+// FP32 tensor map of rank 1-3 (dims[0] contiguous; strides in elements for
+// dims 1.., each a multiple of 4), through the driver entry point so that the
+// library needs no link-time dependency on libcuda.  Out-of-range boxes are
+// zero-filled.  Returns false when the driver call is unavailable or rejects
+// the map (the caller then declines the tensor-core path).
+bool make_tmap_f32(CUtensorMap* m, const float* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                   const uint32_t* box, CUtensorMapSwizzle sw);
+// Number of SMs of the current device (cached per process).
+int device_sms();
 
 }  // namespace tc
 }  // namespace rhosvd

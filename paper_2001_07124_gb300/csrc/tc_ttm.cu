@@ -1,8 +1,17 @@
-// Tensor-core (tcgen05) n-mode product for a mode-1 layout:
-//   Out(j, k) = sum_i X[i + I*j] M(i, k),   M(i, k) = Mp[i + ldm*k]
-// i.e. Z = X_(1)^T Q (the power-iteration TTM of Alg. 1 step 2) and
-// B^T = X_(1)^T Q (the projection B = Q^T X_(1), Alg. 1 step 4), with Out
-// written at Out[j*o_r + k*o_k] (o_r = 1, o_k = J for the J x K "Z layout").
+// Tensor-core (tcgen05) n-mode product on a strided unfolding:
+//   Out(j, k) = sum_i X_(n)(i, j) M(i, k),   M(i, k) = Mp[i + ldm*k],
+//   X_(n)(i, j = l + L*r) = X[l + s_i*i + s_r*r]   (Sec. 2, Eq. for the n-mode product)
+// i.e. Z = X_(n)^T Q (the power-iteration TTM of Alg. 1 step 2), B^T = X_(n)^T Q
+// (the projection B = Q^T X_(n), Alg. 1 step 4) and, with X a tall matrix seen
+// as L = rows, Y R^-1 (the CholeskyQR apply).  Out(j, k) is written at
+// Out[l + r*o_r + k*o_k].
+//
+// Two tile layouts of the 128 j x 32 i stage:
+//   * mode 1 (L = 1, i contiguous): one 2-D box {32 i, 128 j} with 128B swizzle,
+//     each j row holding 32 consecutive i;
+//   * strided (L >= 32): a 3-D box {BL l, 32 i, 128/BL r} over [L, I, Rt]
+//     (BL = 32, 64 or 128), smem [r'][i][l'], so the 32 lanes of a warp (32
+//     consecutive j = consecutive l) read consecutive words for every i.
 //
 // Persistent, warp-specialised: each CTA takes 128-row tiles of j in turn and
 // contracts over all of i in stages of 32:
@@ -16,7 +25,9 @@
 //     accumulator, committing the tile when its last stage is issued;
 //   * warps 8-11 (epilogue): read a finished accumulator (tcgen05.ld), write
 //     the rows of Out, and hand the buffer back while the next tile computes.
-// Requirements (checked by the launcher): I % 4 == 0, ldm % 4 == 0, K <= 64.
+// Requirements (checked by tc_ttm_supported): 16-byte aligned X and M, strides
+// multiple of 4 elements, ldm % 4 == 0, K <= 64; a strided view needs
+// L % 128 == 0 or L in {32, 64} (Rt = 1: any L >= 128).
 #include <algorithm>
 
 #include "common.cuh"
@@ -43,7 +54,7 @@ constexpr int A_STAGE_COLS = 2 * BI;      // 32 hi + 32 lo columns
 constexpr int M_TILE = 64 * BI;           // floats per B tile (N <= 64)
 
 struct __align__(1024) TtmSmem {
-  float x[X_STAGES][TILE_J * BI];          // TMA tile [j][i], 128B rows, 128B swizzle
+  float x[X_STAGES][TILE_J * BI];          // TMA tile: mode 1 [j][i] swizzled, strided [r'][i][l']
   float mraw[X_STAGES][M_TILE];            // TMA tile [k][i], rows k >= K zero-filled
   float b[A_STAGES][2][M_TILE];            // hi / lo B tiles, canonical K-major layout
   uint64_t full_x[X_STAGES], empty_x[X_STAGES];
@@ -58,11 +69,11 @@ struct __align__(1024) TtmSmem {
 // K step ks starts 256 * ks bytes in.  Word w of the tile holds
 // n = 8 (w >> 8) + ((w >> 2) & 7), kk = 4 ((w >> 5) & 7) + (w & 3).
 
-template <int NPAD>
+template <int NPAD, bool M1>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
-tc_ttm_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmM, int I,
-                 int64_t J, int K, float* __restrict__ out, int64_t o_k, int64_t o_r,
-                 const DevStatus* skip, DevStatus* st) {
+tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmM, int I,
+              int64_t L, int64_t J, int bl_bits, int K, float* __restrict__ out, int64_t o_k, int64_t o_r,
+              const DevStatus* skip, DevStatus* st) {
   if (skip != nullptr && skip->orth_fail) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TtmSmem& sm = *reinterpret_cast<TtmSmem*>(
@@ -112,7 +123,12 @@ tc_ttm_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
         const int tile = (int)blockIdx.x + (g / nst) * (int)gridDim.x;
         const int ib = (g % nst) * BI;
         mbar_arrive_expect_tx(&sm.full_x[s], bytes);
-        tma_load_2d(sm.x[s], &tmX, ib, tile * TILE_J, &sm.full_x[s]);
+        if (M1) {
+          tma_load_2d(sm.x[s], &tmX, ib, tile * TILE_J, &sm.full_x[s]);
+        } else {
+          const int64_t j0 = (int64_t)tile * TILE_J, r0 = j0 / L;
+          tma_load_3d(sm.x[s], &tmX, (int)(j0 - r0 * L), ib, (int)r0, &sm.full_x[s]);
+        }
         tma_load_2d(sm.mraw[s], &tmM, ib, 0, &sm.full_x[s]);
       }
     }
@@ -153,16 +169,24 @@ tc_ttm_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
       if (!mbar_wait(&sm.full_x[s], (uint32_t)(g / X_STAGES) & 1u, abort_flag)) { ok = false; break; }
       if (!mbar_wait(&sm.empty_a[a], ((uint32_t)(g / A_STAGES) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
       tc_fence_after();
-      // row `row` of the swizzled X tile: logical 16-byte chunk c sits at chunk c ^ (row & 7)
-      const float4* xr = reinterpret_cast<const float4*>(sm.x[s] + row * BI);
       uint32_t hi[32], lo[32];
+      if (M1) {
+        // row `row` of the swizzled X tile: logical 16-byte chunk c sits at chunk c ^ (row & 7)
+        const float4* xr = reinterpret_cast<const float4*>(sm.x[s] + row * BI);
 #pragma unroll
-      for (int c = 0; c < BI / 4; ++c) {
-        const float4 v = xr[c ^ (row & 7)];
-        split_tf32(v.x, hi[4 * c + 0], lo[4 * c + 0]);
-        split_tf32(v.y, hi[4 * c + 1], lo[4 * c + 1]);
-        split_tf32(v.z, hi[4 * c + 2], lo[4 * c + 2]);
-        split_tf32(v.w, hi[4 * c + 3], lo[4 * c + 3]);
+        for (int c = 0; c < BI / 4; ++c) {
+          const float4 v = xr[c ^ (row & 7)];
+          split_tf32(v.x, hi[4 * c + 0], lo[4 * c + 0]);
+          split_tf32(v.y, hi[4 * c + 1], lo[4 * c + 1]);
+          split_tf32(v.z, hi[4 * c + 2], lo[4 * c + 2]);
+          split_tf32(v.w, hi[4 * c + 3], lo[4 * c + 3]);
+        }
+      } else {
+        // strided tile [r'][i][l']: row = l' + BL r'
+        const int bl = 1 << bl_bits;
+        const float* xr = sm.x[s] + ((row >> bl_bits) * BI) * bl + (row & (bl - 1));
+#pragma unroll
+        for (int i = 0; i < BI; ++i) split_tf32(xr[i * bl], hi[i], lo[i]);
       }
       const uint32_t col = tmem + (uint32_t)(A_COL0 + a * A_STAGE_COLS) + lane_base;
       uint32_t h16[16], l16[16];
@@ -201,6 +225,8 @@ tc_ttm_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
       tc_fence_after();
       const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
       const int64_t j = (int64_t)tile * TILE_J + quad * 32 + lane;
+      const int64_t rj = j / L;
+      float* orow = out + (j - rj * L) + rj * o_r;
 #pragma unroll
       for (int c0 = 0; c0 < NPAD; c0 += 16) {
         uint32_t v[16];
@@ -209,7 +235,7 @@ tc_ttm_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
           const int k = c0 + c;
-          if (k < K && j < J) out[j * o_r + (int64_t)k * o_k] = __uint_as_float(v[c]);
+          if (k < K && j < J) orow[(int64_t)k * o_k] = __uint_as_float(v[c]);
         }
       }
       tc_fence_before();
@@ -229,88 +255,80 @@ tc_ttm_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
 }
 
 // ---------------------------------------------------------------- host side
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn_ttm() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
+// Tile geometry of a strided view: BL = l per tile row block, 0 if unsupported.
+int strided_bl(const View& x) {
+  if (x.L < 32) return 0;
+  if (x.Rt == 1) return x.L >= 128 ? 128 : 0;
+  if (x.L % 128 == 0) return 128;
+  return (x.L == 32 || x.L == 64) ? (int)x.L : 0;
 }
 
-bool tmap2d(CUtensorMap* m, const float* base, uint64_t inner, uint64_t outer, uint64_t outer_stride,
-            uint32_t box_inner, uint32_t box_outer, CUtensorMapSwizzle sw) {
-  EncodeTiledFn fn = encode_fn_ttm();
-  if (fn == nullptr) return false;
-  cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {outer_stride * sizeof(float)};
-  cuuint32_t box[2] = {box_inner, box_outer};
-  cuuint32_t estr[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-int sms_ttm() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
-  return n;
-}
-
-template <int NPAD>
-cudaError_t launch_npad(const CUtensorMap& tmX, const CUtensorMap& tmM, int I, int64_t J, int K, const OView& out,
-                        const DevStatus* skip, DevStatus* st, cudaStream_t stream) {
+template <int NPAD, bool M1>
+cudaError_t launch_npad(const CUtensorMap& tmX, const CUtensorMap& tmM, int I, int64_t L, int64_t J, int bl_bits,
+                        int K, const OView& out, const DevStatus* skip, DevStatus* st, cudaStream_t stream) {
   const size_t smem = sizeof(TtmSmem) + 1024;
-  cudaError_t e = allow_dynamic_smem((const void*)tc_ttm_m1_kernel<NPAD>, smem);
+  cudaError_t e = allow_dynamic_smem((const void*)tc_ttm_kernel<NPAD, M1>, smem);
   if (e != cudaSuccess) return e;
   const int ntiles = (int)((J + TILE_J - 1) / TILE_J);
-  const int grid = std::min(ntiles, sms_ttm());
-  tc_ttm_m1_kernel<NPAD><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmM, I, J, K, out.p, out.o_k, out.o_r, skip,
-                                                                st);
+  const int grid = std::min(ntiles, device_sms());
+  tc_ttm_kernel<NPAD, M1><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmM, I, L, J, bl_bits, K, out.p, out.o_k,
+                                                                out.o_r, skip, st);
   return cudaGetLastError();
+}
+
+template <bool M1>
+cudaError_t launch_m(const CUtensorMap& tmX, const CUtensorMap& tmM, int I, int64_t L, int64_t J, int bl_bits,
+                     int K, const OView& out, const DevStatus* skip, DevStatus* st, cudaStream_t stream) {
+  switch (((K + 15) / 16) * 16) {
+    case 16: return launch_npad<16, M1>(tmX, tmM, I, L, J, bl_bits, K, out, skip, st, stream);
+    case 32: return launch_npad<32, M1>(tmX, tmM, I, L, J, bl_bits, K, out, skip, st, stream);
+    case 48: return launch_npad<48, M1>(tmX, tmM, I, L, J, bl_bits, K, out, skip, st, stream);
+    default: return launch_npad<64, M1>(tmX, tmM, I, L, J, bl_bits, K, out, skip, st, stream);
+  }
 }
 
 }  // namespace
 
 bool tc_ttm_supported(const View& x, int64_t m_i, int64_t m_k, int K, const OView& out) {
-  if (x.L != 1 || x.s_i != 1 || x.s_r != x.I) return false;   // X(i, j) = X[i + I*j]
-  if (m_i != 1 || m_k < x.I || m_k % 4 != 0) return false;     // M column-major, ld multiple of 4
-  if (K < 1 || K > 64 || x.I % 4 != 0 || x.I > (int64_t(1) << 30) || x.Rt < TILE_J) return false;
   (void)out;
-  return encode_fn_ttm() != nullptr;
+  if (m_i != 1 || m_k < x.I || m_k % 4 != 0) return false;     // M column-major, ld multiple of 4
+  if (K < 1 || K > 64 || x.I < 1 || x.I > (int64_t(1) << 30)) return false;
+  const int64_t J = x.L * x.Rt;
+  if (J < TILE_J || J > (int64_t(1) << 40)) return false;
+  if (x.L == 1) return x.s_i == 1 && x.s_r == x.I && x.I % 4 == 0;   // X(i, j) = X[i + I*j]
+  if (strided_bl(x) == 0 || x.s_i % 4 != 0 || (x.Rt > 1 && x.s_r % 4 != 0)) return false;
+  return x.Rt < (int64_t(1) << 31) && x.L < (int64_t(1) << 31);
 }
 
 cudaError_t launch_tc_ttm(const View& x, const float* Mp, int64_t m_k, int K, const OView& out,
                           const DevStatus* skip, DevStatus* st, cudaStream_t stream) {
   if ((reinterpret_cast<uintptr_t>(x.p) & 15) || (reinterpret_cast<uintptr_t>(Mp) & 15)) return cudaErrorNotSupported;
-  const int64_t I = x.I, J = x.Rt;
+  const int64_t I = x.I, J = x.L * x.Rt;
   CUtensorMap tmX, tmM;
-  if (!tmap2d(&tmX, x.p, (uint64_t)I, (uint64_t)J, (uint64_t)I, BI, TILE_J, CU_TENSOR_MAP_SWIZZLE_128B))
-    return cudaErrorNotSupported;
-  if (!tmap2d(&tmM, Mp, (uint64_t)I, (uint64_t)K, (uint64_t)m_k, BI, 64, CU_TENSOR_MAP_SWIZZLE_NONE))
-    return cudaErrorNotSupported;
-  const int npad = ((K + 15) / 16) * 16;
-  switch (npad) {
-    case 16: return launch_npad<16>(tmX, tmM, (int)I, J, K, out, skip, st, stream);
-    case 32: return launch_npad<32>(tmX, tmM, (int)I, J, K, out, skip, st, stream);
-    case 48: return launch_npad<48>(tmX, tmM, (int)I, J, K, out, skip, st, stream);
-    default: return launch_npad<64>(tmX, tmM, (int)I, J, K, out, skip, st, stream);
+  {
+    const uint64_t dims[2] = {(uint64_t)I, (uint64_t)K};
+    const uint64_t strides[1] = {(uint64_t)m_k};
+    const uint32_t box[2] = {BI, 64};
+    if (!make_tmap_f32(&tmM, Mp, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE)) return cudaErrorNotSupported;
   }
+  if (x.L == 1) {
+    const uint64_t dims[2] = {(uint64_t)I, (uint64_t)J};
+    const uint64_t strides[1] = {(uint64_t)I};
+    const uint32_t box[2] = {BI, TILE_J};
+    if (!make_tmap_f32(&tmX, x.p, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorNotSupported;
+    return launch_m<true>(tmX, tmM, (int)I, 1, J, 0, K, out, skip, st, stream);
+  }
+  const int bl = strided_bl(x);
+  if (bl == 0) return cudaErrorNotSupported;
+  int bits = 0;
+  while ((1 << bits) < bl) ++bits;
+  // always rank 3 (the producer issues 3-D copies); a matrix view gets a unit r extent
+  const uint64_t dims[3] = {(uint64_t)x.L, (uint64_t)I, (uint64_t)x.Rt};
+  const uint64_t strides[2] = {(uint64_t)x.s_i, x.Rt > 1 ? (uint64_t)x.s_r : (uint64_t)x.s_i * (uint64_t)I};
+  const uint32_t box[3] = {(uint32_t)bl, BI, (uint32_t)(TILE_J / bl)};
+  const bool okmap = make_tmap_f32(&tmX, x.p, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE);
+  if (!okmap) return cudaErrorNotSupported;
+  return launch_m<false>(tmX, tmM, (int)I, x.L, J, bits, K, out, skip, st, stream);
 }
 
 }  // namespace rhosvd

@@ -165,6 +165,27 @@ def test_tc_ttm_mode1_parity(dims, K):
     assert_close_abs(G, want, bound)
 
 
+# Strided unfoldings (L >= 32) on the tcgen05 TTM kernel through 3-D TMA boxes:
+# L = 32 / 64 (several r per 128-row tile, partial last tile), L % 128 == 0,
+# L >= 128 with Rt == 1, a contraction shorter than one 32-wide stage, 4-way.
+TC_TTM_STRIDED_CASES = [((64, 96, 50), 1, 42), ((32, 48, 30), 1, 16), ((256, 40, 30), 1, 33),
+                        ((32, 32, 200), 2, 64), ((32, 40, 5), 1, 20), ((16, 8, 64, 12), 2, 24),
+                        ((128, 8, 7), 1, 5)]
+
+
+@pytest.mark.parametrize("dims,mode,K", TC_TTM_STRIDED_CASES)
+def test_tc_ttm_strided_parity(dims, mode, K):
+    x = random_tensor(dims, 35)
+    x32 = f32(x)
+    q = np.random.default_rng(36).standard_normal((dims[mode], K)).astype(np.float32)
+    qs = [None] * len(dims)
+    qs[mode] = torch.from_numpy(q).cuda()
+    G = host(R().rhosvd_core(dev(x), dims, qs))
+    want = T.ttm(x32, q.astype(np.float64).T, mode)
+    bound = T.ttm(np.abs(x32), np.abs(q.astype(np.float64)).T, mode)
+    assert_close_abs(G, want, bound)
+
+
 def test_tc_ttm_power_step_z_layout():
     """rhosvd_power's Z = X_(1)^T Q is written in the J x K layout by the same kernel."""
     dims = (512, 40, 30)
