@@ -143,12 +143,16 @@ void op_orth(Ctx& c, float* Y, int64_t m, int K, int64_t ld, int passes = 2) {
 }
 
 // Leading R eigenvectors (K x R) of the Gram of a tall matrix Bt (m x K, ld)
+// Leading dimension of the small K x R factor Ub: a multiple of 4 so that the
+// tensor-core TTMs can stream it with TMA.
+inline int ldu_of(int K) { return (K + 3) & ~3; }
+
 void op_truncate(Ctx& c, const float* Bt, int64_t m, int K, int64_t ld, int R, float* Ub) {
   Scope sc(c);
   double* G = c.take<double>((size_t)K * K);
   op_gram_matrix(c, Bt, m, K, ld, G);
   c.launches += 1;
-  if (!c.dry) c.check(launch_small_eig(G, K, R, Ub, nullptr, c.st, c.s));
+  if (!c.dry) c.check(launch_small_eig(G, K, R, Ub, ldu_of(K), nullptr, c.st, c.s));
 }
 
 void op_omega(Ctx& c, uint64_t seed, uint32_t stream_id, int64_t rows, int cols, float* out) {
@@ -161,12 +165,12 @@ void op_omega(Ctx& c, uint64_t seed, uint32_t stream_id, int64_t rows, int cols,
 struct ModeResult {
   float* Q;     // I x K orthonormal (ld I)
   float* Bt;    // J x K: Bt(j, k) = (Q^T X_(n))(k, j)   (Z layout, ld J)
-  float* Ub;    // K x R leading eigenvectors of B B^T
+  float* Ub;    // K x R leading eigenvectors of B B^T (ld ldu_of(K))
 };
 
 // Steps 1-5 of Alg. 1 on the mode-n unfolding of the tensor at x (geometry g):
 // sketch, orth, q power iterations, projection B, truncation of B B^T.
-// Buffers Yb (I x K), Zb (J x K), Om (J x K, unless explicit) and Ub (K x R)
+// Buffers Yb (I x K), Zb (J x K), Om (J x K, unless explicit) and Ub (K x R, ld ldu_of(K))
 // belong to the caller.
 void alg1_mode(Ctx& c, const float* x, const Geom& g, int n, int K, int R, int q, uint64_t seed,
                const float* omega_explicit, float* Yb, float* Zb, float* Om, float* Ub) {
@@ -192,20 +196,15 @@ void alg1_mode(Ctx& c, const float* x, const Geom& g, int n, int K, int R, int q
 
 // U (I x R) = Q Ub
 void lift_factor(Ctx& c, const float* Q, int64_t I, int K, const float* Ub, int R, float* U) {
-  op_ttm(c, matrix_view(Q, I, K, I), Ub, 1, K, R, OView{U, I, 0});
+  op_ttm(c, matrix_view(Q, I, K, I), Ub, 1, ldu_of(K), R, OView{U, I, 0});
 }
 
-// S_new[l, a, r] = sum_k Ub(k, a) Bt(l + L r, k): the shortcut S_(n) = Ubar_R^T B
+// S_new[l, a, r] = sum_k Ub(k, a) Bt(l + L r, k): the shortcut S_(n) = Ubar_R^T B.
+// Bt is read as a flat J x K matrix (a tall GEMM); the output rows j = l + L r
+// are scattered into the mode-n layout of S_new.
 void refold_core(Ctx& c, const float* Bt, const Geom& g, int n, int K, const float* Ub, int R, float* Snew) {
   const int64_t L = g.L(n), J = g.J(n);
-  View bv;
-  bv.p = Bt;
-  bv.L = L;
-  bv.I = K;
-  bv.Rt = g.Rt(n);
-  bv.s_i = J;
-  bv.s_r = L;
-  op_ttm(c, bv, Ub, 1, K, R, OView{Snew, L, L * R});
+  op_ttm(c, matrix_view(Bt, J, K, J), Ub, 1, ldu_of(K), R, OView{Snew, L, L * R, L});
 }
 
 // T = X x_n M^T with M (I_n x K, m_i/m_k strides): output dims d[n] -> K
@@ -275,7 +274,7 @@ void run_rsthosvd(Ctx& c, const float* X, const Geom& g0, const int32_t* ranks, 
     for (int n = 0; n < g.N; ++n) {
       max_jk = std::max<size_t>(max_jk, (size_t)g.J(n) * pl.K[n]);
       max_ik = std::max<size_t>(max_ik, (size_t)g.d[n] * pl.K[n]);
-      max_kk = std::max<size_t>(max_kk, (size_t)pl.K[n] * ranks[n]);
+      max_kk = std::max<size_t>(max_kk, (size_t)ldu_of(pl.K[n]) * ranks[n]);
       g.d[n] = ranks[n];
       max_s = std::max<size_t>(max_s, (size_t)g.numel());
     }
@@ -317,7 +316,7 @@ void run_rhosvd(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, con
   for (int n = 0; n < g.N; ++n) {
     max_jk = std::max<size_t>(max_jk, (size_t)g.J(n) * pl.K[n]);
     max_ik = std::max<size_t>(max_ik, (size_t)g.d[n] * pl.K[n]);
-    max_kk = std::max<size_t>(max_kk, (size_t)pl.K[n] * ranks[n]);
+    max_kk = std::max<size_t>(max_kk, (size_t)ldu_of(pl.K[n]) * ranks[n]);
   }
   // core chain sizes: T_n = X x_1 U_1^T ... x_n U_n^T
   size_t max_t = 1;
@@ -420,7 +419,7 @@ void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const
     const bool gen = (Omega_t == nullptr || Omega_t[n] == nullptr);
     Omt[n] = gen ? c.take<float>((size_t)pl.S[n] * g.d[n]) : nullptr;
     Pt[n] = c.take<float>((size_t)pl.S[n] * pl.K[n]);
-    Vb[n] = c.take<float>((size_t)pl.K[n] * ranks[n]);
+    Vb[n] = c.take<float>((size_t)ldu_of(pl.K[n]) * ranks[n]);
   }
   bool need_om = false;
   for (int n = 0; n < N; ++n) need_om |= (Omega == nullptr || Omega[n] == nullptr);
@@ -502,7 +501,7 @@ void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const
     cv.s_r = L * K;
     op_gram_df(c, cv, WView{cur, L * K, L}, K, Gd);
     c.launches += 1;
-    if (!c.dry) c.check(launch_small_eig(Gd, K, R, Vb[n], nullptr, c.st, c.s));
+    if (!c.dry) c.check(launch_small_eig(Gd, K, R, Vb[n], ldu_of(K), nullptr, c.st, c.s));
     lift_factor(c, Ys[n], g.d[n], K, Vb[n], R, U[n]);
   }
   Geom tc = cs;
@@ -511,7 +510,7 @@ void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const
   int which = (cur == Cb[0]) ? 1 : 0;   // the buffer not holding C
   for (int n = 0; n < N; ++n) {
     float* dst = (n == N - 1) ? G : bufs[which];
-    ttm_mode(c, chain, tc, n, Vb[n], 1, pl.K[n], ranks[n], dst);
+    ttm_mode(c, chain, tc, n, Vb[n], 1, ldu_of(pl.K[n]), ranks[n], dst);
     tc.d[n] = ranks[n];
     chain = dst;
     which ^= 1;

@@ -28,8 +28,8 @@ namespace {
 constexpr int MAX_SWEEPS = 30;
 
 __global__ void __launch_bounds__(1024)
-small_eig_kernel(const double* __restrict__ G, int K, int R, float* __restrict__ Ub, float* __restrict__ sv,
-                 DevStatus* st) {
+small_eig_kernel(const double* __restrict__ G, int K, int R, float* __restrict__ Ub, int ldu,
+                 float* __restrict__ sv, DevStatus* st) {
   extern __shared__ __align__(16) unsigned char eig_smem[];
   double* Gs = reinterpret_cast<double*>(eig_smem);                       // K x K FP64, then the DW factor
   float* X = reinterpret_cast<float*>(eig_smem + (size_t)K * K * sizeof(double));   // K x K FP32
@@ -58,7 +58,7 @@ small_eig_kernel(const double* __restrict__ G, int K, int R, float* __restrict__
   __syncthreads();
   if (nonfinite || !isfinite(maxdiag)) {
     if (tid == 0) set_error(st, RHOSVD_ENONFINITE);
-    for (int e = tid; e < K * R; e += blockDim.x) Ub[e] = 0.f;
+    for (int e = tid; e < K * R; e += blockDim.x) Ub[(e % K) + (e / K) * ldu] = 0.f;
     return;
   }
   int e2 = 0;
@@ -143,7 +143,7 @@ small_eig_kernel(const double* __restrict__ G, int K, int R, float* __restrict__
     const int rank = e / K, r = e - rank * K;
     const int c = order[rank];
     const float nc = norms[c];
-    Ub[r + rank * K] = (nc > 1e-6f * smax && nc > 0.f) ? X[r + c * K] / nc : 0.f;
+    Ub[r + rank * ldu] = (nc > 1e-6f * smax && nc > 0.f) ? X[r + c * K] / nc : 0.f;
   }
   __syncthreads();
   if (tid == 0) {
@@ -153,12 +153,12 @@ small_eig_kernel(const double* __restrict__ G, int K, int R, float* __restrict__
       const float nc = norms[order[rank]];
       if (nc > 1e-6f * smax && nc > 0.f) continue;
       for (; e_next < K; ++e_next) {
-        float* u = Ub + rank * K;
+        float* u = Ub + rank * ldu;
         for (int r = 0; r < K; ++r) u[r] = (r == e_next) ? 1.f : 0.f;
         for (int pass = 0; pass < 2; ++pass)
           for (int o = 0; o < R; ++o) {
             if (o == rank) continue;
-            const float* v = Ub + o * K;
+            const float* v = Ub + o * ldu;
             float d = 0.f, vv = 0.f;
             for (int r = 0; r < K; ++r) {
               d = fmaf(v[r], u[r], d);
@@ -182,7 +182,7 @@ small_eig_kernel(const double* __restrict__ G, int K, int R, float* __restrict__
 
 }  // namespace
 
-cudaError_t launch_small_eig(const double* G, int K, int R, float* Ub, float* sv, DevStatus* st,
+cudaError_t launch_small_eig(const double* G, int K, int R, float* Ub, int ldu, float* sv, DevStatus* st,
                              cudaStream_t stream) {
   const size_t smem = (size_t)K * K * (sizeof(double) + sizeof(float));
   cudaError_t e = allow_dynamic_smem((const void*)small_eig_kernel,
@@ -191,7 +191,7 @@ cudaError_t launch_small_eig(const double* G, int K, int R, float* Ub, float* sv
   // one warp per rotation pair (at most 32 warps), at least the 256 threads the factorisation uses
   int warps = (K + 1) / 2;
   warps = warps < 8 ? 8 : (warps > 32 ? 32 : warps);
-  small_eig_kernel<<<1, 32 * warps, smem, stream>>>(G, K, R, Ub, sv, st);
+  small_eig_kernel<<<1, 32 * warps, smem, stream>>>(G, K, R, Ub, ldu, sv, st);
   return cudaGetLastError();
 }
 

@@ -28,10 +28,13 @@ struct WView {
   int64_t w_r, w_k;
 };
 
-// Output of a TTM: Out(j, k) at base[l + k*o_k + r*o_r].
+// Output of a TTM: Out(j, k) at base[l + k*o_k + r*o_r], where j = l + L*r is
+// split with L = o_L when o_L > 0 (an input read as a flat matrix whose rows
+// map onto a strided output), else with the input view's L.
 struct OView {
   float* p;
   int64_t o_k, o_r;
+  int64_t o_L = 0;
 };
 
 // ---- sketch.cu
@@ -125,8 +128,8 @@ cudaError_t launch_reduce_d(const double* part, int splits, int64_t n, double* o
 // ---- eig.cu
 // Leading R eigenvectors (descending) of the symmetric PSD K x K FP64 matrix
 // G: semidefinite Cholesky G = L L^T (FP64), then one-sided Jacobi on L^T in
-// FP32.  Ub is K x R (ld K); sv (nullable) receives sqrt(eigenvalues), K entries.
-cudaError_t launch_small_eig(const double* G, int K, int R, float* Ub, float* sv, DevStatus* st,
+// FP32.  Ub is K x R (leading dimension ldu >= K); sv (nullable) receives sqrt(eigenvalues), K entries.
+cudaError_t launch_small_eig(const double* G, int K, int R, float* Ub, int ldu, float* sv, DevStatus* st,
                              cudaStream_t stream);
 
 // ---- misc

@@ -183,8 +183,10 @@ ttm_kernel(View x, const float* __restrict__ M, int64_t m_i, int64_t m_k, int K,
     const int64_t j = j0 + tid;
     if (j < J) {
       const int64_t r = j / x.L, l = j - r * x.L;
+      const int64_t oL = out.o_L > 0 ? out.o_L : x.L;
+      const int64_t ro = j / oL;
       xoff[tid] = l + r * x.s_r;
-      ooff[tid] = l + r * out.o_r;
+      ooff[tid] = (j - ro * oL) + ro * out.o_r;
     } else {
       xoff[tid] = -1;
       ooff[tid] = -1;

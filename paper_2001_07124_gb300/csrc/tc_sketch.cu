@@ -1,6 +1,11 @@
-// Tensor-core (tcgen05) mode-1 sketch Y = X_(1) W for an X whose first mode
-// is contiguous (L = 1): Y(i,k) = sum_j X[i + I*j] W[j + J*k] (Alg. 1 step 2,
-// Alg. 6 line 3, Alg. 9 line 1 for n = 1; the dominant pass of R-STHOSVD).
+// Tensor-core (tcgen05) sketch Y = X_(n) W on a strided unfolding:
+// Y(i,k) = sum_j X_(n)(i,j) W[j + J*k], X_(n)(i, j = l + L*r) = X[l + s_i*i + s_r*r]
+// (Alg. 1 step 2, Alg. 6 line 3, Alg. 9 line 1; for n = 1 the dominant pass of
+// R-STHOSVD).  Two stage layouts of the 16 j x 512 i X tile:
+//   * mode 1 (L = 1): 2-D boxes {256 i, 16 j}, smem [jj][256 i];
+//   * strided (L % 16 == 0): 3-D boxes {16 l, 256 i, 1 r} over [L, I, Rt] with
+//     64-byte swizzle, smem [i][16 l], each lane reading its own 64-byte row as
+//     four float4 (16-byte chunk c of row i sits at chunk c ^ ((i >> 1) & 3)).
 //
 // The contraction over j is split over CTAs (one CTA per SM, persistent); each
 // CTA owns up to 512 rows i (four 128-row MMA tiles) and a contiguous range of
@@ -19,8 +24,9 @@
 //     A_hi*B_hi + A_hi*B_lo + A_lo*B_hi into FP32 accumulators in TMEM.
 //   * At the end the transform warps read the accumulators (tcgen05.ld) and
 //     write the partial sums.
-// Requirements (checked by the launcher, which otherwise declines): I % 4 == 0,
-// J % 4 == 0 (TMA strides), K <= 64.
+// Requirements (checked by tc_sketch_supported): K <= 64, J >= 1024, W a
+// plain J x K matrix with J % 4 == 0, 16-byte aligned pointers; mode 1 needs
+// I % 4 == 0, a strided view L % 16 == 0 and strides that are multiples of 4.
 #include <algorithm>
 
 #include "common.cuh"
@@ -46,7 +52,7 @@ constexpr int A_STAGE_COLS = 128;         // per stage: 4 tiles x (16 hi + 16 lo
 constexpr int B_TILE = 64 * BJ;           // floats per B tile (N <= 64)
 
 struct __align__(1024) SketchSmem {
-  float x[X_STAGES][ROWS / BOXW][BJ * BOXW];   // TMA boxes: [box][jj][256]
+  float x[X_STAGES][ROWS / BOXW][BJ * BOXW];   // TMA boxes: mode 1 [box][jj][256], strided [box][i][16]
   float wraw[X_STAGES][B_TILE];                // TMA box [n][jj], rows n >= K are zero-filled
   float b[A_STAGES][2][B_TILE];                // hi / lo B tiles, canonical K-major layout
   uint64_t full_x[X_STAGES], empty_x[X_STAGES];
@@ -61,10 +67,10 @@ struct __align__(1024) SketchSmem {
 // 8-row x 16-byte core matrices with LBO = 128 (K direction) and SBO = 512
 // (N direction); the second MMA K step starts 256 bytes in.
 
-template <int NPAD>
+template <int NPAD, bool M1>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
-tc_sketch_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, int I,
-                    int64_t J, int K, int64_t jchunk, float* __restrict__ part, DevStatus* st) {
+tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, int I,
+                 int64_t L, int64_t J, int K, int64_t jchunk, float* __restrict__ part, DevStatus* st) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   SketchSmem& sm = *reinterpret_cast<SketchSmem*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -113,7 +119,14 @@ tc_sketch_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
         if (!mbar_wait(&sm.empty_x[s], ph ^ 1u, abort_flag)) { ok = false; break; }
         mbar_arrive_expect_tx(&sm.full_x[s], bytes);
         const int jt = (int)(jb + (int64_t)kb * BJ);
-        for (int bx = 0; bx < nbox; ++bx) tma_load_2d(sm.x[s][bx], &tmX, i0 + bx * BOXW, jt, &sm.full_x[s]);
+        if (M1) {
+          for (int bx = 0; bx < nbox; ++bx) tma_load_2d(sm.x[s][bx], &tmX, i0 + bx * BOXW, jt, &sm.full_x[s]);
+        } else {
+          const int64_t rj = (int64_t)jt / L;
+          const int lj = (int)((int64_t)jt - rj * L);
+          for (int bx = 0; bx < nbox; ++bx)
+            tma_load_3d(sm.x[s][bx], &tmX, lj, i0 + bx * BOXW, (int)rj, &sm.full_x[s]);
+        }
         tma_load_2d(sm.wraw[s], &tmW, jt, 0, &sm.full_x[s]);
       }
     }
@@ -160,12 +173,25 @@ tc_sketch_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
         const int t = 2 * wg + tt;
         if (t < mt) {
           const int r = t * 128 + row_in_tile;       // row within the CTA's block
-          const float* xb = sm.x[s][r / BOXW] + (r % BOXW);
           uint32_t hi[16], lo[16];
+          if (M1) {
+            const float* xb = sm.x[s][r / BOXW] + (r % BOXW);
 #pragma unroll
-          for (int jj = 0; jj < BJ; ++jj) {
-            const float v = (jj < valid && r < rows) ? xb[jj * BOXW] : 0.f;
-            split_tf32(v, hi[jj], lo[jj]);
+            for (int jj = 0; jj < BJ; ++jj) {
+              const float v = (jj < valid && r < rows) ? xb[jj * BOXW] : 0.f;
+              split_tf32(v, hi[jj], lo[jj]);
+            }
+          } else {
+            const int rr = r % BOXW;
+            const float4* xr = reinterpret_cast<const float4*>(sm.x[s][r / BOXW] + rr * BJ);
+#pragma unroll
+            for (int c = 0; c < BJ / 4; ++c) {
+              float4 v = xr[c ^ ((rr >> 1) & 3)];
+              if (r >= rows) v = make_float4(0.f, 0.f, 0.f, 0.f);
+              const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+              for (int u = 0; u < 4; ++u) split_tf32((4 * c + u < valid) ? e[u] : 0.f, hi[4 * c + u], lo[4 * c + u]);
+            }
           }
           const uint32_t col = tmem + (uint32_t)(A_COL0 + a * A_STAGE_COLS + t * 32);
           tmem_st_x16(col + lane_base, hi);
@@ -234,65 +260,44 @@ tc_sketch_m1_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_consta
 }
 
 // ---------------------------------------------------------------- host side
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeTiledFn encode_fn() {
-  static EncodeTiledFn fn = nullptr;
-  static bool tried = false;
-  if (!tried) {
-    tried = true;
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  return fn;
+template <int NPAD, bool M1>
+cudaError_t launch_k(const CUtensorMap& tmX, const CUtensorMap& tmW, int I, int64_t L, int64_t J, int K,
+                     const TcSketchPlan& pl, float* part, DevStatus* st, cudaStream_t stream) {
+  const size_t smem = sizeof(SketchSmem) + 1024;
+  cudaError_t e = allow_dynamic_smem((const void*)tc_sketch_kernel<NPAD, M1>, smem);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)pl.splits, (unsigned)pl.mgroups);
+  tc_sketch_kernel<NPAD, M1><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmW, I, L, J, K, pl.jchunk, part, st);
+  return cudaGetLastError();
 }
 
-// 2-D FP32 tensor map: inner dimension contiguous, outer stride in elements.
-bool make_tmap_2d(CUtensorMap* m, const float* base, uint64_t inner, uint64_t outer, uint64_t outer_stride,
-                  uint32_t box_inner, uint32_t box_outer) {
-  EncodeTiledFn fn = encode_fn();
-  if (fn == nullptr) return false;
-  cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {outer_stride * sizeof(float)};
-  cuuint32_t box[2] = {box_inner, box_outer};
-  cuuint32_t estr[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-int num_sms() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
+template <bool M1>
+cudaError_t launch_m(const CUtensorMap& tmX, const CUtensorMap& tmW, int I, int64_t L, int64_t J, int K,
+                     const TcSketchPlan& pl, float* part, DevStatus* st, cudaStream_t stream) {
+  switch (((K + 15) / 16) * 16) {
+    case 16: return launch_k<16, M1>(tmX, tmW, I, L, J, K, pl, part, st, stream);
+    case 32: return launch_k<32, M1>(tmX, tmW, I, L, J, K, pl, part, st, stream);
+    case 48: return launch_k<48, M1>(tmX, tmW, I, L, J, K, pl, part, st, stream);
+    default: return launch_k<64, M1>(tmX, tmW, I, L, J, K, pl, part, st, stream);
   }
-  return n;
 }
 
 }  // namespace
 
 bool tc_sketch_supported(const View& x, const WView& w, int K) {
-  if (x.L != 1 || x.s_i != 1 || x.s_r != x.I) return false;           // mode-1 layout
-  const int64_t J = x.Rt;
-  if (w.w_r != 1 || w.w_k != J) return false;                          // W is J x K, ld J
-  if (K < 1 || K > 64 || x.I % 4 != 0 || J % 4 != 0 || x.I > (int64_t(1) << 30)) return false;
+  const int64_t J = x.L * x.Rt;
+  if (w.w_r != x.L || w.w_k != J || J % 4 != 0) return false;      // W is a plain J x K matrix
+  if (K < 1 || K > 64 || x.I < 1 || x.I > (int64_t(1) << 30) || J < 1024 || J >= (int64_t(1) << 31)) return false;
   if ((reinterpret_cast<uintptr_t>(x.p) & 15) || (reinterpret_cast<uintptr_t>(w.p) & 15)) return false;
-  return J >= 1024 && encode_fn() != nullptr;
+  if (x.L == 1) return x.s_i == 1 && x.s_r == x.I && x.I % 4 == 0;  // mode-1 layout
+  if (x.L % BJ != 0 || x.s_i % 4 != 0 || (x.Rt > 1 && x.s_r % 4 != 0)) return false;
+  return x.L < (int64_t(1) << 31) && x.Rt < (int64_t(1) << 31);
 }
 
 TcSketchPlan plan_tc_sketch(int64_t I, int K, int64_t J) {
   TcSketchPlan pl;
   pl.mgroups = (int)((I + ROWS - 1) / ROWS);
-  int64_t splits = std::max<int64_t>(1, num_sms() / pl.mgroups);
+  int64_t splits = std::max<int64_t>(1, device_sms() / pl.mgroups);
   int64_t chunk = (J + splits - 1) / splits;
   chunk = ((chunk + BJ - 1) / BJ) * BJ;
   pl.jchunk = chunk;
@@ -303,34 +308,30 @@ TcSketchPlan plan_tc_sketch(int64_t I, int K, int64_t J) {
 
 cudaError_t launch_tc_sketch(const View& x, const WView& w, int K, float* Y, int64_t ldy, float* part,
                              DevStatus* st, cudaStream_t stream) {
-  const int64_t I = x.I, J = x.Rt;
+  const int64_t I = x.I, J = x.L * x.Rt;
   TcSketchPlan pl = plan_tc_sketch(I, K, J);
   CUtensorMap tmX, tmW;
-  if (!make_tmap_2d(&tmX, x.p, (uint64_t)I, (uint64_t)J, (uint64_t)I, BOXW, BJ)) return cudaErrorNotSupported;
-  if (!make_tmap_2d(&tmW, w.p, (uint64_t)J, (uint64_t)K, (uint64_t)J, BJ, 64)) return cudaErrorNotSupported;
-  const size_t smem = sizeof(SketchSmem) + 1024;
-  const dim3 grid((unsigned)pl.splits, (unsigned)pl.mgroups);
-  cudaError_t e;
-  const int npad = ((K + 15) / 16) * 16;
-  switch (npad) {
-    case 16:
-      if ((e = allow_dynamic_smem((const void*)tc_sketch_m1_kernel<16>, smem)) != cudaSuccess) return e;
-      tc_sketch_m1_kernel<16><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmW, (int)I, J, K, pl.jchunk, part, st);
-      break;
-    case 32:
-      if ((e = allow_dynamic_smem((const void*)tc_sketch_m1_kernel<32>, smem)) != cudaSuccess) return e;
-      tc_sketch_m1_kernel<32><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmW, (int)I, J, K, pl.jchunk, part, st);
-      break;
-    case 48:
-      if ((e = allow_dynamic_smem((const void*)tc_sketch_m1_kernel<48>, smem)) != cudaSuccess) return e;
-      tc_sketch_m1_kernel<48><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmW, (int)I, J, K, pl.jchunk, part, st);
-      break;
-    default:
-      if ((e = allow_dynamic_smem((const void*)tc_sketch_m1_kernel<64>, smem)) != cudaSuccess) return e;
-      tc_sketch_m1_kernel<64><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmW, (int)I, J, K, pl.jchunk, part, st);
-      break;
+  {
+    const uint64_t dims[2] = {(uint64_t)J, (uint64_t)K};
+    const uint64_t strides[1] = {(uint64_t)J};
+    const uint32_t box[2] = {BJ, 64};
+    if (!make_tmap_f32(&tmW, w.p, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE)) return cudaErrorNotSupported;
   }
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  cudaError_t e;
+  if (x.L == 1) {
+    const uint64_t dims[2] = {(uint64_t)I, (uint64_t)J};
+    const uint64_t strides[1] = {(uint64_t)I};
+    const uint32_t box[2] = {BOXW, BJ};
+    if (!make_tmap_f32(&tmX, x.p, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE)) return cudaErrorNotSupported;
+    e = launch_m<true>(tmX, tmW, (int)I, 1, J, K, pl, part, st, stream);
+  } else {
+    const uint64_t dims[3] = {(uint64_t)x.L, (uint64_t)I, (uint64_t)x.Rt};
+    const uint64_t strides[2] = {(uint64_t)x.s_i, x.Rt > 1 ? (uint64_t)x.s_r : (uint64_t)x.s_i * (uint64_t)I};
+    const uint32_t box[3] = {BJ, BOXW, 1};
+    if (!make_tmap_f32(&tmX, x.p, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B)) return cudaErrorNotSupported;
+    e = launch_m<false>(tmX, tmW, (int)I, x.L, J, K, pl, part, st, stream);
+  }
+  if (e != cudaSuccess) return e;
   return launch_reduce_partials_f(part, pl.splits, I, K, Y, ldy, stream);
 }
 

@@ -3,8 +3,9 @@
 //   X_(n)(i, j = l + L*r) = X[l + s_i*i + s_r*r]   (Sec. 2, Eq. for the n-mode product)
 // i.e. Z = X_(n)^T Q (the power-iteration TTM of Alg. 1 step 2), B^T = X_(n)^T Q
 // (the projection B = Q^T X_(n), Alg. 1 step 4) and, with X a tall matrix seen
-// as L = rows, Y R^-1 (the CholeskyQR apply).  Out(j, k) is written at
-// Out[l + r*o_r + k*o_k].
+// as L = rows, Y R^-1 (the CholeskyQR apply) and the refold Ubar^T B.
+// Out(j, k) is written at Out[l + r*o_r + k*o_k] with j = l + o_L*r (o_L
+// defaults to the input's L).
 //
 // Two tile layouts of the 128 j x 32 i stage:
 //   * mode 1 (L = 1, i contiguous): one 2-D box {32 i, 128 j} with 128B swizzle,
@@ -73,7 +74,7 @@ template <int NPAD, bool M1>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmM, int I,
               int64_t L, int64_t J, int bl_bits, int K, float* __restrict__ out, int64_t o_k, int64_t o_r,
-              const DevStatus* skip, DevStatus* st) {
+              int64_t o_L, const DevStatus* skip, DevStatus* st) {
   if (skip != nullptr && skip->orth_fail) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TtmSmem& sm = *reinterpret_cast<TtmSmem*>(
@@ -225,8 +226,8 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       tc_fence_after();
       const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
       const int64_t j = (int64_t)tile * TILE_J + quad * 32 + lane;
-      const int64_t rj = j / L;
-      float* orow = out + (j - rj * L) + rj * o_r;
+      const int64_t rj = j / o_L;
+      float* orow = out + (j - rj * o_L) + rj * o_r;
 #pragma unroll
       for (int c0 = 0; c0 < NPAD; c0 += 16) {
         uint32_t v[16];
@@ -271,8 +272,9 @@ cudaError_t launch_npad(const CUtensorMap& tmX, const CUtensorMap& tmM, int I, i
   if (e != cudaSuccess) return e;
   const int ntiles = (int)((J + TILE_J - 1) / TILE_J);
   const int grid = std::min(ntiles, device_sms());
+  const int64_t o_L = out.o_L > 0 ? out.o_L : L;
   tc_ttm_kernel<NPAD, M1><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmM, I, L, J, bl_bits, K, out.p, out.o_k,
-                                                                out.o_r, skip, st);
+                                                                out.o_r, o_L, skip, st);
   return cudaGetLastError();
 }
 

@@ -136,6 +136,25 @@ def test_tc_sketch_mode1_parity(dims, K):
     assert_close_abs(Y3, a @ om3, np.abs(a) @ np.abs(om3))
 
 
+# Strided unfoldings (L % 16 == 0, J >= 1024) on the tcgen05 sketch kernel
+# through 64-byte-swizzled 3-D TMA boxes: L = 16 / 32 / 128 / L*I*Rt with
+# Rt = 1, I below / across one 256-row box and above one 512-row group, 4-way.
+TC_STRIDED_CASES = [((32, 512, 40), 1, 42), ((16, 100, 70), 1, 16), ((128, 300, 9), 1, 33),
+                    ((32, 32, 600), 2, 64), ((16, 8, 40, 12), 2, 20), ((32, 16, 8, 36), 3, 7)]
+
+
+@pytest.mark.parametrize("dims,mode,K", TC_STRIDED_CASES)
+def test_tc_sketch_strided_parity(dims, mode, K):
+    x = random_tensor(dims, 25)
+    X = dev(x)
+    a = T.unfold(f32(x), mode)
+    J = int(np.prod(dims)) // dims[mode]
+    om = gaussian_matrix(26, J, K)
+    om64 = om.astype(np.float64)
+    Y = host(R().rhosvd_sketch(X, dims, mode, K, Omega=dev_mat(om)))
+    assert_close_abs(Y, a @ om64, np.abs(a) @ np.abs(om64))
+
+
 def test_tc_sketch_is_deterministic():
     dims, K = (512, 64, 64), 42
     X = dev(random_tensor(dims, 23))
