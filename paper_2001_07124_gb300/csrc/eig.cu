@@ -12,7 +12,9 @@
 // R = L^T, and Jacobi on R^T = L converges in few sweeps.  At convergence
 // L V = U Sigma, so U is the normalised columns of the rotated L and V is never
 // accumulated; accuracy is set by sigma_1 / (sigma_R - sigma_R+1) in FP32.
-// Pairs follow the round-robin (circle) ordering, one warp per rotation.
+// Pairs follow the round-robin (circle) ordering; each rotation is handled by
+// a group of 8 lanes (4 pairs per warp, 3-shuffle dot products), which keeps
+// the number of warps, and so the issue slots a round takes, small.
 // Columns at FP32 noise level (rank below R) are replaced by an orthonormal
 // completion (Gram-Schmidt on unit vectors).
 #include <math.h>
@@ -26,8 +28,10 @@ namespace rhosvd {
 namespace {
 
 constexpr int MAX_SWEEPS = 30;
+constexpr int PAIR_LANES = 8;            // lanes per rotation pair
 
-__global__ void __launch_bounds__(1024)
+template <int KB>                        // KB >= K, a multiple of 16
+__global__ void __launch_bounds__(512, 1)
 small_eig_kernel(const double* __restrict__ G, int K, int R, float* __restrict__ Ub, int ldu,
                  float* __restrict__ sv, DevStatus* st) {
   extern __shared__ __align__(16) unsigned char eig_smem[];
@@ -64,8 +68,8 @@ small_eig_kernel(const double* __restrict__ G, int K, int R, float* __restrict__
   int e2 = 0;
   if (maxdiag > 0.0) {
     e2 = 2 * (ilogb(maxdiag) / 2);
-    chol_grid<DWOps>(Gs, K, e2, (double)K * 1e-14 * ldexp(maxdiag, -e2), true, X, reinterpret_cast<df64*>(Gs),
-                     rs_dw, &flag);
+    chol_grid<DWOps, KB>(Gs, K, e2, (double)K * 1e-14 * ldexp(maxdiag, -e2), true, X,
+                         reinterpret_cast<df64*>(Gs), rs_dw, &flag);
   } else {
     for (int e = tid; e < K * K; e += blockDim.x) X[e] = 0.f;
   }
@@ -84,28 +88,56 @@ small_eig_kernel(const double* __restrict__ G, int K, int R, float* __restrict__
     if (tid == 0) rotated = 0;
     __syncthreads();
     for (int s = 0; s < n - 1; ++s) {
-      for (int w = warp; w < npairs; w += nwarps) {
+      const int g = lane / PAIR_LANES, gl = lane % PAIR_LANES;
+      for (int w = warp * (32 / PAIR_LANES) + g; w < npairs + g; w += nwarps * (32 / PAIR_LANES)) {
+        // every lane of the warp takes part in the shuffles; groups past the last pair idle
+        const bool live = w < npairs;
         int xa = w - 1 + s, xb = n - 2 - w + s;          // circle method, both < 2(n-1)
         if (xa >= n - 1) xa -= n - 1;
         if (xb >= n - 1) xb -= n - 1;
         const int a = (w == 0) ? 0 : xa + 1, b = xb + 1;
-        const int p = min(a, b), q = max(a, b);
-        if (q >= K) continue;
+        const int p = min(a, b), q = live ? max(a, b) : K;
+        // the pair's columns stay in registers from the dot product to the rotation
+        constexpr int NR = KB / PAIR_LANES;
+        float xv[NR], yv[NR];
         float gamma = 0.f;
-        for (int r = lane; r < K; r += 32) gamma = fmaf(X[r + p * K], X[r + q * K], gamma);
-        gamma = warp_sum(gamma);
+#pragma unroll
+        for (int u = 0; u < NR; ++u) {
+          const int r = gl + PAIR_LANES * u;
+          const bool in = (q < K) && (r < K);
+          xv[u] = in ? X[r + p * K] : 0.f;
+          yv[u] = in ? X[r + q * K] : 0.f;
+          gamma = fmaf(xv[u], yv[u], gamma);
+        }
+#pragma unroll
+        for (int o = PAIR_LANES / 2; o > 0; o >>= 1) gamma += __shfl_xor_sync(0xffffffffu, gamma, o);
+        if (q >= K) continue;
         const float alpha = norms[p], beta = norms[q];
-        if (gamma != 0.f && fabsf(gamma) > jtol * sqrtf(alpha * beta)) {
+        // gamma != 0 implies alpha, beta > 0; sqrt(v) = v * rsqrt(v) avoids the product's underflow
+        if (gamma != 0.f && fabsf(gamma) > jtol * (alpha * rsqrtf(alpha)) * (beta * rsqrtf(beta))) {
+          // t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)); c, s from t keep the rotation
+          // orthogonal to rounding whatever t's own accuracy
           const float zeta = __fdividef(beta - alpha, 2.f * gamma);
-          const float t = copysignf(1.f, zeta) * __frcp_rn(fabsf(zeta) + sqrtf(fmaf(zeta, zeta, 1.f)));
+          const float az = fabsf(zeta);
+          float t;
+          if (az < 1e15f) {
+            const float h = fmaf(zeta, zeta, 1.f);
+            t = __fdividef(1.f, az + h * rsqrtf(h));
+          } else {
+            t = __fdividef(0.5f, az);
+          }
+          t = copysignf(t, zeta);
           const float c = rsqrtf(fmaf(t, t, 1.f));
           const float sn = c * t;
-          for (int r = lane; r < K; r += 32) {
-            const float x = X[r + p * K], y = X[r + q * K];
-            X[r + p * K] = c * x - sn * y;
-            X[r + q * K] = sn * x + c * y;
+#pragma unroll
+          for (int u = 0; u < NR; ++u) {
+            const int r = gl + PAIR_LANES * u;
+            if (r < K) {
+              X[r + p * K] = c * xv[u] - sn * yv[u];
+              X[r + q * K] = sn * xv[u] + c * yv[u];
+            }
           }
-          if (lane == 0) {
+          if (gl == 0) {
             norms[p] = fmaxf(alpha - t * gamma, 0.f);
             norms[q] = beta + t * gamma;
             rotated = 1;
@@ -180,19 +212,31 @@ small_eig_kernel(const double* __restrict__ G, int K, int R, float* __restrict__
   }
 }
 
+template <int KB>
+static cudaError_t launch_eig_kb(const double* G, int K, int R, float* Ub, int ldu, float* sv, DevStatus* st,
+                                 cudaStream_t stream) {
+  const size_t smem = (size_t)K * K * (sizeof(double) + sizeof(float));
+  cudaError_t e = allow_dynamic_smem((const void*)small_eig_kernel<KB>,
+                                     (size_t)KB * KB * (sizeof(double) + sizeof(float)));
+  if (e != cudaSuccess) return e;
+  // one 8-lane group per rotation pair, at least the 256 threads the factorisation uses
+  const int npairs = (K + 1) / 2;
+  int warps = (npairs + 32 / PAIR_LANES - 1) / (32 / PAIR_LANES);
+  warps = warps < 8 ? 8 : warps;
+  small_eig_kernel<KB><<<1, 32 * warps, smem, stream>>>(G, K, R, Ub, ldu, sv, st);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_small_eig(const double* G, int K, int R, float* Ub, int ldu, float* sv, DevStatus* st,
                              cudaStream_t stream) {
-  const size_t smem = (size_t)K * K * (sizeof(double) + sizeof(float));
-  cudaError_t e = allow_dynamic_smem((const void*)small_eig_kernel,
-                                     (size_t)RHOSVD_MAX_K * RHOSVD_MAX_K * (sizeof(double) + sizeof(float)));
-  if (e != cudaSuccess) return e;
-  // one warp per rotation pair (at most 32 warps), at least the 256 threads the factorisation uses
-  int warps = (K + 1) / 2;
-  warps = warps < 8 ? 8 : (warps > 32 ? 32 : warps);
-  small_eig_kernel<<<1, 32 * warps, smem, stream>>>(G, K, R, Ub, ldu, sv, st);
-  return cudaGetLastError();
+  if (K <= 16) return launch_eig_kb<16>(G, K, R, Ub, ldu, sv, st, stream);
+  if (K <= 32) return launch_eig_kb<32>(G, K, R, Ub, ldu, sv, st, stream);
+  if (K <= 48) return launch_eig_kb<48>(G, K, R, Ub, ldu, sv, st, stream);
+  if (K <= 64) return launch_eig_kb<64>(G, K, R, Ub, ldu, sv, st, stream);
+  if (K <= 96) return launch_eig_kb<96>(G, K, R, Ub, ldu, sv, st, stream);
+  return launch_eig_kb<128>(G, K, R, Ub, ldu, sv, st, stream);
 }
 
 }  // namespace rhosvd

@@ -42,9 +42,11 @@ __device__ __forceinline__ float warp_max(float v) {
 // non-positive at double-word precision), 1e-4 for the second (cond(Q1) > 100).
 //
 // With Minv != nullptr the kernel also writes R^-1 = L^-T (FP32, K x K,
-// column-major, leading dimension ldm), so that the apply Q = Y R^-1 is a
-// plain GEMM: column c of L^-1 by forward substitution (one thread per
-// column), from the same FP32 factor the row-wise solve would use.
+// column-major, leading dimension ldm), so that the apply Q = Y R^-1 is a plain
+// GEMM; the inverse comes from forward substitution run inside the
+// factorisation's own steps (chol_grid), from the FP32 factor the row-wise
+// solve would use.
+template <int KB>
 __global__ void __launch_bounds__(CH_THREADS)
 chol_kernel(const double* __restrict__ G, int K, float* __restrict__ Lout, float* __restrict__ Minv, int ldm,
             int pass, int fail_code, DevStatus* st) {
@@ -52,6 +54,7 @@ chol_kernel(const double* __restrict__ G, int K, float* __restrict__ Lout, float
   extern __shared__ __align__(16) unsigned char ch_smem[];
   double* Gs = reinterpret_cast<double*>(ch_smem);                 // K x K FP64
   unsigned char* work = ch_smem + (size_t)K * K * sizeof(double);  // FP32 factorisation storage
+  float* Tinv = (Minv != nullptr) ? reinterpret_cast<float*>(work + (size_t)K * K * sizeof(float)) : nullptr;
   __shared__ int nonfinite, flag;
   __shared__ float wmax[CH_THREADS / 32];
   __shared__ double maxdiag;
@@ -93,11 +96,11 @@ chol_kernel(const double* __restrict__ G, int K, float* __restrict__ Lout, float
     const int e = 2 * (ilogb(maxdiag) / 2);  // even power of two: exact scaling and unscaling
     const double tol = ((pass == 0) ? (double)K * 1e-14 : 1e-4) * ldexp(maxdiag, -e);
     if (pass == 1 && allmax <= 1e-2f)
-      ok = chol_grid<F32Ops>(Gs, K, e, tol, false, Lout, reinterpret_cast<float*>(work), rs_f, &flag);
+      ok = chol_grid<F32Ops, KB>(Gs, K, e, tol, false, Lout, reinterpret_cast<float*>(work), rs_f, &flag, Tinv);
     else
       // the double-word factor overwrites Gs in place: same element size, and each
       // element is read and rewritten by the same thread
-      ok = chol_grid<DWOps>(Gs, K, e, tol, false, Lout, reinterpret_cast<df64*>(Gs), rs_dw, &flag);
+      ok = chol_grid<DWOps, KB>(Gs, K, e, tol, false, Lout, reinterpret_cast<df64*>(Gs), rs_dw, &flag, Tinv);
   }
   if (!ok) {
     if (tid == 0) {
@@ -109,27 +112,10 @@ chol_kernel(const double* __restrict__ G, int K, float* __restrict__ Lout, float
   }
   if (pass == 0 && tid == 0) st->orth_fail = 0;
   if (Minv == nullptr) return;
-  // L (FP32) was written to Lout by this block; stage it and L^-1 over the Gram storage
-  float* Ls = reinterpret_cast<float*>(ch_smem);     // K x K, column-major
-  float* Li = Ls + K * K;                            // K x K: Li[i + c*K] = (L^-1)(i, c)
   __syncthreads();
-  for (int e = tid; e < K * K; e += CH_THREADS) Ls[e] = Lout[e];
-  __syncthreads();
-  if (tid < K) {
-    const int c = tid;
-    float* x = Li + c * K;
-    for (int i = 0; i < c; ++i) x[i] = 0.f;
-    x[c] = 1.f / Ls[c + c * K];
-    for (int i = c + 1; i < K; ++i) {
-      float s = 0.f;
-      for (int k = c; k < i; ++k) s = fmaf(Ls[i + k * K], x[k], s);
-      x[i] = -s / Ls[i + i * K];
-    }
-  }
-  __syncthreads();
-  for (int e = tid; e < K * K; e += CH_THREADS) {     // Minv(i, c) = (L^-1)(c, i)
-    const int c = e / K, i = e - c * K;
-    Minv[i + (int64_t)c * ldm] = Li[c + i * K];
+  for (int e = tid; e < K * K; e += CH_THREADS) {     // Minv(i, c) = (L^-1)(c, i) = Tinv(c, i) / L(c, c)
+    const int i = e / K, c = e - i * K;
+    Minv[i + (int64_t)c * ldm] = (c >= i) ? Tinv[c + i * K] / Lout[c + c * K] : 0.f;
   }
 }
 
@@ -309,14 +295,26 @@ householder_kernel(float* A, int64_t m, int K, int64_t ld, DevStatus* st, int fo
 
 }  // namespace
 
+template <int KB>
+static cudaError_t launch_chol_kb(const double* G, int K, float* L, float* Minv, int ldm, int pass, int fail_code,
+                                  DevStatus* st, cudaStream_t stream) {
+  // Gram (FP64) + FP32 factor, + the inverse's working matrix when R^-1 is requested (K <= 64)
+  const size_t smem = (size_t)K * K * (sizeof(double) + (Minv != nullptr ? 2 : 1) * sizeof(float));
+  cudaError_t e = allow_dynamic_smem((const void*)chol_kernel<KB>,
+                                     (size_t)KB * KB * (sizeof(double) + (KB <= 64 ? 2 : 1) * sizeof(float)));
+  if (e != cudaSuccess) return e;
+  chol_kernel<KB><<<1, CH_THREADS, smem, stream>>>(G, K, L, Minv, ldm, pass, fail_code, st);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_chol(const double* G, int K, float* L, float* Minv, int ldm, int pass, int fail_code,
                         DevStatus* st, cudaStream_t stream) {
-  const size_t smem = (size_t)K * K * (sizeof(double) + sizeof(float));
-  cudaError_t e = allow_dynamic_smem((const void*)chol_kernel,
-                                     (size_t)RHOSVD_MAX_K * RHOSVD_MAX_K * (sizeof(double) + sizeof(float)));
-  if (e != cudaSuccess) return e;
-  chol_kernel<<<1, CH_THREADS, smem, stream>>>(G, K, L, Minv, ldm, pass, fail_code, st);
-  return cudaGetLastError();
+  if (K <= 16) return launch_chol_kb<16>(G, K, L, Minv, ldm, pass, fail_code, st, stream);
+  if (K <= 32) return launch_chol_kb<32>(G, K, L, Minv, ldm, pass, fail_code, st, stream);
+  if (K <= 48) return launch_chol_kb<48>(G, K, L, Minv, ldm, pass, fail_code, st, stream);
+  if (K <= 64) return launch_chol_kb<64>(G, K, L, Minv, ldm, pass, fail_code, st, stream);
+  if (K <= 96) return launch_chol_kb<96>(G, K, L, nullptr, ldm, pass, fail_code, st, stream);
+  return launch_chol_kb<128>(G, K, L, nullptr, ldm, pass, fail_code, st, stream);
 }
 
 template <int KB>

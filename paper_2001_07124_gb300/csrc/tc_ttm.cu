@@ -58,6 +58,7 @@ struct __align__(1024) TtmSmem {
   float x[X_STAGES][TILE_J * BI];          // TMA tile: mode 1 [j][i] swizzled, strided [r'][i][l']
   float mraw[X_STAGES][M_TILE];            // TMA tile [k][i], rows k >= K zero-filled
   float b[A_STAGES][2][M_TILE];            // hi / lo B tiles, canonical K-major layout
+  float ostage[4][32 * 17];                // per epilogue warp: 32 rows x 16 columns (+1 pad)
   uint64_t full_x[X_STAGES], empty_x[X_STAGES];
   uint64_t full_a[A_STAGES], empty_a[A_STAGES];
   uint64_t d_full[2], d_empty[2];
@@ -228,15 +229,38 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       const int64_t j = (int64_t)tile * TILE_J + quad * 32 + lane;
       const int64_t rj = j / o_L;
       float* orow = out + (j - rj * o_L) + rj * o_r;
+      if (o_k == 1 && o_L == 1) {
+        // rows of the output are contiguous in k (row j at out + j*o_r): stage 32 rows x
+        // 16 columns per warp and store two 64-byte row segments per instruction
+        float* stg = sm.ostage[quad];
+        const int64_t jw = (int64_t)tile * TILE_J + quad * 32;   // first row of this warp
 #pragma unroll
-      for (int c0 = 0; c0 < NPAD; c0 += 16) {
-        uint32_t v[16];
-        tmem_ld_x16(tmem + lane_base + (uint32_t)(buf * D_COLS + c0), v);
-        tmem_wait_ld();
+        for (int c0 = 0; c0 < NPAD; c0 += 16) {
+          uint32_t v[16];
+          tmem_ld_x16(tmem + lane_base + (uint32_t)(buf * D_COLS + c0), v);
+          tmem_wait_ld();
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int k = c0 + c;
-          if (k < K && j < J) orow[(int64_t)k * o_k] = __uint_as_float(v[c]);
+          for (int c = 0; c < 16; ++c) stg[lane * 17 + c] = __uint_as_float(v[c]);
+          __syncwarp();
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int rr = 2 * q + (lane >> 4), cc = lane & 15;
+            const int64_t jr = jw + rr;
+            if (c0 + cc < K && jr < J) out[jr * o_r + c0 + cc] = stg[rr * 17 + cc];
+          }
+          __syncwarp();
+        }
+      } else {
+#pragma unroll
+        for (int c0 = 0; c0 < NPAD; c0 += 16) {
+          uint32_t v[16];
+          tmem_ld_x16(tmem + lane_base + (uint32_t)(buf * D_COLS + c0), v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int k = c0 + c;
+            if (k < K && j < J) orow[(int64_t)k * o_k] = __uint_as_float(v[c]);
+          }
         }
       }
       tc_fence_before();
