@@ -148,4 +148,5 @@ __device__ bool chol_grid(const double* Gs, int K, int e, double tol, bool semid
   return true;
 }
 
+
 }  // namespace rhosvd
