@@ -10,6 +10,11 @@ needed between steps.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 on the host cores instead (the comparison arm of this project).
+``--primitive sketch|power|orth`` times one C-ABI primitive on the workload's
+mode-1 shapes instead (a kernel micro-benchmark for profiling; its line is not
+the benchmark line): sketch = rhosvd_sketch(X, mode 1, Omega_1), power =
+rhosvd_power (TTM, CholeskyQR2 of Z, sketch), orth = rhosvd_orth of a J_1 x K_1
+Gaussian matrix.
 Multi-GPU: every rank decomposes its own tensor (independent replicas, no
 data-path collective); value = all decompositions / slowest rank's time.
 """
@@ -162,6 +167,45 @@ def run_reference(args, w, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_primitive(args, w):
+    """Time one primitive on the workload's mode-1 shapes (device-drawn inputs)."""
+    import torch
+    import paper_2001_07124_gb300 as pkg
+    from paper_2001_07124_gb300 import rhosvd as R
+    pkg.build()
+    R.lib()
+    dims = w.dims
+    Kp, _, _ = R.rhosvd_plan(dims, w.ranks, w.algo, w.p, w.q, K=w.K, S=w.S)
+    K0, I0 = Kp[0], dims[0]
+    J0 = int(np.prod(dims)) // I0
+    g = torch.Generator(device="cuda")
+    g.manual_seed(w.seed)
+    ws = R.Workspace(R.rhosvd_primitive_workspace_size(dims, K0))
+    if args.primitive == "sketch":
+        X = torch.randn(int(np.prod(dims)), device="cuda", generator=g)
+        om = R.rhosvd_omega(w.omega_seed, 0, J0, K0).t().contiguous().reshape(-1)
+        Y = R.empty_colmajor((I0, K0))
+        call = lambda: R.rhosvd_sketch(X, dims, 0, K0, Omega=om, Y=Y, ws=ws)
+    elif args.primitive == "power":
+        X = torch.randn(int(np.prod(dims)), device="cuda", generator=g)
+        Q, _ = R.rhosvd_orth(torch.randn(I0, K0, device="cuda", generator=g), ws=ws)
+        call = lambda: R.rhosvd_power(X, dims, 0, Q.clone(), ws=ws)
+    else:
+        Z = torch.randn(K0, J0, device="cuda", generator=g).t()
+        call = lambda: R.rhosvd_orth(Z, ws=ws)
+    for _ in range(args.warmup):
+        call()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        call()
+    ev1.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"primitive": args.primitive, "workload": w.name, "mode": 1, "K": K0,
+                      "ms_per_call": ev0.elapsed_time(ev1) / args.steps, "calls": args.steps}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -170,6 +214,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="decay512_rsthosvd", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--primitive", choices=["sketch", "power", "orth"], default=None)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -180,6 +225,8 @@ def main():
 
     if args.impl == "reference":
         return run_reference(args, w, rank)
+    if args.primitive is not None:
+        return run_primitive(args, w)
 
     import torch
     import paper_2001_07124_gb300 as pkg
@@ -303,11 +350,12 @@ def main():
     sk_bytes = (X.numel() + J0 * K0 + I0 * K0) * 4      # X once, Omega_1 once, Y once
     sk_gbs = sk_bytes / (sk_ms * 1e-3) / 1e9
     hbm_peak = float(peaks["hbm_gbs"])
-    roofline = {"bound": "hbm", "kernel": "sketch_partial_kernel (mode-1 sketch Y = X_(1) Omega_1 + reduce)",
+    roofline = {"bound": "hbm",
+                "kernel": "tc_sketch_kernel<48,1> + reduce_partials (mode-1 sketch Y = X_(1) Omega_1, rhosvd_sketch)",
                 "achieved": round(sk_gbs, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(sk_gbs / hbm_peak, 4),
                 "peak_source": peak_src, "algorithmic_bytes_per_launch": sk_bytes, "ms_per_launch": sk_ms,
-                "traffic": _traffic_for(os.path.join(ROOT, "paper_2001_07124_gb300", "csrc", "sketch.cu"),
-                                        "sketch_mode1_512")}
+                "traffic": _traffic_for(os.path.join(ROOT, "paper_2001_07124_gb300", "csrc", "tc_sketch.cu"),
+                                        "tc_sketch_mode1_512")}
 
     # ---------------------------------------------------------------- CPU oracle and error gate
     cpu = None

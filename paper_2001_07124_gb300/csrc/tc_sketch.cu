@@ -53,7 +53,7 @@ constexpr int B_TILE = 64 * BJ;           // floats per B tile (N <= 64)
 
 struct __align__(1024) SketchSmem {
   float x[X_STAGES][ROWS / BOXW][BJ * BOXW];   // TMA boxes: mode 1 [box][jj][256], strided [box][i][16]
-  float wraw[X_STAGES][B_TILE];                // TMA box [n][jj], rows n >= K are zero-filled
+  float wraw[X_STAGES][B_TILE];                // TMA box [n][jj] (64B swizzle), rows n >= K are zero-filled
   float b[A_STAGES][2][B_TILE];                // hi / lo B tiles, canonical K-major layout
   uint64_t full_x[X_STAGES], empty_x[X_STAGES];
   uint64_t full_a[A_STAGES], empty_a[A_STAGES];
@@ -205,7 +205,8 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
       for (int u = 0; u < NPAD * BJ / NUM_XFORM; ++u) {
         const int w = tid + u * NUM_XFORM;
         const int n = 8 * (w >> 7) + ((w >> 2) & 7), jj = 4 * ((w >> 5) & 3) + (w & 3);
-        const float v = (jj < valid && n < K) ? sm.wraw[s][n * BJ + jj] : 0.f;
+        // raw W tile rows are 64-byte swizzled: 16-byte chunk c of row n sits at c ^ ((n >> 1) & 3)
+        const float v = (jj < valid && n < K) ? sm.wraw[s][n * BJ + (((jj >> 2) ^ ((n >> 1) & 3)) << 2) + (jj & 3)] : 0.f;
         uint32_t h, l;
         split_tf32(v, h, l);
         reinterpret_cast<uint32_t*>(sm.b[a][0])[w] = h;
@@ -315,7 +316,7 @@ cudaError_t launch_tc_sketch(const View& x, const WView& w, int K, float* Y, int
     const uint64_t dims[2] = {(uint64_t)J, (uint64_t)K};
     const uint64_t strides[1] = {(uint64_t)J};
     const uint32_t box[2] = {BJ, 64};
-    if (!make_tmap_f32(&tmW, w.p, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE)) return cudaErrorNotSupported;
+    if (!make_tmap_f32(&tmW, w.p, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B)) return cudaErrorNotSupported;
   }
   cudaError_t e;
   if (x.L == 1) {

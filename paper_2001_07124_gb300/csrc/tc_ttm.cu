@@ -56,7 +56,7 @@ constexpr int M_TILE = 64 * BI;           // floats per B tile (N <= 64)
 
 struct __align__(1024) TtmSmem {
   float x[X_STAGES][TILE_J * BI];          // TMA tile: mode 1 [j][i] swizzled, strided [r'][i][l']
-  float mraw[X_STAGES][M_TILE];            // TMA tile [k][i], rows k >= K zero-filled
+  float mraw[X_STAGES][M_TILE];            // TMA tile [k][i] (128B swizzle), rows k >= K zero-filled
   float b[A_STAGES][2][M_TILE];            // hi / lo B tiles, canonical K-major layout
   float ostage[4][32 * 17];                // per epilogue warp: 32 rows x 16 columns (+1 pad)
   uint64_t full_x[X_STAGES], empty_x[X_STAGES];
@@ -205,7 +205,8 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       for (int u = 0; u < NPAD * BI / 128; ++u) {
         const int w = xt + u * 128;
         const int n = 8 * (w >> 8) + ((w >> 2) & 7), kk = 4 * ((w >> 5) & 7) + (w & 3);
-        const float v = (n < K) ? sm.mraw[s][n * BI + kk] : 0.f;
+        // raw M tile rows are 128-byte swizzled: 16-byte chunk c of row n sits at c ^ (n & 7)
+        const float v = (n < K) ? sm.mraw[s][n * BI + (((kk >> 2) ^ (n & 7)) << 2) + (kk & 3)] : 0.f;
         uint32_t h, l;
         split_tf32(v, h, l);
         reinterpret_cast<uint32_t*>(sm.b[a][0])[w] = h;
@@ -251,17 +252,18 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           __syncwarp();
         }
       } else {
+        // all accumulator columns of the row in flight at once, one wait
+        uint32_t v[NPAD / 16][16];
 #pragma unroll
-        for (int c0 = 0; c0 < NPAD; c0 += 16) {
-          uint32_t v[16];
-          tmem_ld_x16(tmem + lane_base + (uint32_t)(buf * D_COLS + c0), v);
-          tmem_wait_ld();
+        for (int c0 = 0; c0 < NPAD / 16; ++c0) tmem_ld_x16(tmem + lane_base + (uint32_t)(buf * D_COLS + 16 * c0), v[c0]);
+        tmem_wait_ld();
+#pragma unroll
+        for (int c0 = 0; c0 < NPAD / 16; ++c0)
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
-            const int k = c0 + c;
-            if (k < K && j < J) orow[(int64_t)k * o_k] = __uint_as_float(v[c]);
+            const int k = 16 * c0 + c;
+            if (k < K && j < J) orow[(int64_t)k * o_k] = __uint_as_float(v[c0][c]);
           }
-        }
       }
       tc_fence_before();
       mbar_arrive(&sm.d_empty[buf]);
@@ -335,7 +337,7 @@ cudaError_t launch_tc_ttm(const View& x, const float* Mp, int64_t m_k, int K, co
     const uint64_t dims[2] = {(uint64_t)I, (uint64_t)K};
     const uint64_t strides[1] = {(uint64_t)m_k};
     const uint32_t box[2] = {BI, 64};
-    if (!make_tmap_f32(&tmM, Mp, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE)) return cudaErrorNotSupported;
+    if (!make_tmap_f32(&tmM, Mp, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorNotSupported;
   }
   if (x.L == 1) {
     const uint64_t dims[2] = {(uint64_t)I, (uint64_t)J};
