@@ -215,6 +215,7 @@ def main():
     ap.add_argument("--workload", default="decay512_rsthosvd", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--primitive", choices=["sketch", "power", "orth"], default=None)
+    ap.add_argument("--no-graph", action="store_true", help="launch the decomposition kernel by kernel")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -258,11 +259,18 @@ def main():
     out = (G, Us)
     stream = torch.cuda.current_stream()
 
-    def step():
+    def eager_step():
         R.rhosvd_decompose(X, dims, ranks, ws=ws, out=out, check=False, **kw)
 
     for _ in range(args.warmup):
-        step()
+        eager_step()
+    step = eager_step
+    if not args.no_graph:
+        # the whole decomposition as one CUDA graph launch (same kernels, same buffers)
+        graph = R.DecomposeGraph(X, dims, ranks, ws=ws, out=out, warmup=1, **kw)
+        step = graph.replay
+        for _ in range(2):
+            step()
     code, flags = R.rhosvd_device_status(ws)
     if code != 0:
         raise RuntimeError(f"device status {code} after warm-up")
@@ -381,7 +389,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded low-rank tensor, device-drawn Philox test matrices)",
             "config": {"workload": w.name, "dims": list(dims), "ranks": list(ranks), "algo": w.algo, "p": w.p,
-                       "q": w.q, "parallelism": f"replicas{world}", "l2_flush": "input 512 MiB > 129 MB L2"},
+                       "q": w.q, "parallelism": f"replicas{world}", "l2_flush": "input 512 MiB > 129 MB L2",
+                       "launch": "eager" if args.no_graph else "cuda_graph"},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},

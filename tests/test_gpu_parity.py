@@ -425,6 +425,26 @@ def test_bitwise_deterministic():
         np.testing.assert_array_equal(a, b)
 
 
+def test_decompose_graph_replay_matches_eager():
+    """The CUDA-graph form of a decomposition gives bitwise the eager result,
+    also after new data is copied into the captured input buffer."""
+    dims, ranks = (96, 80, 64), (8, 7, 6)
+    x1 = lowrank_tensor(dims, ranks, 41, noise=1e-3)
+    x2 = lowrank_tensor(dims, ranks, 42, noise=1e-3)
+    X = dev(x1)
+    graph = R().DecomposeGraph(X, dims, ranks, algo="rsthosvd", p=5, q=1, seed=3)
+    for x in (x1, x2):
+        X.copy_(dev(x))
+        graph.replay()
+        torch.cuda.synchronize()
+        g_gr, u_gr = graph.result()
+        g_gr, u_gr = host(g_gr), [host(u) for u in u_gr]
+        g_ea, u_ea = R().rhosvd_decompose(dev(x), dims, ranks, algo="rsthosvd", p=5, q=1, seed=3)
+        np.testing.assert_array_equal(g_gr, host(g_ea))
+        for a, b in zip(u_gr, u_ea):
+            np.testing.assert_array_equal(a, host(b))
+
+
 def test_device_status_cleared_between_calls():
     rh = R()
     dims, ranks = (20, 21, 22), (3, 3, 3)
