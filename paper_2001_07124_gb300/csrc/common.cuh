@@ -89,6 +89,17 @@ __device__ __forceinline__ df64 dw_add(df64 x, df64 y) {
   return df64{s, t};
 }
 __device__ __forceinline__ df64 dw_neg(df64 x) { return df64{-x.hi, -x.lo}; }
+// DW + DW, the cheaper ("sloppy") algorithm: one TwoSum on the high parts and
+// one renormalisation; its error is bounded relative to |x| + |y| rather than
+// |x + y| (Joldes, Muller, Popescu 2017), which is what a backward-stable
+// elimination such as Cholesky needs (|dA| <= c u |L||L^T| with u ~ 2^-44).
+__device__ __forceinline__ df64 dw_add_sloppy(df64 x, df64 y) {
+  float s, t;
+  two_sum(x.hi, y.hi, s, t);
+  t += x.lo + y.lo;
+  fast_two_sum(s, t, s, t);
+  return df64{s, t};
+}
 // DW x DW with FMA
 __device__ __forceinline__ df64 dw_mul(df64 x, df64 y) {
   const float ch = x.hi * y.hi;

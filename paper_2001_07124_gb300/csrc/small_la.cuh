@@ -24,7 +24,8 @@ struct DWOps {
   __device__ static T from(double v) { return dw_from_double(v); }
   __device__ static T zero() { return df64{0.f, 0.f}; }
   __device__ static T mul(T a, T b) { return dw_mul(a, b); }
-  __device__ static T sub(T a, T b) { return dw_add(a, dw_neg(b)); }
+  // the trailing update only needs backward stability: the cheaper DW sum suffices
+  __device__ static T sub(T a, T b) { return dw_add_sloppy(a, dw_neg(b)); }
   __device__ static T rsqrt(T d) { return dw_rsqrt(d); }
   __device__ static float hi(T a) { return a.hi; }
 };
