@@ -143,11 +143,11 @@ void op_orth(Ctx& c, float* Y, int64_t m, int K, int64_t ld, int passes = 2) {
   if (!c.dry) c.check(launch_householder(Y, m, K, ld, c.st, false, c.s));
 }
 
-// Leading R eigenvectors (K x R) of the Gram of a tall matrix Bt (m x K, ld)
 // Leading dimension of the small K x R factor Ub: a multiple of 4 so that the
 // tensor-core TTMs can stream it with TMA.
 inline int ldu_of(int K) { return (K + 3) & ~3; }
 
+// Leading R eigenvectors (K x R) of the Gram of a tall matrix Bt (m x K, ld)
 void op_truncate(Ctx& c, const float* Bt, int64_t m, int K, int64_t ld, int R, float* Ub) {
   Scope sc(c);
   double* G = c.take<double>((size_t)K * K);
