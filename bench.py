@@ -10,6 +10,11 @@ needed between steps.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
 on the host cores instead (the comparison arm of this project).
+``--serve N`` runs the serving loop (paper_2001_07124_gb300/serving.py) on N
+Poisson-arriving requests (200 req/s; cubic sizes log-uniform in [64, 768] on
+multiples of 64; ranks uniform in 8..64; R-STHOSVD p = 10, q = 1; 150 GB device
+budget) with 4 slots and, for comparison, with 1 slot; its JSON line reports
+p50/p99 latency and decomps/s (not the benchmark line).
 ``--primitive sketch|power|orth`` times one C-ABI primitive on the workload's
 mode-1 shapes instead (a kernel micro-benchmark for profiling; its line is not
 the benchmark line): sketch = rhosvd_sketch(X, mode 1, Omega_1), power =
@@ -167,6 +172,50 @@ def run_reference(args, w, rank):
     print(json.dumps(line), flush=True)
 
 
+def run_serving(args):
+    """Poisson request stream through the serving loop, 4 slots vs 1 slot."""
+    import torch
+    import paper_2001_07124_gb300 as pkg
+    from paper_2001_07124_gb300 import serving
+    pkg.build()
+    rng = np.random.default_rng(1005)
+    n = args.serve
+    rate = 200.0
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    sizes = np.clip(np.rint(np.exp(rng.uniform(np.log(64), np.log(768), size=n)) / 64) * 64, 64, 768).astype(int)
+    ranks = np.minimum(rng.integers(8, 65, size=n), sizes)
+    # one low-rank-plus-noise tensor per size, drawn on the device and kept in pinned host memory
+    pool = {}
+    g = torch.Generator(device="cuda")
+    for I in sorted(set(sizes.tolist())):
+        g.manual_seed(1005 + I)
+        r = 64
+        core = torch.randn(r, r, r, device="cuda", generator=g)
+        U = [torch.linalg.qr(torch.randn(I, r, device="cuda", generator=g))[0] for _ in range(3)]
+        x = torch.einsum("abc,ia,jb,kc->kji", core, U[0], U[1], U[2])      # (k, j, i): i fastest
+        noise = torch.randn(x.shape, device="cuda", generator=g)
+        x = x + 1e-3 * x.norm() / noise.norm() * noise
+        pool[I] = x.contiguous().reshape(-1).cpu().pin_memory()
+        del x, noise, core, U
+    torch.cuda.empty_cache()
+
+    def requests():
+        return [serving.Request(i, (int(sizes[i]),) * 3, (int(ranks[i]),) * 3, float(arrivals[i]),
+                                x_host=pool[int(sizes[i])], p=10, q=1, seed=i) for i in range(n)]
+
+    # warm-up: every size once, so per-kernel attributes and caches are settled
+    serving.serve([serving.Request(i, (I,) * 3, (8,) * 3, 0.0, x_host=pool[I], p=10, q=1)
+                   for i, I in enumerate(sorted(pool))], slots=1)
+    line = {"mode": "serve", "requests": n, "arrival_rate_per_s": rate,
+            "sizes": "cubic, log-uniform in [64, 768], multiples of 64", "ranks": "uniform 8..64",
+            "algo": "rsthosvd p=10 q=1 (fixed rank)", "budget_gb": 150,
+            "note": "fixed-accuracy (adaptive range finder) requests not implemented"}
+    for slots in (4, 1):
+        res = serving.serve(requests(), slots=slots, budget_bytes=150 * 10 ** 9)
+        line[f"slots{slots}"] = serving.latency_summary(res)
+    print(json.dumps(line), flush=True)
+
+
 def run_primitive(args, w):
     """Time one primitive on the workload's mode-1 shapes (device-drawn inputs)."""
     import torch
@@ -216,6 +265,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--primitive", choices=["sketch", "power", "orth"], default=None)
     ap.add_argument("--no-graph", action="store_true", help="launch the decomposition kernel by kernel")
+    ap.add_argument("--serve", type=int, default=0, metavar="N", help="serving run with N requests")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -228,6 +278,8 @@ def main():
         return run_reference(args, w, rank)
     if args.primitive is not None:
         return run_primitive(args, w)
+    if args.serve > 0:
+        return run_serving(args)
 
     import torch
     import paper_2001_07124_gb300 as pkg
@@ -303,26 +355,54 @@ def main():
     value = world * args.steps / (elapsed_ms / 1e3)
 
     # ---------------------------------------------------------------- e2e through host buffers
-    g_host = torch.empty(G.numel(), dtype=torch.float32).pin_memory()
-    u_host = [torch.empty(u.numel(), dtype=torch.float32).pin_memory() for u in Us]
+    # Every step copies its tensor from pinned host memory and reads its factors and
+    # core back.  Two device inputs alternate: step i's host-to-device copy runs on a
+    # copy stream while step i-1 computes (the usual double buffering a caller does).
     xh = x_host.pin_memory()
-    Xd = X
+    nbuf = 2
+    Xb = [X] + [torch.empty_like(X) for _ in range(nbuf - 1)]
+    outs = [out] + [(R.empty_colmajor(ranks), [R.empty_colmajor((dims[n], ranks[n])) for n in range(len(dims))])
+                    for _ in range(nbuf - 1)]
+    wss = [ws] + [R.Workspace(ws.nbytes) for _ in range(nbuf - 1)]
+    if args.no_graph:
+        runs = [(lambda b=b: R.rhosvd_decompose(Xb[b], dims, ranks, ws=wss[b], out=outs[b], check=False, **kw))
+                for b in range(nbuf)]
+    else:
+        gs = [graph] + [R.DecomposeGraph(Xb[b], dims, ranks, ws=wss[b], out=outs[b], warmup=1, **kw)
+                        for b in range(1, nbuf)]
+        runs = [g.replay for g in gs]
+    host_out = [(torch.empty(G.numel(), dtype=torch.float32).pin_memory(),
+                 [torch.empty(u.numel(), dtype=torch.float32).pin_memory() for u in Us]) for _ in range(nbuf)]
+    copy_stream = torch.cuda.Stream()
+    h2d_done = [torch.cuda.Event() for _ in range(nbuf)]
+    buf_free = [torch.cuda.Event() for _ in range(nbuf)]
+    for e in buf_free:
+        e.record(stream)
 
-    def e2e_step():
-        Xd.copy_(xh, non_blocking=True)
-        step()
-        g_host.copy_(G, non_blocking=True)
-        for a, b in zip(u_host, Us):
-            a.copy_(b, non_blocking=True)
+    def e2e_step(i):
+        b = i % nbuf
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(buf_free[b])          # step i - nbuf has finished with this buffer
+            Xb[b].copy_(xh, non_blocking=True)
+            h2d_done[b].record(copy_stream)
+        stream.wait_event(h2d_done[b])
+        runs[b]()
+        gh, uh = host_out[b]
+        gd, ud = outs[b]
+        gh.copy_(gd, non_blocking=True)
+        for a, c in zip(uh, ud):
+            a.copy_(c, non_blocking=True)
+        buf_free[b].record(stream)
 
     e2e_steps = max(3, min(args.steps, 50))
-    for _ in range(2):
-        e2e_step()
+    for i in range(2 * nbuf):
+        e2e_step(i)
     barrier()
     torch.cuda.synchronize()
     ev0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
+    for i in range(e2e_steps):
+        e2e_step(i)
+    stream.wait_stream(copy_stream)
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -393,7 +473,7 @@ def main():
                        "launch": "eager" if args.no_graph else "cuda_graph"},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": e2e_steps},
+                    "steps": e2e_steps, "overlap": "double-buffered: step i's H2D copy runs during step i-1"},
             "gpu_launches": launches * args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,
