@@ -415,6 +415,74 @@ class DecomposeGraph:
                                              for n in range(len(self.dims))]
 
 
+class BatchGraph:
+    """Many independent decompositions in one CUDA graph.
+
+    items: list of (X, dims, ranks) with X a column-major device tensor; each
+    item gets its own workspace and output buffers.  The items are spread over
+    ``branches`` parallel branches of the graph (item i on branch i % branches),
+    so the GPU overlaps independent decompositions; ``replay()`` runs the whole
+    batch with one launch.  ``results()`` returns (G, [U_n]) views per item."""
+
+    def __init__(self, items, branches=16, warmup=1, **kw):
+        import torch
+        self.items = []
+        for X, dims, ranks in items:
+            X = colmajor(X, dims)
+            N = len(dims)
+            out = (empty_colmajor(ranks), [empty_colmajor((dims[n], ranks[n])) for n in range(N)])
+            shape, opts = make_shape(dims), make_opts(kw.get("algo", "rsthosvd"), kw.get("p", 10),
+                                                     kw.get("q", 1), kw.get("seed", 0), kw.get("K"), kw.get("S"))
+            need = int(lib().rhosvd_workspace_size(ctypes.byref(shape), _i32(ranks), ctypes.byref(opts)))
+            if need == 0:
+                _check(1, "rhosvd_workspace_size")
+            self.items.append((X, tuple(dims), tuple(ranks), Workspace(need), out))
+        self.kw = kw
+        nb = max(1, min(int(branches), len(self.items)))
+        self.streams = [torch.cuda.Stream() for _ in range(nb)]
+        cur = torch.cuda.current_stream()
+        for s in self.streams:
+            s.wait_stream(cur)
+        for _ in range(warmup):
+            self._enqueue()
+        for s in self.streams:
+            cur.wait_stream(s)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            cap = torch.cuda.current_stream()
+            fork = torch.cuda.Event()
+            fork.record(cap)
+            for s in self.streams:
+                s.wait_event(fork)
+            self._enqueue()
+            for s in self.streams:
+                done = torch.cuda.Event()
+                done.record(s)
+                cap.wait_event(done)
+
+    def _enqueue(self):
+        for i, (X, dims, ranks, ws, out) in enumerate(self.items):
+            rhosvd_decompose(X, dims, ranks, ws=ws, out=out, check=False, stream=self.streams[i % len(self.streams)],
+                             **self.kw)
+
+    def replay(self):
+        self.graph.replay()
+
+    def results(self):
+        res = []
+        for X, dims, ranks, ws, (G, Us) in self.items:
+            res.append((fortran_view(G, ranks), [matrix(Us[n], dims[n], ranks[n]) for n in range(len(dims))]))
+        return res
+
+    def device_status(self):
+        """Worst device status over the items (synchronises)."""
+        worst = 0
+        for X, dims, ranks, ws, out in self.items:
+            code, _ = rhosvd_device_status(ws)
+            worst = worst or code
+        return worst
+
+
 def rhosvd_device_status(ws, stream=None):
     flags = ctypes.c_int32(0)
     code = lib().rhosvd_device_status(ws.ptr, ws.nbytes, _stream(stream), ctypes.byref(flags))

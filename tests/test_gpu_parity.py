@@ -445,6 +445,27 @@ def test_decompose_graph_replay_matches_eager():
             np.testing.assert_array_equal(a, host(b))
 
 
+def test_batch_graph_matches_eager():
+    """Independent decompositions captured on parallel branches of one CUDA graph
+    give bitwise the eager per-tensor results."""
+    rng = np.random.default_rng(71)
+    items, eager = [], []
+    for b in range(12):
+        dims = tuple(int(v) for v in rng.integers(16, 70, size=3))
+        ranks = tuple(int(min(r, d)) for r, d in zip(rng.integers(4, 12, size=3), dims))
+        x = lowrank_tensor(dims, ranks, 700 + b, noise=1e-3)
+        items.append((dev(x), dims, ranks))
+    batch = R().BatchGraph(items, branches=4, p=5, q=1, seed=5)
+    batch.replay()
+    torch.cuda.synchronize()
+    assert batch.device_status() == 0
+    for (g_b, u_b), (X, dims, ranks) in zip(batch.results(), items):
+        g_e, u_e = R().rhosvd_decompose(X, dims, ranks, p=5, q=1, seed=5)
+        np.testing.assert_array_equal(host(g_b), host(g_e))
+        for a, c in zip(u_b, u_e):
+            np.testing.assert_array_equal(host(a), host(c))
+
+
 def test_device_status_cleared_between_calls():
     rh = R()
     dims, ranks = (20, 21, 22), (3, 3, 3)
