@@ -50,7 +50,24 @@ sys.path.insert(0, ROOT)
 
 from workloads import WORKLOADS, device_layout  # noqa: E402
 
-METRIC = "decomps/s (R-STHOSVD 512^3 FP32, rank 32, p=10, q=1)"
+_ALGO_NAMES = {"rhosvd": "RP-HOSVD", "rsthosvd": "R-STHOSVD", "rpet": "R-PET"}
+
+
+def _l2_note(w) -> str:
+    mib = 4 * int(np.prod(w.dims)) / 2 ** 20
+    if mib * 2 ** 20 > 129e6:
+        return f"input {mib:.0f} MiB > 129 MB L2"
+    return f"input {mib:.1f} MiB fits in L2 (not flushed)"
+
+
+def metric_name(w) -> str:
+    """Metric label of a workload, e.g. decomps/s (R-STHOSVD 512^3 FP32, rank 32, p=10, q=1)."""
+    d = w.dims
+    shape = f"{d[0]}^{len(d)}" if len(set(d)) == 1 else "x".join(str(v) for v in d)
+    r = w.ranks
+    rank = str(r[0]) if len(set(r)) == 1 else "(" + ",".join(str(v) for v in r) + ")"
+    par = f"K={w.K[0]}, S={w.S[0]}" if w.algo == "rpet" and w.K else f"p={w.p}, q={w.q}"
+    return f"decomps/s ({_ALGO_NAMES[w.algo]} {shape} FP32, rank {rank}, {par})"
 UNIT = "decomps/s"
 
 
@@ -164,12 +181,12 @@ def run_reference(args, w, rank):
     total = sum(times)
     value = args.steps / total
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": metric_name(w), "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded low-rank tensor, seeded Philox test matrices)",
         "config": {"workload": w.name, "dims": list(w.dims), "ranks": list(w.ranks), "p": w.p, "q": w.q,
-                   "algo": w.algo, "l2_flush": "input 512 MiB > L2"},
+                   "algo": w.algo, "l2_flush": _l2_note(w)},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": _CORES, "kind": "oracle",
                          "sample": f"full workload, {args.steps} decompositions"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -519,7 +536,7 @@ def main():
                 "achieved": round(sk_gbs, 1), "peak": hbm_peak, "unit": "GB/s", "frac": round(sk_gbs / hbm_peak, 4),
                 "peak_source": peak_src, "algorithmic_bytes_per_launch": sk_bytes, "ms_per_launch": sk_ms,
                 "traffic": _traffic_for(os.path.join(ROOT, "paper_2001_07124_gb300", "csrc", "tc_sketch.cu"),
-                                        "tc_sketch_mode1_512")}
+                                        f"tc_sketch_mode1:{w.name}")}
 
     # ---------------------------------------------------------------- CPU oracle and error gate
     cpu = None
@@ -535,17 +552,17 @@ def main():
         accuracy = {"E_gpu": e_gpu, "E_oracle": e_or, "max_principal_sine": sine,
                     "pass": bool(abs(e_gpu - e_or) <= 1e-5 and sine <= 1e-4)}
         cpu = {"value": 1.0 / t_or, "unit": UNIT, "cores": _CORES, "kind": "oracle",
-               "sample": "one full 512^3 R-STHOSVD decomposition in FP64 NumPy (seeded Philox test matrices)"}
+               "sample": f"one full decomposition of the {w.name} workload in FP64 NumPy (seeded Philox test matrices)"}
 
     launches = R.rhosvd_launch_count(dims, ranks, w.algo, w.p, w.q, K=w.K, S=w.S)
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "metric": metric_name(w), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded low-rank tensor, device-drawn Philox test matrices)",
             "config": {"workload": w.name, "dims": list(dims), "ranks": list(ranks), "algo": w.algo, "p": w.p,
-                       "q": w.q, "parallelism": f"replicas{world}", "l2_flush": "input 512 MiB > 129 MB L2",
+                       "q": w.q, "parallelism": f"replicas{world}", "l2_flush": _l2_note(w),
                        "launch": "eager" if args.no_graph else "cuda_graph"},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -379,24 +379,30 @@ void run_rhosvd(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, con
 // Core sketch chain H = X x_1 Omega~_1 ... x_N Omega~_N (Alg. 9 line 3).
 void core_sketch_chain(Ctx& c, const float* X, const Geom& g, const int* S, uint64_t seed,
                        const float* const* Om_t, float* const* om_t_buf, float* H) {
-  size_t max_t = 1;
+  size_t max_t = 1, max_m = 1;
   {
     Geom t = g;
     for (int n = 0; n < g.N; ++n) {
       t.d[n] = S[n];
       max_t = std::max<size_t>(max_t, (size_t)t.numel());
+      max_m = std::max<size_t>(max_m, (size_t)g.d[n] * S[n]);
     }
   }
   Scope sc(c);
   float* Tb[2] = {c.take<float>(max_t), c.take<float>(max_t)};
+  float* Mt = c.take<float>(max_m);                   // Omega~_n^T, I_n x S_n column-major
   Geom t = g;
   const float* cur = X;
   int ping = 0;
+  (void)seed;
   for (int n = 0; n < g.N; ++n) {
     const float* om = (Om_t != nullptr && Om_t[n] != nullptr) ? Om_t[n] : om_t_buf[n];
     float* dst = (n == g.N - 1) ? H : Tb[ping];
-    // M(i, s) = Omega~(s, i) at om[s + i*S]
-    ttm_mode(c, cur, t, n, om, S[n], 1, S[n], dst);
+    // the TTM takes M(i, s) = Omega~(s, i) column-major (I_n x S_n), the layout the
+    // tensor-core kernel streams with TMA
+    c.launches += 1;
+    if (!c.dry) c.check(launch_transpose(om, S[n], g.d[n], S[n], Mt, c.s));
+    ttm_mode(c, cur, t, n, Mt, 1, g.d[n], S[n], dst);
     t.d[n] = S[n];
     cur = dst;
     ping ^= 1;

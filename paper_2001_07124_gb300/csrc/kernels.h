@@ -133,6 +133,9 @@ cudaError_t launch_small_eig(const double* G, int K, int R, float* Ub, int ldu, 
                              cudaStream_t stream);
 
 // ---- misc
+// out (cols x rows, column-major) = in^T for a small rows x cols matrix (ld).
+cudaError_t launch_transpose(const float* in, int64_t rows, int64_t cols, int64_t ld, float* out,
+                             cudaStream_t st);
 cudaError_t launch_fill_identity(float* U, int64_t I, int R, cudaStream_t st);
 
 }  // namespace rhosvd

@@ -23,6 +23,15 @@ __global__ void omega_kernel(uint64_t seed, uint32_t stream_id, int64_t rows, in
   }
 }
 
+// out (cols x rows, column-major) = in^T, in rows x cols with leading dimension ld
+__global__ void transpose_kernel(const float* __restrict__ in, int64_t rows, int64_t cols, int64_t ld,
+                                 float* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  const int64_t c = e / rows, r = e - c * rows;      // read in column order (coalesced)
+  out[c + r * cols] = in[r + c * ld];
+}
+
 __global__ void fill_identity_kernel(float* U, int64_t I, int R) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= I * R) return;
@@ -37,6 +46,14 @@ cudaError_t launch_omega(uint64_t seed, uint32_t stream_id, int64_t rows, int co
   if (rows == 0 || cols == 0) return cudaSuccess;
   dim3 grid((unsigned)((rows + 255) / 256), (unsigned)((cols + 3) / 4));
   omega_kernel<<<grid, 256, 0, st>>>(seed, stream_id, rows, cols, out, ld);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_transpose(const float* in, int64_t rows, int64_t cols, int64_t ld, float* out,
+                             cudaStream_t st) {
+  const int64_t n = rows * cols;
+  if (n == 0) return cudaSuccess;
+  transpose_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, rows, cols, ld, out);
   return cudaGetLastError();
 }
 

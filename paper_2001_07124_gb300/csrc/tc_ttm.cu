@@ -27,8 +27,10 @@
 //   * warps 8-11 (epilogue): read a finished accumulator (tcgen05.ld), write
 //     the rows of Out, and hand the buffer back while the next tile computes.
 // Requirements (checked by tc_ttm_supported): 16-byte aligned X and M, strides
-// multiple of 4 elements, ldm % 4 == 0, K <= 64; a strided view needs
-// L % 128 == 0 or L in {32, 64} (Rt = 1: any L >= 128).
+// multiple of 4 elements, ldm % 4 == 0, K <= 64, L % 4 == 0.  When 128
+// consecutive j would straddle r (L not a multiple of 128, not 32 or 64, and
+// Rt > 1) the tiles are laid out per r: ceil(L / 128) tiles of 128 l for each
+// r, the rows past L zero-filled by TMA and not written.
 #include <algorithm>
 
 #include "common.cuh"
@@ -74,14 +76,16 @@ struct __align__(1024) TtmSmem {
 template <int NPAD, bool M1>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmM, int I,
-              int64_t L, int64_t J, int bl_bits, int K, float* __restrict__ out, int64_t o_k, int64_t o_r,
-              int64_t o_L, const DevStatus* skip, DevStatus* st) {
+              int64_t L, int64_t J, int bl_bits, int tpr, int K, float* __restrict__ out, int64_t o_k,
+              int64_t o_r, int64_t o_L, const DevStatus* skip, DevStatus* st) {
   if (skip != nullptr && skip->orth_fail) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   TtmSmem& sm = *reinterpret_cast<TtmSmem*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int ntiles = (int)((J + TILE_J - 1) / TILE_J);
+  // tpr > 0: tiles never straddle r (tpr tiles of 128 l per r, rows l >= L are
+  // zero-filled by TMA and not written); tpr == 0: tiles of 128 consecutive j
+  const int ntiles = tpr > 0 ? (int)(tpr * (J / L)) : (int)((J + TILE_J - 1) / TILE_J);
   const int nst = (I + BI - 1) / BI;                  // stages per tile
   constexpr uint32_t idesc = idesc_tf32(128, NPAD);
 
@@ -127,6 +131,8 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         mbar_arrive_expect_tx(&sm.full_x[s], bytes);
         if (M1) {
           tma_load_2d(sm.x[s], &tmX, ib, tile * TILE_J, &sm.full_x[s]);
+        } else if (tpr > 0) {
+          tma_load_3d(sm.x[s], &tmX, (tile % tpr) * TILE_J, ib, tile / tpr, &sm.full_x[s]);
         } else {
           const int64_t j0 = (int64_t)tile * TILE_J, r0 = j0 / L;
           tma_load_3d(sm.x[s], &tmX, (int)(j0 - r0 * L), ib, (int)r0, &sm.full_x[s]);
@@ -227,10 +233,14 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       if (!mbar_wait(&sm.d_full[buf], (uint32_t)(tl >> 1) & 1u, abort_flag)) { ok = false; break; }
       tc_fence_after();
       const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
-      const int64_t j = (int64_t)tile * TILE_J + quad * 32 + lane;
+      int64_t j = (int64_t)tile * TILE_J + quad * 32 + lane;
+      if (tpr > 0) {                                   // row l of this r's tile; l >= L is padding
+        const int64_t l = (int64_t)(tile % tpr) * TILE_J + quad * 32 + lane;
+        j = (l < L) ? l + L * (int64_t)(tile / tpr) : J;
+      }
       const int64_t rj = j / o_L;
       float* orow = out + (j - rj * o_L) + rj * o_r;
-      if (o_k == 1 && o_L == 1) {
+      if (o_k == 1 && o_L == 1 && tpr == 0) {
         // rows of the output are contiguous in k (row j at out + j*o_r): stage 32 rows x
         // 16 columns per warp and store two 64-byte row segments per instruction
         float* stg = sm.ostage[quad];
@@ -282,49 +292,56 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 }
 
 // ---------------------------------------------------------------- host side
-// Tile geometry of a strided view: BL = l per tile row block, 0 if unsupported.
-int strided_bl(const View& x) {
-  if (x.L < 32) return 0;
-  if (x.Rt == 1) return x.L >= 128 ? 128 : 0;
+// Tile geometry of a strided view: BL = l per tile row block (0 if unsupported),
+// and whether tiles are laid out per r (tpr = ceil(L / 128) tiles of 128 l for
+// each r, the last one partial) because 128 consecutive j would straddle r.
+int strided_bl(const View& x, int* tpr) {
+  *tpr = 0;
+  if (x.L < 4 || x.L % 4 != 0) return 0;
+  if (x.Rt == 1 && x.L >= 128) return 128;
   if (x.L % 128 == 0) return 128;
-  return (x.L == 32 || x.L == 64) ? (int)x.L : 0;
+  if (x.L == 32 || x.L == 64) return (int)x.L;
+  *tpr = (int)((x.L + TILE_J - 1) / TILE_J);
+  return 128;
 }
 
 template <int NPAD, bool M1>
 cudaError_t launch_npad(const CUtensorMap& tmX, const CUtensorMap& tmM, int I, int64_t L, int64_t J, int bl_bits,
-                        int K, const OView& out, const DevStatus* skip, DevStatus* st, cudaStream_t stream) {
+                        int tpr, int K, const OView& out, const DevStatus* skip, DevStatus* st, cudaStream_t stream) {
   const size_t smem = sizeof(TtmSmem) + 1024;
   cudaError_t e = allow_dynamic_smem((const void*)tc_ttm_kernel<NPAD, M1>, smem);
   if (e != cudaSuccess) return e;
-  const int ntiles = (int)((J + TILE_J - 1) / TILE_J);
+  const int ntiles = tpr > 0 ? (int)(tpr * (J / L)) : (int)((J + TILE_J - 1) / TILE_J);
   const int grid = std::min(ntiles, device_sms());
   const int64_t o_L = out.o_L > 0 ? out.o_L : L;
-  tc_ttm_kernel<NPAD, M1><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmM, I, L, J, bl_bits, K, out.p, out.o_k,
-                                                                out.o_r, o_L, skip, st);
+  tc_ttm_kernel<NPAD, M1><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmM, I, L, J, bl_bits, tpr, K, out.p,
+                                                                out.o_k, out.o_r, o_L, skip, st);
   return cudaGetLastError();
 }
 
 template <bool M1>
 cudaError_t launch_m(const CUtensorMap& tmX, const CUtensorMap& tmM, int I, int64_t L, int64_t J, int bl_bits,
-                     int K, const OView& out, const DevStatus* skip, DevStatus* st, cudaStream_t stream) {
+                     int tpr, int K, const OView& out, const DevStatus* skip, DevStatus* st, cudaStream_t stream) {
   switch (((K + 15) / 16) * 16) {
-    case 16: return launch_npad<16, M1>(tmX, tmM, I, L, J, bl_bits, K, out, skip, st, stream);
-    case 32: return launch_npad<32, M1>(tmX, tmM, I, L, J, bl_bits, K, out, skip, st, stream);
-    case 48: return launch_npad<48, M1>(tmX, tmM, I, L, J, bl_bits, K, out, skip, st, stream);
-    default: return launch_npad<64, M1>(tmX, tmM, I, L, J, bl_bits, K, out, skip, st, stream);
+    case 16: return launch_npad<16, M1>(tmX, tmM, I, L, J, bl_bits, tpr, K, out, skip, st, stream);
+    case 32: return launch_npad<32, M1>(tmX, tmM, I, L, J, bl_bits, tpr, K, out, skip, st, stream);
+    case 48: return launch_npad<48, M1>(tmX, tmM, I, L, J, bl_bits, tpr, K, out, skip, st, stream);
+    default: return launch_npad<64, M1>(tmX, tmM, I, L, J, bl_bits, tpr, K, out, skip, st, stream);
   }
 }
 
 }  // namespace
 
 bool tc_ttm_supported(const View& x, int64_t m_i, int64_t m_k, int K, const OView& out) {
-  (void)out;
   if (m_i != 1 || m_k < x.I || m_k % 4 != 0) return false;     // M column-major, ld multiple of 4
   if (K < 1 || K > 64 || x.I < 1 || x.I > (int64_t(1) << 30)) return false;
   const int64_t J = x.L * x.Rt;
   if (J < TILE_J || J > (int64_t(1) << 40)) return false;
   if (x.L == 1) return x.s_i == 1 && x.s_r == x.I && x.I % 4 == 0;   // X(i, j) = X[i + I*j]
-  if (strided_bl(x) == 0 || x.s_i % 4 != 0 || (x.Rt > 1 && x.s_r % 4 != 0)) return false;
+  int tpr = 0;
+  if (strided_bl(x, &tpr) == 0 || x.s_i % 4 != 0 || (x.Rt > 1 && x.s_r % 4 != 0)) return false;
+  if (tpr > 0 && out.o_L > 0 && out.o_L != x.L) return false;     // per-r tiles split j by the input's L
+  if (tpr > 0 && (int64_t)tpr * x.Rt >= (int64_t(1) << 31)) return false;
   return x.Rt < (int64_t(1) << 31) && x.L < (int64_t(1) << 31);
 }
 
@@ -344,9 +361,10 @@ cudaError_t launch_tc_ttm(const View& x, const float* Mp, int64_t m_k, int K, co
     const uint64_t strides[1] = {(uint64_t)I};
     const uint32_t box[2] = {BI, TILE_J};
     if (!make_tmap_f32(&tmX, x.p, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorNotSupported;
-    return launch_m<true>(tmX, tmM, (int)I, 1, J, 0, K, out, skip, st, stream);
+    return launch_m<true>(tmX, tmM, (int)I, 1, J, 0, 0, K, out, skip, st, stream);
   }
-  const int bl = strided_bl(x);
+  int tpr = 0;
+  const int bl = strided_bl(x, &tpr);
   if (bl == 0) return cudaErrorNotSupported;
   int bits = 0;
   while ((1 << bits) < bl) ++bits;
@@ -356,7 +374,7 @@ cudaError_t launch_tc_ttm(const View& x, const float* Mp, int64_t m_k, int K, co
   const uint32_t box[3] = {(uint32_t)bl, BI, (uint32_t)(TILE_J / bl)};
   const bool okmap = make_tmap_f32(&tmX, x.p, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE);
   if (!okmap) return cudaErrorNotSupported;
-  return launch_m<false>(tmX, tmM, (int)I, x.L, J, bits, K, out, skip, st, stream);
+  return launch_m<false>(tmX, tmM, (int)I, x.L, J, bits, tpr, K, out, skip, st, stream);
 }
 
 }  // namespace rhosvd

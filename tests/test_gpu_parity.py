@@ -184,12 +184,16 @@ def test_tc_ttm_mode1_parity(dims, K):
     assert_close_abs(G, want, bound)
 
 
-# Strided unfoldings (L >= 32) on the tcgen05 TTM kernel through 3-D TMA boxes:
+# Strided unfoldings on the tcgen05 TTM kernel through 3-D TMA boxes:
 # L = 32 / 64 (several r per 128-row tile, partial last tile), L % 128 == 0,
-# L >= 128 with Rt == 1, a contraction shorter than one 32-wide stage, 4-way.
+# L >= 128 with Rt == 1, a contraction shorter than one 32-wide stage, 4-way,
+# and per-r tiles for other L (padding rows past L).
 TC_TTM_STRIDED_CASES = [((64, 96, 50), 1, 42), ((32, 48, 30), 1, 16), ((256, 40, 30), 1, 33),
                         ((32, 32, 200), 2, 64), ((32, 40, 5), 1, 20), ((16, 8, 64, 12), 2, 24),
-                        ((128, 8, 7), 1, 5)]
+                        ((128, 8, 7), 1, 5),
+                        # per-r tiles (128 consecutive j would straddle r): L = 40, 200, 720, 12
+                        ((40, 96, 12), 1, 40), ((200, 64, 5), 1, 26), ((36, 20, 40, 3), 2, 33),
+                        ((12, 16, 30), 1, 9)]
 
 
 @pytest.mark.parametrize("dims,mode,K", TC_TTM_STRIDED_CASES)
