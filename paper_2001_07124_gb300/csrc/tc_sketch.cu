@@ -6,6 +6,9 @@
 //   * strided (L % 16 == 0): 3-D boxes {16 l, 256 i, 1 r} over [L, I, Rt] with
 //     64-byte swizzle, smem [i][16 l], each lane reading its own 64-byte row as
 //     four float4 (16-byte chunk c of row i sits at chunk c ^ ((i >> 1) & 3)).
+// Short modes (I <= 128) stage 64 j x 128 rows instead (four 16-j chunks of
+// one MMA tile, mode-1 box {128 i, 64 j}, strided boxes {16 l, 128 i, 1 r} per
+// chunk), so that every stage still moves 32 KB of X.
 //
 // The contraction over j is split over CTAs (one CTA per SM, persistent); each
 // CTA owns up to 512 rows i (four 128-row MMA tiles) and a contiguous range of
@@ -38,24 +41,36 @@ namespace {
 
 using namespace tc;
 
-constexpr int BJ = 16;                    // j per stage (two tf32 MMA K steps of 8)
-constexpr int X_STAGES = 5;
+constexpr int BJ = 16;                    // j per MMA chunk (two tf32 MMA K steps of 8)
 constexpr int A_STAGES = 2;
-constexpr int ROWS = 512;                 // rows i per CTA (4 MMA tiles)
-constexpr int BOXW = 256;                 // TMA box width in i
 constexpr int NUM_XFORM = 256;            // warps 0-7
 constexpr int NUM_THREADS = NUM_XFORM + 64;   // + warp 8 producer, warp 9 MMA issuer
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int D_COLS = 64;                // accumulator columns reserved per tile
 constexpr int A_COL0 = 4 * D_COLS;        // first TMEM column of the A stages
-constexpr int A_STAGE_COLS = 128;         // per stage: 4 tiles x (16 hi + 16 lo)
+constexpr int A_STAGE_COLS = 128;         // per stage: 4 slots x (16 hi + 16 lo)
 constexpr int B_TILE = 64 * BJ;           // floats per B tile (N <= 64)
+constexpr int STAGE_FLOATS = 8192;        // X floats per stage (32 KB)
 
+// Stage geometry, NC = chunks of 16 j per stage: NC = 1 stages 16 j x 512 rows
+// (four 128-row MMA tiles), NC = 4 stages 64 j x 128 rows (one tile, four
+// chunks) for short modes (I <= 128).  The four TMEM A slots of a stage hold
+// tiles (NC = 1) or chunks (NC = 4).
+template <int NC>
+struct Geo {
+  static constexpr int ROWS = 512 / NC;                   // rows i per CTA
+  static constexpr int SBJ = BJ * NC;                     // j per stage
+  static constexpr int BOXW = ROWS < 256 ? ROWS : 256;    // rows per TMA box
+  static constexpr int X_STAGES = NC == 1 ? 5 : 3;
+};
+
+template <int NC>
 struct __align__(1024) SketchSmem {
-  float x[X_STAGES][ROWS / BOXW][BJ * BOXW];   // TMA boxes: mode 1 [box][jj][256], strided [box][i][16]
-  float wraw[X_STAGES][B_TILE];                // TMA box [n][jj] (64B swizzle), rows n >= K are zero-filled
-  float b[A_STAGES][2][B_TILE];                // hi / lo B tiles, canonical K-major layout
-  uint64_t full_x[X_STAGES], empty_x[X_STAGES];
+  // mode 1: boxes [box][jj][BOXW]; strided: boxes [box][i][16] (NC = 1: row boxes, NC = 4: chunk boxes)
+  float x[Geo<NC>::X_STAGES][STAGE_FLOATS];
+  float wraw[Geo<NC>::X_STAGES][NC][B_TILE];   // TMA boxes [n][jj] (64B swizzle), rows n >= K zero-filled
+  float b[A_STAGES][2][NC][B_TILE];            // hi / lo B tiles, canonical K-major layout
+  uint64_t full_x[Geo<NC>::X_STAGES], empty_x[Geo<NC>::X_STAGES];
   uint64_t full_a[A_STAGES], empty_a[A_STAGES];
   uint64_t done;
   uint32_t tmem_base;
@@ -67,22 +82,25 @@ struct __align__(1024) SketchSmem {
 // 8-row x 16-byte core matrices with LBO = 128 (K direction) and SBO = 512
 // (N direction); the second MMA K step starts 256 bytes in.
 
-template <int NPAD, bool M1>
+template <int NPAD, bool M1, int NC>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, int I,
                  int64_t L, int64_t J, int K, int64_t jchunk, float* __restrict__ part, DevStatus* st) {
+  using G = Geo<NC>;
+  constexpr int X_STAGES = G::X_STAGES, ROWS = G::ROWS, SBJ = G::SBJ, BOXW = G::BOXW;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  SketchSmem& sm = *reinterpret_cast<SketchSmem*>(
+  SketchSmem<NC>& sm = *reinterpret_cast<SketchSmem<NC>*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int split = blockIdx.x;
   const int i0 = blockIdx.y * ROWS;
   const int rows = min(ROWS, I - i0);
   const int mt = (rows + 127) / 128;                 // MMA tiles in this CTA
-  const int nbox = (rows + BOXW - 1) / BOXW;
+  const int nslot = NC == 1 ? mt : NC;               // occupied A slots per stage
+  const int nbox = M1 ? (rows + BOXW - 1) / BOXW : (NC == 1 ? (rows + BOXW - 1) / BOXW : NC);
   const int64_t jb = (int64_t)split * jchunk;
   const int64_t je = min(J, jb + jchunk);
-  const int nkb = (int)((je - jb + BJ - 1) / BJ);
+  const int nkb = (int)((je - jb + SBJ - 1) / SBJ);
   constexpr uint32_t idesc = idesc_tf32(128, NPAD);
 
   if (tid == 0) {
@@ -112,22 +130,27 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
   if (warp == 8) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      const uint32_t bytes = (uint32_t)(nbox * BJ * BOXW * 4 + B_TILE * 4);
+      const uint32_t box_bytes = M1 ? (uint32_t)(SBJ * BOXW * 4) : (uint32_t)(BJ * BOXW * 4);
+      const uint32_t bytes = (uint32_t)nbox * box_bytes + (uint32_t)(NC * B_TILE * 4);
       for (int kb = 0; kb < nkb && ok; ++kb) {
         const int s = kb % X_STAGES;
         const uint32_t ph = (uint32_t)(kb / X_STAGES) & 1u;
         if (!mbar_wait(&sm.empty_x[s], ph ^ 1u, abort_flag)) { ok = false; break; }
         mbar_arrive_expect_tx(&sm.full_x[s], bytes);
-        const int jt = (int)(jb + (int64_t)kb * BJ);
+        const int jt = (int)(jb + (int64_t)kb * SBJ);
         if (M1) {
-          for (int bx = 0; bx < nbox; ++bx) tma_load_2d(sm.x[s][bx], &tmX, i0 + bx * BOXW, jt, &sm.full_x[s]);
+          for (int bx = 0; bx < nbox; ++bx)
+            tma_load_2d(sm.x[s] + bx * SBJ * BOXW, &tmX, i0 + bx * BOXW, jt, &sm.full_x[s]);
         } else {
           const int64_t rj = (int64_t)jt / L;
           const int lj = (int)((int64_t)jt - rj * L);
-          for (int bx = 0; bx < nbox; ++bx)
-            tma_load_3d(sm.x[s][bx], &tmX, lj, i0 + bx * BOXW, (int)rj, &sm.full_x[s]);
+          for (int bx = 0; bx < nbox; ++bx) {
+            const int li = NC == 1 ? lj : lj + BJ * bx;          // chunk boxes walk l
+            const int ii = NC == 1 ? i0 + bx * BOXW : i0;         // row boxes walk i
+            tma_load_3d(sm.x[s] + bx * BJ * BOXW, &tmX, li, ii, (int)rj, &sm.full_x[s]);
+          }
         }
-        tma_load_2d(sm.wraw[s], &tmW, jt, 0, &sm.full_x[s]);
+        for (int c = 0; c < NC; ++c) tma_load_2d(sm.wraw[s][c], &tmW, jt + BJ * c, 0, &sm.full_x[s]);
       }
     }
   } else if (warp == 9) {
@@ -138,15 +161,16 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
         const uint32_t ph = (uint32_t)(kb / A_STAGES) & 1u;
         if (!mbar_wait(&sm.full_a[a], ph, abort_flag)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t bhi = smem_u32(sm.b[a][0]), blo = smem_u32(sm.b[a][1]);
-        for (int t = 0; t < mt; ++t) {
+        for (int u = 0; u < nslot; ++u) {
+          const int t = NC == 1 ? u : 0, c = NC == 1 ? 0 : u;
           const uint32_t d = tmem + (uint32_t)(t * D_COLS);
-          const uint32_t ahi = tmem + (uint32_t)(A_COL0 + a * A_STAGE_COLS + t * 32);
+          const uint32_t ahi = tmem + (uint32_t)(A_COL0 + a * A_STAGE_COLS + u * 32);
+          const uint32_t bhi = smem_u32(sm.b[a][0][c]), blo = smem_u32(sm.b[a][1][c]);
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
             const uint64_t dbh = smem_desc_kmajor_nosw(bhi + ks * 256, 128, 512);
             const uint64_t dbl = smem_desc_kmajor_nosw(blo + ks * 256, 128, 512);
-            mma_tf32_ts(d, ahi + ks * 8, dbh, idesc, (kb > 0 || ks > 0) ? 1u : 0u);
+            mma_tf32_ts(d, ahi + ks * 8, dbh, idesc, (kb > 0 || c > 0 || ks > 0) ? 1u : 0u);
             mma_tf32_ts(d, ahi + ks * 8, dbl, idesc, 1u);
             mma_tf32_ts(d, ahi + 16 + ks * 8, dbh, idesc, 1u);
           }
@@ -163,37 +187,40 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
     for (int kb = 0; kb < nkb && ok; ++kb) {
       const int s = kb % X_STAGES, a = kb % A_STAGES;
       const uint32_t phx = (uint32_t)(kb / X_STAGES) & 1u, pha = (uint32_t)(kb / A_STAGES) & 1u;
-      const int64_t rem = je - (jb + (int64_t)kb * BJ);
-      const int valid = rem < BJ ? (int)rem : BJ;
+      const int64_t rem = je - (jb + (int64_t)kb * SBJ);
+      const int valid = rem < SBJ ? (int)rem : SBJ;   // valid j of this stage
       if (!mbar_wait(&sm.full_x[s], phx, abort_flag)) { ok = false; break; }
       if (!mbar_wait(&sm.empty_a[a], pha ^ 1u, abort_flag)) { ok = false; break; }
       tc_fence_after();
 #pragma unroll
-      for (int tt = 0; tt < 2; ++tt) {
-        const int t = 2 * wg + tt;
-        if (t < mt) {
+      for (int uu = 0; uu < 2; ++uu) {
+        const int u = 2 * wg + uu;                    // A slot: tile (NC = 1) or chunk (NC = 4)
+        if (u < nslot) {
+          const int t = NC == 1 ? u : 0, c = NC == 1 ? 0 : u;
           const int r = t * 128 + row_in_tile;       // row within the CTA's block
+          const int vc = valid - BJ * c;              // valid j of this chunk (may be <= 0)
           uint32_t hi[16], lo[16];
           if (M1) {
-            const float* xb = sm.x[s][r / BOXW] + (r % BOXW);
+            const float* xb = sm.x[s] + (r / BOXW) * SBJ * BOXW + (r % BOXW) + BJ * c * BOXW;
 #pragma unroll
             for (int jj = 0; jj < BJ; ++jj) {
-              const float v = (jj < valid && r < rows) ? xb[jj * BOXW] : 0.f;
+              const float v = (jj < vc && r < rows) ? xb[jj * BOXW] : 0.f;
               split_tf32(v, hi[jj], lo[jj]);
             }
           } else {
-            const int rr = r % BOXW;
-            const float4* xr = reinterpret_cast<const float4*>(sm.x[s][r / BOXW] + rr * BJ);
+            const int bx = NC == 1 ? r / BOXW : c;
+            const int rr = NC == 1 ? r % BOXW : r;
+            const float4* xr = reinterpret_cast<const float4*>(sm.x[s] + bx * BJ * BOXW + rr * BJ);
 #pragma unroll
-            for (int c = 0; c < BJ / 4; ++c) {
-              float4 v = xr[c ^ ((rr >> 1) & 3)];
+            for (int q = 0; q < BJ / 4; ++q) {
+              float4 v = xr[q ^ ((rr >> 1) & 3)];
               if (r >= rows) v = make_float4(0.f, 0.f, 0.f, 0.f);
               const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-              for (int u = 0; u < 4; ++u) split_tf32((4 * c + u < valid) ? e[u] : 0.f, hi[4 * c + u], lo[4 * c + u]);
+              for (int w = 0; w < 4; ++w) split_tf32((4 * q + w < vc) ? e[w] : 0.f, hi[4 * q + w], lo[4 * q + w]);
             }
           }
-          const uint32_t col = tmem + (uint32_t)(A_COL0 + a * A_STAGE_COLS + t * 32);
+          const uint32_t col = tmem + (uint32_t)(A_COL0 + a * A_STAGE_COLS + u * 32);
           tmem_st_x16(col + lane_base, hi);
           tmem_st_x16(col + 16 + lane_base, lo);
         }
@@ -202,15 +229,20 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
       // canonical layout word by word (conflict-free stores): word w holds
       // n = 8 (w >> 7) + ((w >> 2) & 7), jj = 4 ((w >> 5) & 3) + (w & 3).
 #pragma unroll
-      for (int u = 0; u < NPAD * BJ / NUM_XFORM; ++u) {
-        const int w = tid + u * NUM_XFORM;
-        const int n = 8 * (w >> 7) + ((w >> 2) & 7), jj = 4 * ((w >> 5) & 3) + (w & 3);
-        // raw W tile rows are 64-byte swizzled: 16-byte chunk c of row n sits at c ^ ((n >> 1) & 3)
-        const float v = (jj < valid && n < K) ? sm.wraw[s][n * BJ + (((jj >> 2) ^ ((n >> 1) & 3)) << 2) + (jj & 3)] : 0.f;
-        uint32_t h, l;
-        split_tf32(v, h, l);
-        reinterpret_cast<uint32_t*>(sm.b[a][0])[w] = h;
-        reinterpret_cast<uint32_t*>(sm.b[a][1])[w] = l;
+      for (int c = 0; c < NC; ++c) {
+        const int vc = valid - BJ * c;
+#pragma unroll
+        for (int u = 0; u < NPAD * BJ / NUM_XFORM; ++u) {
+          const int w = tid + u * NUM_XFORM;
+          const int n = 8 * (w >> 7) + ((w >> 2) & 7), jj = 4 * ((w >> 5) & 3) + (w & 3);
+          // raw W tile rows are 64-byte swizzled: 16-byte chunk q of row n sits at q ^ ((n >> 1) & 3)
+          const float v =
+              (jj < vc && n < K) ? sm.wraw[s][c][n * BJ + (((jj >> 2) ^ ((n >> 1) & 3)) << 2) + (jj & 3)] : 0.f;
+          uint32_t h, l;
+          split_tf32(v, h, l);
+          reinterpret_cast<uint32_t*>(sm.b[a][0][c])[w] = h;
+          reinterpret_cast<uint32_t*>(sm.b[a][1][c])[w] = l;
+        }
       }
       fence_proxy_async_smem();
       tmem_wait_st();
@@ -261,26 +293,33 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
 }
 
 // ---------------------------------------------------------------- host side
-template <int NPAD, bool M1>
+template <int NPAD, bool M1, int NC>
 cudaError_t launch_k(const CUtensorMap& tmX, const CUtensorMap& tmW, int I, int64_t L, int64_t J, int K,
                      const TcSketchPlan& pl, float* part, DevStatus* st, cudaStream_t stream) {
-  const size_t smem = sizeof(SketchSmem) + 1024;
-  cudaError_t e = allow_dynamic_smem((const void*)tc_sketch_kernel<NPAD, M1>, smem);
+  const size_t smem = sizeof(SketchSmem<NC>) + 1024;
+  cudaError_t e = allow_dynamic_smem((const void*)tc_sketch_kernel<NPAD, M1, NC>, smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)pl.splits, (unsigned)pl.mgroups);
-  tc_sketch_kernel<NPAD, M1><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmW, I, L, J, K, pl.jchunk, part, st);
+  tc_sketch_kernel<NPAD, M1, NC><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmW, I, L, J, K, pl.jchunk, part, st);
   return cudaGetLastError();
 }
 
-template <bool M1>
+template <bool M1, int NC>
 cudaError_t launch_m(const CUtensorMap& tmX, const CUtensorMap& tmW, int I, int64_t L, int64_t J, int K,
                      const TcSketchPlan& pl, float* part, DevStatus* st, cudaStream_t stream) {
   switch (((K + 15) / 16) * 16) {
-    case 16: return launch_k<16, M1>(tmX, tmW, I, L, J, K, pl, part, st, stream);
-    case 32: return launch_k<32, M1>(tmX, tmW, I, L, J, K, pl, part, st, stream);
-    case 48: return launch_k<48, M1>(tmX, tmW, I, L, J, K, pl, part, st, stream);
-    default: return launch_k<64, M1>(tmX, tmW, I, L, J, K, pl, part, st, stream);
+    case 16: return launch_k<16, M1, NC>(tmX, tmW, I, L, J, K, pl, part, st, stream);
+    case 32: return launch_k<32, M1, NC>(tmX, tmW, I, L, J, K, pl, part, st, stream);
+    case 48: return launch_k<48, M1, NC>(tmX, tmW, I, L, J, K, pl, part, st, stream);
+    default: return launch_k<64, M1, NC>(tmX, tmW, I, L, J, K, pl, part, st, stream);
   }
+}
+
+// Chunks per stage for a view: 4 (64 j x 128 rows) for short modes, else 1.
+int chunks_for(const View& x) {
+  if (x.I > 128) return 1;
+  if (x.L == 1) return 4;
+  return (x.L % (BJ * 4) == 0) ? 4 : 1;             // a 64-j stage must not cross r
 }
 
 }  // namespace
@@ -295,22 +334,30 @@ bool tc_sketch_supported(const View& x, const WView& w, int K) {
   return x.L < (int64_t(1) << 31) && x.Rt < (int64_t(1) << 31);
 }
 
-TcSketchPlan plan_tc_sketch(int64_t I, int K, int64_t J) {
+static TcSketchPlan plan_nc(int64_t I, int64_t J, int nc) {
   TcSketchPlan pl;
-  pl.mgroups = (int)((I + ROWS - 1) / ROWS);
+  const int rows = 512 / nc, sbj = BJ * nc;
+  pl.mgroups = (int)((I + rows - 1) / rows);
   int64_t splits = std::max<int64_t>(1, device_sms() / pl.mgroups);
   int64_t chunk = (J + splits - 1) / splits;
-  chunk = ((chunk + BJ - 1) / BJ) * BJ;
+  chunk = ((chunk + sbj - 1) / sbj) * sbj;
   pl.jchunk = chunk;
   pl.splits = (int)((J + chunk - 1) / chunk);
-  (void)K;
   return pl;
+}
+
+TcSketchPlan plan_tc_sketch(int64_t I, int K, int64_t J) {
+  (void)K;
+  // the larger of the two possible split counts sizes the partial sums
+  const TcSketchPlan a = plan_nc(I, J, 1), b = plan_nc(I, J, 4);
+  return (a.splits * a.mgroups >= b.splits * b.mgroups) ? a : b;
 }
 
 cudaError_t launch_tc_sketch(const View& x, const WView& w, int K, float* Y, int64_t ldy, float* part,
                              DevStatus* st, cudaStream_t stream) {
   const int64_t I = x.I, J = x.L * x.Rt;
-  TcSketchPlan pl = plan_tc_sketch(I, K, J);
+  const int nc = chunks_for(x);
+  const TcSketchPlan pl = plan_nc(I, J, nc);
   CUtensorMap tmX, tmW;
   {
     const uint64_t dims[2] = {(uint64_t)J, (uint64_t)K};
@@ -319,18 +366,21 @@ cudaError_t launch_tc_sketch(const View& x, const WView& w, int K, float* Y, int
     if (!make_tmap_f32(&tmW, w.p, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B)) return cudaErrorNotSupported;
   }
   cudaError_t e;
+  const uint32_t boxw = nc == 1 ? 256u : 128u;
   if (x.L == 1) {
     const uint64_t dims[2] = {(uint64_t)I, (uint64_t)J};
     const uint64_t strides[1] = {(uint64_t)I};
-    const uint32_t box[2] = {BOXW, BJ};
+    const uint32_t box[2] = {boxw, (uint32_t)(BJ * nc)};
     if (!make_tmap_f32(&tmX, x.p, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE)) return cudaErrorNotSupported;
-    e = launch_m<true>(tmX, tmW, (int)I, 1, J, K, pl, part, st, stream);
+    e = nc == 1 ? launch_m<true, 1>(tmX, tmW, (int)I, 1, J, K, pl, part, st, stream)
+                : launch_m<true, 4>(tmX, tmW, (int)I, 1, J, K, pl, part, st, stream);
   } else {
     const uint64_t dims[3] = {(uint64_t)x.L, (uint64_t)I, (uint64_t)x.Rt};
     const uint64_t strides[2] = {(uint64_t)x.s_i, x.Rt > 1 ? (uint64_t)x.s_r : (uint64_t)x.s_i * (uint64_t)I};
-    const uint32_t box[3] = {BJ, BOXW, 1};
+    const uint32_t box[3] = {BJ, boxw, 1};
     if (!make_tmap_f32(&tmX, x.p, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B)) return cudaErrorNotSupported;
-    e = launch_m<false>(tmX, tmW, (int)I, x.L, J, K, pl, part, st, stream);
+    e = nc == 1 ? launch_m<false, 1>(tmX, tmW, (int)I, x.L, J, K, pl, part, st, stream)
+                : launch_m<false, 4>(tmX, tmW, (int)I, x.L, J, K, pl, part, st, stream);
   }
   if (e != cudaSuccess) return e;
   return launch_reduce_partials_f(part, pl.splits, I, K, Y, ldy, stream);

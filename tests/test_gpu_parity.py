@@ -138,9 +138,11 @@ def test_tc_sketch_mode1_parity(dims, K):
 
 # Strided unfoldings (L % 16 == 0, J >= 1024) on the tcgen05 sketch kernel
 # through 64-byte-swizzled 3-D TMA boxes: L = 16 / 32 / 128 / L*I*Rt with
-# Rt = 1, I below / across one 256-row box and above one 512-row group, 4-way.
+# Rt = 1, I below / across one 256-row box and above one 512-row group, 4-way;
+# short modes (I <= 128, L % 64 == 0) stage 64 j x 128 rows.
 TC_STRIDED_CASES = [((32, 512, 40), 1, 42), ((16, 100, 70), 1, 16), ((128, 300, 9), 1, 33),
-                    ((32, 32, 600), 2, 64), ((16, 8, 40, 12), 2, 20), ((32, 16, 8, 36), 3, 7)]
+                    ((32, 32, 600), 2, 64), ((16, 8, 40, 12), 2, 20), ((32, 16, 8, 36), 3, 7),
+                    ((64, 128, 30), 1, 26)]
 
 
 @pytest.mark.parametrize("dims,mode,K", TC_STRIDED_CASES)
