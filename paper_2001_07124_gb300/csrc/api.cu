@@ -161,6 +161,24 @@ void op_omega(Ctx& c, uint64_t seed, uint32_t stream_id, int64_t rows, int cols,
   if (!c.dry) c.check(launch_omega(seed, stream_id, rows, cols, out, rows, c.s));
 }
 
+// Y = X_(n) Omega with Omega the seeded Gaussian test matrix of (seed, stream_id)
+// (J x K, Alg. 1 step 1).  Where the tensor-core sketch can generate it (modes
+// with I > 128), Omega is computed inside the sketch kernel and never stored;
+// otherwise it is drawn into Om (J x K, caller's buffer) and sketched from memory.
+void op_sketch_seeded(Ctx& c, const View& x, int K, uint64_t seed, uint32_t stream_id, float* Y, int64_t ldy,
+                      float* Om) {
+  const int64_t J = x.L * x.Rt;
+  if (c.st != nullptr && tc_sketch_seeded_supported(x, K)) {
+    Scope sc(c);
+    float* part = c.take<float>(sketch_scratch_floats(x.I, K, J));
+    c.launches += 2;
+    if (!c.dry) c.check(launch_tc_sketch_seeded(x, K, seed, stream_id, Y, ldy, part, c.st, c.s));
+    return;
+  }
+  op_omega(c, seed, stream_id, J, K, Om);
+  op_sketch(c, x, WView{Om, x.L, J}, K, Y, ldy);
+}
+
 // ------------------------------------------------------------------ Alg. 1 on one mode
 
 struct ModeResult {
@@ -177,12 +195,10 @@ void alg1_mode(Ctx& c, const float* x, const Geom& g, int n, int K, int R, int q
                const float* omega_explicit, float* Yb, float* Zb, float* Om, float* Ub) {
   const View xv = mode_view(x, g, n);
   const int64_t I = g.d[n], L = g.L(n), J = g.J(n);
-  const float* W = omega_explicit;
-  if (W == nullptr) {
-    op_omega(c, seed, (uint32_t)n, J, K, Om);
-    W = Om;
-  }
-  op_sketch(c, xv, WView{W, L, J}, K, Yb, I);            // Y = X_(n) Omega
+  if (omega_explicit != nullptr)
+    op_sketch(c, xv, WView{omega_explicit, L, J}, K, Yb, I);   // Y = X_(n) Omega
+  else
+    op_sketch_seeded(c, xv, K, seed, (uint32_t)n, Yb, I, Om);
   op_orth(c, Yb, I, K, I, q > 0 ? 1 : 2);               // Q = orth(Y)
   const OView zo{Zb, J, L};                              // Z(j,k) at j + k*J
   for (int it = 0; it < q; ++it) {
@@ -452,11 +468,10 @@ void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const
   // lines 1-2: factor sketches and their orthonormal bases
   for (int n = 0; n < N; ++n) {
     const float* W = (Omega != nullptr) ? Omega[n] : nullptr;
-    if (W == nullptr) {
-      op_omega(c, seed, (uint32_t)n, g.J(n), pl.K[n], Om);
-      W = Om;
-    }
-    op_sketch(c, mode_view(X, g, n), WView{W, g.L(n), g.J(n)}, pl.K[n], Ys[n], g.d[n]);
+    if (W != nullptr)
+      op_sketch(c, mode_view(X, g, n), WView{W, g.L(n), g.J(n)}, pl.K[n], Ys[n], g.d[n]);
+    else
+      op_sketch_seeded(c, mode_view(X, g, n), pl.K[n], seed, (uint32_t)n, Ys[n], g.d[n], Om);
     op_orth(c, Ys[n], g.d[n], pl.K[n], g.d[n]);
   }
   // line 3: core sketch
@@ -661,13 +676,12 @@ rhosvd_status rhosvd_sketch(const float* X, const rhosvd_shape* shape, int32_t m
   Ctx c;
   if ((s = begin(c, ws, ws_bytes, stream)) != RHOSVD_OK) return s;
   const int64_t J = g.J(mode);
-  const float* W = Omega;
-  if (W == nullptr) {
+  if (Omega == nullptr) {
     float* Om = c.take<float>((size_t)J * K);
-    op_omega(c, seed, (uint32_t)mode, J, K, Om);
-    W = Om;
+    op_sketch_seeded(c, mode_view(X, g, mode), K, seed, (uint32_t)mode, Y, g.d[mode], Om);
+  } else {
+    op_sketch(c, mode_view(X, g, mode), WView{Omega, g.L(mode), J}, K, Y, g.d[mode]);
   }
-  op_sketch(c, mode_view(X, g, mode), WView{W, g.L(mode), J}, K, Y, g.d[mode]);
   return finish(c);
 }
 
@@ -707,10 +721,10 @@ rhosvd_status rhosvd_sketch_all(const float* X, const rhosvd_shape* shape, const
       Scope inner(c);
       if (W == nullptr) {
         float* Om = c.take<float>((size_t)J * K[n]);
-        op_omega(c, seed, (uint32_t)n, J, K[n], Om);
-        W = Om;
+        op_sketch_seeded(c, mode_view(X, g, n), K[n], seed, (uint32_t)n, Y[n], g.d[n], Om);
+      } else {
+        op_sketch(c, mode_view(X, g, n), WView{W, g.L(n), J}, K[n], Y[n], g.d[n]);
       }
-      op_sketch(c, mode_view(X, g, n), WView{W, g.L(n), J}, K[n], Y[n], g.d[n]);
     }
   }
   if (H != nullptr) {

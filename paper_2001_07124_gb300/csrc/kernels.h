@@ -70,6 +70,12 @@ cudaError_t launch_tc_sketch(const View& x, const WView& w, int K, float* Y, int
 // Sketch with the fastest kernel that supports the layout; part must hold
 // sketch_scratch_floats(x.I, K, J) floats.
 size_t sketch_scratch_floats(int64_t I, int K, int64_t J);
+// The tensor-core sketch with W = the seeded Gaussian Omega of (seed, stream_id),
+// generated inside the kernel; cudaErrorNotSupported when the view does not
+// take the tensor-core path (the caller then materialises Omega).
+bool tc_sketch_seeded_supported(const View& x, int K);
+cudaError_t launch_tc_sketch_seeded(const View& x, int K, uint64_t seed, uint32_t stream_id, float* Y, int64_t ldy,
+                                    float* part, DevStatus* st, cudaStream_t stream);
 cudaError_t launch_sketch_auto(const View& x, const WView& w, int K, float* Y, int64_t ldy, float* part,
                                DevStatus* st, cudaStream_t stream);
 // G = X_(n) W accumulated in double-float, reduced in FP64 to Gd (K x I... as I x K, ld = I).

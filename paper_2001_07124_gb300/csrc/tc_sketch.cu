@@ -31,6 +31,7 @@
 // plain J x K matrix with J % 4 == 0, 16-byte aligned pointers; mode 1 needs
 // I % 4 == 0, a strided view L % 16 == 0 and strides that are multiples of 4.
 #include <algorithm>
+#include <cstring>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -82,10 +83,15 @@ struct __align__(1024) SketchSmem {
 // 8-row x 16-byte core matrices with LBO = 128 (K direction) and SBO = 512
 // (N direction); the second MMA K step starts 256 bytes in.
 
-template <int NPAD, bool M1, int NC>
+// GEN: W is the seeded Gaussian test matrix Omega(j, k) of (seed, stream),
+// computed in the transform warps from the counter-based generator (the same
+// function the omega kernel evaluates, so the values are identical) instead of
+// being read from memory.
+template <int NPAD, bool M1, int NC, bool GEN>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, int I,
-                 int64_t L, int64_t J, int K, int64_t jchunk, float* __restrict__ part, DevStatus* st) {
+                 int64_t L, int64_t J, int K, int64_t jchunk, float* __restrict__ part, uint64_t seed,
+                 uint32_t stream_id, DevStatus* st) {
   using G = Geo<NC>;
   constexpr int X_STAGES = G::X_STAGES, ROWS = G::ROWS, SBJ = G::SBJ, BOXW = G::BOXW;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -131,7 +137,7 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       const uint32_t box_bytes = M1 ? (uint32_t)(SBJ * BOXW * 4) : (uint32_t)(BJ * BOXW * 4);
-      const uint32_t bytes = (uint32_t)nbox * box_bytes + (uint32_t)(NC * B_TILE * 4);
+      const uint32_t bytes = (uint32_t)nbox * box_bytes + (GEN ? 0u : (uint32_t)(NC * B_TILE * 4));
       for (int kb = 0; kb < nkb && ok; ++kb) {
         const int s = kb % X_STAGES;
         const uint32_t ph = (uint32_t)(kb / X_STAGES) & 1u;
@@ -150,7 +156,8 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
             tma_load_3d(sm.x[s] + bx * BJ * BOXW, &tmX, li, ii, (int)rj, &sm.full_x[s]);
           }
         }
-        for (int c = 0; c < NC; ++c) tma_load_2d(sm.wraw[s][c], &tmW, jt + BJ * c, 0, &sm.full_x[s]);
+        if (!GEN)
+          for (int c = 0; c < NC; ++c) tma_load_2d(sm.wraw[s][c], &tmW, jt + BJ * c, 0, &sm.full_x[s]);
       }
     }
   } else if (warp == 9) {
@@ -228,8 +235,31 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
       // B tiles: element (n, jj) of W, split into hi / lo.  Threads walk the
       // canonical layout word by word (conflict-free stores): word w holds
       // n = 8 (w >> 7) + ((w >> 2) & 7), jj = 4 ((w >> 5) & 3) + (w & 3).
+      if (GEN) {
+        // Omega(j, 4g..4g+3) from one generator call; thread = (jj, g) of a chunk
+        constexpr int NQ = NPAD / 4;
+        const int64_t jt = jb + (int64_t)kb * SBJ;
 #pragma unroll
-      for (int c = 0; c < NC; ++c) {
+        for (int c = 0; c < NC; ++c) {
+          const int vc = valid - BJ * c;
+          for (int q = tid; q < BJ * NQ; q += NUM_XFORM) {
+            const int jj = q % BJ, g = q / BJ;
+            float z[4] = {0.f, 0.f, 0.f, 0.f};
+            if (jj < vc && 4 * g < K) omega_quad(seed, stream_id, (uint64_t)(jt + BJ * c + jj), (uint32_t)g, z);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int n = 4 * g + e;
+              const int w = (n >> 3) * 128 + (jj >> 2) * 32 + (n & 7) * 4 + (jj & 3);
+              uint32_t h, l;
+              split_tf32(n < K ? z[e] : 0.f, h, l);
+              reinterpret_cast<uint32_t*>(sm.b[a][0][c])[w] = h;
+              reinterpret_cast<uint32_t*>(sm.b[a][1][c])[w] = l;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < (GEN ? 0 : NC); ++c) {
         const int vc = valid - BJ * c;
 #pragma unroll
         for (int u = 0; u < NPAD * BJ / NUM_XFORM; ++u) {
@@ -293,26 +323,40 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
 }
 
 // ---------------------------------------------------------------- host side
-template <int NPAD, bool M1, int NC>
+struct Gen {
+  bool on;
+  uint64_t seed;
+  uint32_t stream;
+};
+
+template <int NPAD, bool M1, int NC, bool GEN>
 cudaError_t launch_k(const CUtensorMap& tmX, const CUtensorMap& tmW, int I, int64_t L, int64_t J, int K,
-                     const TcSketchPlan& pl, float* part, DevStatus* st, cudaStream_t stream) {
+                     const TcSketchPlan& pl, float* part, const Gen& gen, DevStatus* st, cudaStream_t stream) {
   const size_t smem = sizeof(SketchSmem<NC>) + 1024;
-  cudaError_t e = allow_dynamic_smem((const void*)tc_sketch_kernel<NPAD, M1, NC>, smem);
+  cudaError_t e = allow_dynamic_smem((const void*)tc_sketch_kernel<NPAD, M1, NC, GEN>, smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)pl.splits, (unsigned)pl.mgroups);
-  tc_sketch_kernel<NPAD, M1, NC><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmW, I, L, J, K, pl.jchunk, part, st);
+  tc_sketch_kernel<NPAD, M1, NC, GEN><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmW, I, L, J, K, pl.jchunk, part,
+                                                                          gen.seed, gen.stream, st);
   return cudaGetLastError();
+}
+
+template <bool M1, int NC, bool GEN>
+cudaError_t launch_g(const CUtensorMap& tmX, const CUtensorMap& tmW, int I, int64_t L, int64_t J, int K,
+                     const TcSketchPlan& pl, float* part, const Gen& gen, DevStatus* st, cudaStream_t stream) {
+  switch (((K + 15) / 16) * 16) {
+    case 16: return launch_k<16, M1, NC, GEN>(tmX, tmW, I, L, J, K, pl, part, gen, st, stream);
+    case 32: return launch_k<32, M1, NC, GEN>(tmX, tmW, I, L, J, K, pl, part, gen, st, stream);
+    case 48: return launch_k<48, M1, NC, GEN>(tmX, tmW, I, L, J, K, pl, part, gen, st, stream);
+    default: return launch_k<64, M1, NC, GEN>(tmX, tmW, I, L, J, K, pl, part, gen, st, stream);
+  }
 }
 
 template <bool M1, int NC>
 cudaError_t launch_m(const CUtensorMap& tmX, const CUtensorMap& tmW, int I, int64_t L, int64_t J, int K,
-                     const TcSketchPlan& pl, float* part, DevStatus* st, cudaStream_t stream) {
-  switch (((K + 15) / 16) * 16) {
-    case 16: return launch_k<16, M1, NC>(tmX, tmW, I, L, J, K, pl, part, st, stream);
-    case 32: return launch_k<32, M1, NC>(tmX, tmW, I, L, J, K, pl, part, st, stream);
-    case 48: return launch_k<48, M1, NC>(tmX, tmW, I, L, J, K, pl, part, st, stream);
-    default: return launch_k<64, M1, NC>(tmX, tmW, I, L, J, K, pl, part, st, stream);
-  }
+                     const TcSketchPlan& pl, float* part, const Gen& gen, DevStatus* st, cudaStream_t stream) {
+  return gen.on ? launch_g<M1, NC, true>(tmX, tmW, I, L, J, K, pl, part, gen, st, stream)
+                : launch_g<M1, NC, false>(tmX, tmW, I, L, J, K, pl, part, gen, st, stream);
 }
 
 // Chunks per stage for a view: 4 (64 j x 128 rows) for short modes, else 1.
@@ -353,13 +397,14 @@ TcSketchPlan plan_tc_sketch(int64_t I, int K, int64_t J) {
   return (a.splits * a.mgroups >= b.splits * b.mgroups) ? a : b;
 }
 
-cudaError_t launch_tc_sketch(const View& x, const WView& w, int K, float* Y, int64_t ldy, float* part,
-                             DevStatus* st, cudaStream_t stream) {
+static cudaError_t tc_sketch_impl(const View& x, const WView& w, int K, float* Y, int64_t ldy, float* part,
+                                  const Gen& gen, DevStatus* st, cudaStream_t stream) {
   const int64_t I = x.I, J = x.L * x.Rt;
   const int nc = chunks_for(x);
   const TcSketchPlan pl = plan_nc(I, J, nc);
   CUtensorMap tmX, tmW;
-  {
+  memset(&tmW, 0, sizeof(tmW));
+  if (!gen.on) {
     const uint64_t dims[2] = {(uint64_t)J, (uint64_t)K};
     const uint64_t strides[1] = {(uint64_t)J};
     const uint32_t box[2] = {BJ, 64};
@@ -372,18 +417,39 @@ cudaError_t launch_tc_sketch(const View& x, const WView& w, int K, float* Y, int
     const uint64_t strides[1] = {(uint64_t)I};
     const uint32_t box[2] = {boxw, (uint32_t)(BJ * nc)};
     if (!make_tmap_f32(&tmX, x.p, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE)) return cudaErrorNotSupported;
-    e = nc == 1 ? launch_m<true, 1>(tmX, tmW, (int)I, 1, J, K, pl, part, st, stream)
-                : launch_m<true, 4>(tmX, tmW, (int)I, 1, J, K, pl, part, st, stream);
+    e = nc == 1 ? launch_m<true, 1>(tmX, tmW, (int)I, 1, J, K, pl, part, gen, st, stream)
+                : launch_m<true, 4>(tmX, tmW, (int)I, 1, J, K, pl, part, gen, st, stream);
   } else {
     const uint64_t dims[3] = {(uint64_t)x.L, (uint64_t)I, (uint64_t)x.Rt};
     const uint64_t strides[2] = {(uint64_t)x.s_i, x.Rt > 1 ? (uint64_t)x.s_r : (uint64_t)x.s_i * (uint64_t)I};
     const uint32_t box[3] = {BJ, boxw, 1};
     if (!make_tmap_f32(&tmX, x.p, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B)) return cudaErrorNotSupported;
-    e = nc == 1 ? launch_m<false, 1>(tmX, tmW, (int)I, x.L, J, K, pl, part, st, stream)
-                : launch_m<false, 4>(tmX, tmW, (int)I, x.L, J, K, pl, part, st, stream);
+    e = nc == 1 ? launch_m<false, 1>(tmX, tmW, (int)I, x.L, J, K, pl, part, gen, st, stream)
+                : launch_m<false, 4>(tmX, tmW, (int)I, x.L, J, K, pl, part, gen, st, stream);
   }
   if (e != cudaSuccess) return e;
   return launch_reduce_partials_f(part, pl.splits, I, K, Y, ldy, stream);
+}
+
+cudaError_t launch_tc_sketch(const View& x, const WView& w, int K, float* Y, int64_t ldy, float* part,
+                             DevStatus* st, cudaStream_t stream) {
+  return tc_sketch_impl(x, w, K, Y, ldy, part, Gen{false, 0, 0}, st, stream);
+}
+
+// In-kernel generation pays where a stage needs at most about one generator call
+// per transform thread (512-row stages); with 128-row stages (64 j per stage) the
+// generator would become the slowest stage of the pipeline, so the caller draws
+// Omega into memory first.
+bool tc_sketch_seeded_supported(const View& x, int K) {
+  const int64_t J = x.L * x.Rt;
+  return tc_sketch_supported(x, WView{nullptr, x.L, J}, K) && chunks_for(x) == 1;
+}
+
+cudaError_t launch_tc_sketch_seeded(const View& x, int K, uint64_t seed, uint32_t stream_id, float* Y, int64_t ldy,
+                                    float* part, DevStatus* st, cudaStream_t stream) {
+  const int64_t J = x.L * x.Rt;
+  if (st == nullptr || !tc_sketch_seeded_supported(x, K)) return cudaErrorNotSupported;
+  return tc_sketch_impl(x, WView{nullptr, x.L, J}, K, Y, ldy, part, Gen{true, seed, stream_id}, st, stream);
 }
 
 }  // namespace rhosvd

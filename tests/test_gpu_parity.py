@@ -157,6 +157,19 @@ def test_tc_sketch_strided_parity(dims, mode, K):
     assert_close_abs(Y, a @ om64, np.abs(a) @ np.abs(om64))
 
 
+@pytest.mark.parametrize("dims,mode,K", [((512, 64, 64), 0, 42), ((128, 36, 111), 0, 7), ((32, 512, 40), 1, 42),
+                                         ((16, 8, 40, 12), 2, 20), ((100, 48, 50), 0, 33)])
+def test_seeded_sketch_generates_omega_in_kernel(dims, mode, K):
+    """With no explicit Omega the tensor-core sketch draws the test matrix inside
+    the kernel; it equals, bit for bit, the sketch with the materialised matrix."""
+    X = dev(random_tensor(dims, 27))
+    J = int(np.prod(dims)) // dims[mode]
+    om = R().rhosvd_omega(91, mode, J, K).t().contiguous().reshape(-1)
+    y_mat = host(R().rhosvd_sketch(X, dims, mode, K, Omega=om))
+    y_gen = host(R().rhosvd_sketch(X, dims, mode, K, seed=91))
+    np.testing.assert_array_equal(y_gen, y_mat)
+
+
 def test_tc_sketch_is_deterministic():
     dims, K = (512, 64, 64), 42
     X = dev(random_tensor(dims, 23))
