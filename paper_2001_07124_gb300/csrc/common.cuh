@@ -73,6 +73,40 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
   s = a + b;
   e = b - (s - a);
 }
+// 2^k as a float for -126 <= k <= 127 (0 below, +inf above).
+__device__ __forceinline__ float pow2f(int k) {
+  return (k < -126) ? 0.f : (k > 127 ? __int_as_float(0x7f800000) : __int_as_float((k + 127) << 23));
+}
+// Double-word pair of a finite double times 2^-e, with integer and FP32
+// instructions only (GB300's FP64 pipe is narrow): the significand's top 24
+// bits give the high part exactly, the low 29 bits, rounded, the low part, and
+// one FastTwoSum renormalises (48 significant bits in all).  Values whose
+// scaled magnitude is below 2^-126 become 0.
+__device__ __forceinline__ df64 dw_from_double_scaled(double v, int e) {
+  const long long b = __double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex == 0) return df64{0.f, 0.f};
+  const long long m = (b & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;   // 53-bit significand
+  const int E = ex - 1075 - e;                                        // v 2^-e = m 2^E
+  const float h = (float)(int)(m >> 29) * pow2f(E + 29);
+  const float l = (float)(int)(m & 0x1FFFFFFF) * pow2f(E);
+  float hi, lo;
+  fast_two_sum(h, l, hi, lo);
+  return (b < 0) ? df64{-hi, -lo} : df64{hi, lo};
+}
+// A double's value truncated to float (no rounding; 0 below the normal float
+// range), by bit manipulation: for estimates that must not use the FP64 pipe.
+__device__ __forceinline__ float f32_trunc(double v) {
+  const long long b = __double_as_longlong(v);
+  const int ex = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  const int sign = (int)((b >> 32) & 0x80000000LL);
+  if (ex <= 0) return __int_as_float(sign);
+  if (ex >= 255) return __int_as_float(sign | 0x7f800000);
+  return __int_as_float(sign | (ex << 23) | (int)((b >> 29) & 0x7fffff));
+}
+__device__ __forceinline__ bool finite_bits(double v) {
+  return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
+}
 __device__ __forceinline__ df64 dw_from_double(double v) {
   const float hi = __double2float_rn(v);
   return df64{hi, __double2float_rn(v - (double)hi)};

@@ -49,7 +49,7 @@ small_eig_kernel(const double* __restrict__ G, int K, int R, float* __restrict__
   for (int e = tid; e < K * K; e += blockDim.x) {      // one bulk load, independent requests
     const double v = G[e];
     Gs[e] = v;
-    if (!isfinite(v)) nonfinite = 1;
+    if (!finite_bits(v)) nonfinite = 1;
   }
   __syncthreads();
   if (warp == 0) {

@@ -66,7 +66,7 @@ chol_kernel(const double* __restrict__ G, int K, float* __restrict__ Lout, float
   for (int e = tid; e < K * K; e += CH_THREADS) {
     const double v = G[e];
     Gs[e] = v;
-    if (!isfinite(v)) nonfinite = 1;
+    if (!finite_bits(v)) nonfinite = 1;
   }
   __syncthreads();
   if (warp == 0) {
@@ -80,8 +80,8 @@ chol_kernel(const double* __restrict__ G, int K, float* __restrict__ Lout, float
   for (int e = tid; e < K * K; e += CH_THREADS) {
     const int c = e / K, r = e - c * K;
     if (r > c) {
-      const float grr = (float)Gs[r + r * K], gcc = (float)Gs[c + c * K];
-      const float cs = (grr > 0.f && gcc > 0.f) ? fabsf((float)Gs[e]) * rsqrtf(grr) * rsqrtf(gcc) : 1.f;
+      const float grr = f32_trunc(Gs[r + r * K]), gcc = f32_trunc(Gs[c + c * K]);
+      const float cs = (grr > 0.f && gcc > 0.f) ? fabsf(f32_trunc(Gs[e])) * rsqrtf(grr) * rsqrtf(gcc) : 1.f;
       cmax = fminf(fmaxf(cmax, cs), 1.f);
     }
   }

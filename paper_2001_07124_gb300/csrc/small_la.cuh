@@ -13,6 +13,7 @@ constexpr int CHOL_GRID_THREADS = 256;
 struct F32Ops {
   using T = float;
   __device__ static T from(double v) { return __double2float_rn(v); }
+  __device__ static T from_scaled(double v, int e) { return dw_from_double_scaled(v, e).hi; }
   __device__ static T zero() { return 0.f; }
   __device__ static T mul(T a, T b) { return a * b; }
   __device__ static T sub(T a, T b) { return a - b; }
@@ -22,6 +23,7 @@ struct F32Ops {
 struct DWOps {
   using T = df64;
   __device__ static T from(double v) { return dw_from_double(v); }
+  __device__ static T from_scaled(double v, int e) { return dw_from_double_scaled(v, e); }
   __device__ static T zero() { return df64{0.f, 0.f}; }
   __device__ static T mul(T a, T b) { return dw_mul(a, b); }
   // the trailing update only needs backward stability: the cheaper DW sum suffices
@@ -60,16 +62,17 @@ __device__ bool chol_grid(const double* Gs, int K, int e, double tol, bool semid
   const bool active = tid < CHOL_GRID_THREADS;     // larger blocks only join the barriers
   if (active)
     for (int c = ty; c < K; c += 16)
-      for (int r = tx; r < K; r += 16) A[r + c * K] = (r >= c) ? Ops::from(ldexp(Gs[r + c * K], -e)) : Ops::zero();
+      for (int r = tx; r < K; r += 16) A[r + c * K] = (r >= c) ? Ops::from_scaled(Gs[r + c * K], e) : Ops::zero();
   if (active && Tinv != nullptr)
     for (int i = ty; i < K; i += 16)
       for (int c = tx; c < K; c += 16) Tinv[i + c * K] = (i == c) ? 1.f : 0.f;
   __syncthreads();
   const float scale = ldexpf(1.f, e / 2);
+  const float tolf = (float)tol;                    // converted once (FP64 pipe)
   if (tid == 0) {
     *flag = 0;
     const T d0 = A[0];
-    if (Ops::hi(d0) > (float)tol) rs_s[0] = Ops::rsqrt(d0);
+    if (Ops::hi(d0) > tolf) rs_s[0] = Ops::rsqrt(d0);
     else if (semidef) rs_s[0] = Ops::zero();
     else *flag = 1;
   }
@@ -130,14 +133,14 @@ __device__ bool chol_grid(const double* Gs, int K, int e, double tol, bool semid
         }
         if (tid == 0 && i == j + 1) {              // thread (0,0) has just finalised A(j+1, j+1)
           const T dn = A[(j + 1) + (j + 1) * K];
-          if (Ops::hi(dn) > (float)tol) rs_s[j + 1] = Ops::rsqrt(dn);
+          if (Ops::hi(dn) > tolf) rs_s[j + 1] = Ops::rsqrt(dn);
           else if (semidef) rs_s[j + 1] = Ops::zero();
           else *flag = 1;
         }
       }
     } else if (tid == 0 && j + 1 < K) {            // zero column: the next pivot is unchanged
       const T dn = A[(j + 1) + (j + 1) * K];
-      if (Ops::hi(dn) > (float)tol) rs_s[j + 1] = Ops::rsqrt(dn);
+      if (Ops::hi(dn) > tolf) rs_s[j + 1] = Ops::rsqrt(dn);
       else if (semidef) rs_s[j + 1] = Ops::zero();
       else *flag = 1;
     }
