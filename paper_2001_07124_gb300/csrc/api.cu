@@ -168,7 +168,7 @@ void op_omega(Ctx& c, uint64_t seed, uint32_t stream_id, int64_t rows, int cols,
 void op_sketch_seeded(Ctx& c, const View& x, int K, uint64_t seed, uint32_t stream_id, float* Y, int64_t ldy,
                       float* Om) {
   const int64_t J = x.L * x.Rt;
-  if (c.st != nullptr && tc_sketch_seeded_supported(x, K)) {
+  if (tc_sketch_seeded_supported(x, K)) {          // same decision in dry runs (launch counting)
     Scope sc(c);
     float* part = c.take<float>(sketch_scratch_floats(x.I, K, J));
     c.launches += 2;
