@@ -307,31 +307,46 @@ def run_batch(args):
 
 
 def run_primitive(args, w):
-    """Time one primitive on the workload's mode-1 shapes (device-drawn inputs)."""
+    """Time one primitive on one mode of the workload (device-drawn inputs):
+    sketch (explicit Omega), power step, orthonormalisation of a J_n x K_n matrix,
+    or the core TTM chain with widths K_n (S_n for a single-pass workload)."""
     import torch
     import paper_2001_07124_gb300 as pkg
     from paper_2001_07124_gb300 import rhosvd as R
     pkg.build()
     R.lib()
     dims = w.dims
+    n = args.mode - 1
+    if not 0 <= n < len(dims):
+        raise SystemExit(f"--mode must be in 1..{len(dims)}")
     Kp, _, _ = R.rhosvd_plan(dims, w.ranks, w.algo, w.p, w.q, K=w.K, S=w.S)
-    K0, I0 = Kp[0], dims[0]
-    J0 = int(np.prod(dims)) // I0
+    Kn, In = Kp[n], dims[n]
+    Jn = int(np.prod(dims)) // In
     g = torch.Generator(device="cuda")
     g.manual_seed(w.seed)
-    ws = R.Workspace(R.rhosvd_primitive_workspace_size(dims, K0))
+    ws = R.Workspace(R.rhosvd_primitive_workspace_size(dims, max(Kp)))
+    X = torch.randn(int(np.prod(dims)), device="cuda", generator=g)
     if args.primitive == "sketch":
-        X = torch.randn(int(np.prod(dims)), device="cuda", generator=g)
-        om = R.rhosvd_omega(w.omega_seed, 0, J0, K0).t().contiguous().reshape(-1)
-        Y = R.empty_colmajor((I0, K0))
-        call = lambda: R.rhosvd_sketch(X, dims, 0, K0, Omega=om, Y=Y, ws=ws)
+        om = R.rhosvd_omega(w.omega_seed, n, Jn, Kn).t().contiguous().reshape(-1)
+        Y = R.empty_colmajor((In, Kn))
+        call = lambda: R.rhosvd_sketch(X, dims, n, Kn, Omega=om, Y=Y, ws=ws)
     elif args.primitive == "power":
-        X = torch.randn(int(np.prod(dims)), device="cuda", generator=g)
-        Q, _ = R.rhosvd_orth(torch.randn(I0, K0, device="cuda", generator=g), ws=ws)
-        call = lambda: R.rhosvd_power(X, dims, 0, Q.clone(), ws=ws)
-    else:
-        Z = torch.randn(K0, J0, device="cuda", generator=g).t()
+        Q, _ = R.rhosvd_orth(torch.randn(In, Kn, device="cuda", generator=g), ws=ws)
+        call = lambda: R.rhosvd_power(X, dims, n, Q.clone(), ws=ws)
+    elif args.primitive == "orth":
+        del X
+        Z = torch.randn(Kn, Jn, device="cuda", generator=g).t()
         call = lambda: R.rhosvd_orth(Z, ws=ws)
+    else:
+        widths = list(w.S) if w.S else list(Kp)
+        Qs = [R.rhosvd_orth(torch.randn(dims[m], widths[m], device="cuda", generator=g), ws=ws)[0]
+              for m in range(len(dims))]
+        t, mt = list(dims), 1
+        for m in range(len(dims)):
+            t[m] = widths[m]
+            mt = max(mt, int(np.prod(t)))
+        cws = R.Workspace(256 + 2 * (mt * 4 + 256))
+        call = lambda: R.rhosvd_core(X, dims, Qs, ws=cws)
     for _ in range(args.warmup):
         call()
     torch.cuda.synchronize()
@@ -341,7 +356,7 @@ def run_primitive(args, w):
         call()
     ev1.record()
     torch.cuda.synchronize()
-    print(json.dumps({"primitive": args.primitive, "workload": w.name, "mode": 1, "K": K0,
+    print(json.dumps({"primitive": args.primitive, "workload": w.name, "mode": args.mode, "K": Kn,
                       "ms_per_call": ev0.elapsed_time(ev1) / args.steps, "calls": args.steps}), flush=True)
 
 
@@ -353,7 +368,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="decay512_rsthosvd", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--primitive", choices=["sketch", "power", "orth"], default=None)
+    ap.add_argument("--primitive", choices=["sketch", "power", "orth", "core"], default=None)
+    ap.add_argument("--mode", type=int, default=1, help="mode (1-based) of --primitive sketch/power/orth")
     ap.add_argument("--no-graph", action="store_true", help="launch the decomposition kernel by kernel")
     ap.add_argument("--serve", type=int, default=0, metavar="N", help="serving run with N requests")
     ap.add_argument("--batch", type=int, default=0, metavar="N", help="batched run with N small tensors")

@@ -46,6 +46,7 @@ small_eig_kernel(const double* __restrict__ G, int K, int R, float* __restrict__
 
   if (tid == 0) nonfinite = 0;
   __syncthreads();
+  #pragma unroll 8
   for (int e = tid; e < K * K; e += blockDim.x) {      // one bulk load, independent requests
     const double v = G[e];
     Gs[e] = v;

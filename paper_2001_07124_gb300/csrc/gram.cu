@@ -55,7 +55,7 @@ gram_kernel(const float* __restrict__ A, int64_t m, int K, int64_t ld, int64_t r
   for (int64_t rt = r0; rt < r1; rt += GR_TILE) {
     const int nrow = (r1 - rt < GR_TILE) ? (int)(r1 - rt) : GR_TILE;
     __syncthreads();
-    for (int e = tid; e < K * GR_TILE; e += GR_THREADS) {
+        for (int e = tid; e < K * GR_TILE; e += GR_THREADS) {
       const int c = e / GR_TILE, r = e % GR_TILE;
       tile[c * LD + r] = (r < nrow) ? __ldg(A + (rt + r) + (int64_t)c * ld) : 0.f;
     }
@@ -130,6 +130,7 @@ gram_f32_kernel(const float* __restrict__ A, int64_t m, int K, int64_t ld, int64
   for (int64_t rt = r0; rt < r1; rt += GR_TILE, ++ntile) {
     const int nrow = (r1 - rt < GR_TILE) ? (int)(r1 - rt) : GR_TILE;
     __syncthreads();
+#pragma unroll 8
     for (int e = tid; e < 4 * nb * GR_TILE; e += GR_THREADS) {
       const int c = e / GR_TILE, r = e % GR_TILE;
       gf_smem[c * GF_LD + r] = (r < nrow && c < K) ? __ldg(A + (rt + r) + (int64_t)c * ld) : 0.f;

@@ -60,7 +60,7 @@ cudaError_t launch_reduce_partials_f(const float* part, int splits, int64_t I, i
 // ---- tc_sketch.cu: tcgen05 (3xTF32) sketch for mode-1 layouts
 struct TcSketchPlan {
   int splits, mgroups;
-  int64_t jchunk;
+  int64_t jchunk;   // j per block; blocks are dealt round-robin over the splits
 };
 bool tc_sketch_supported(const View& x, const WView& w, int K);
 TcSketchPlan plan_tc_sketch(int64_t I, int K, int64_t J);

@@ -63,6 +63,7 @@ chol_kernel(const double* __restrict__ G, int K, float* __restrict__ Lout, float
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) nonfinite = 0;
   __syncthreads();
+  #pragma unroll 8
   for (int e = tid; e < K * K; e += CH_THREADS) {
     const double v = G[e];
     Gs[e] = v;
@@ -125,8 +126,10 @@ chol_kernel(const double* __restrict__ G, int K, float* __restrict__ Lout, float
 // solves L^T x = q, i.e. Y (L L^T)^-1 = Y G^-1 (normal-equation pseudo-inverse).
 // One thread per row, the row in registers (KB >= K, fully unrolled), L in
 // shared memory row-major for the forward sweep and column-major for the
-// backward sweep; the row tile is staged through shared memory so that global
-// loads and stores are coalesced.
+// backward sweep.  Every load of the row and of L is issued before the first
+// one is used (unrolled, no dependence between them), so the prologue costs
+// one memory round trip rather than one per element; for a fixed column the
+// 32 lanes of a warp touch 32 consecutive rows, so the accesses coalesce.
 constexpr int TR_ROWS = 128;
 
 template <int KB>
@@ -138,56 +141,49 @@ trsm_rows_kernel(float* __restrict__ Y, int64_t m, int K, int64_t ld, const floa
   float* Lr = tr_smem;                 // K x KB row-major: Lr[c*KB + k] = L(c,k)
   float* Lc = Lr + KB * KB;            // KB x K column-major: Lc[k + c*KB] = L(k,c)
   float* dinv = Lc + KB * KB;          // 1 / L(c,c)
-  float* tile = dinv + KB;             // TR_ROWS x pitch
-  const int pitch = K | 1;             // odd pitch: conflict-free per-thread rows
   const int tid = threadIdx.x;
-  for (int e = tid; e < KB * KB; e += TR_ROWS) {
-    const int c = e / KB, k = e - c * KB;
-    const float v = (c < K && k < K) ? L[c + k * K] : 0.f;     // L(c,k)
-    Lr[c * KB + k] = v;
-    Lc[c + k * KB] = v;                                         // L(c,k) at column k
+  const int64_t row = (int64_t)blockIdx.x * TR_ROWS + tid;
+  const bool live = row < m;
+  float q[KB];
+#pragma unroll
+  for (int c = 0; c < KB; ++c) q[c] = (live && c < K) ? Y[row + (int64_t)c * ld] : 0.f;
+  constexpr int LU = (KB * KB + TR_ROWS - 1) / TR_ROWS;
+#pragma unroll 16
+  for (int u = 0; u < LU; ++u) {
+    const int e = tid + u * TR_ROWS;
+    if (e < KB * KB) {
+      const int c = e / KB, k = e - c * KB;
+      const float v = (c < K && k < K) ? L[c + k * K] : 0.f;     // L(c,k)
+      Lr[c * KB + k] = v;
+      Lc[c + k * KB] = v;                                         // L(c,k) at column k
+    }
   }
-  for (int c = tid; c < KB; c += TR_ROWS) dinv[c] = (c < K) ? 1.f / L[c + c * K] : 0.f;
-  const int64_t r0 = (int64_t)blockIdx.x * TR_ROWS;
-  const int nrow = (int)((m - r0) < TR_ROWS ? (m - r0) : TR_ROWS);
-  for (int e = tid; e < TR_ROWS * K; e += TR_ROWS) {
-    const int t = e % TR_ROWS, c = e / TR_ROWS;
-    if (t < nrow) tile[t * pitch + c] = Y[(r0 + t) + (int64_t)c * ld];
-  }
+  if (tid < KB) dinv[tid] = (tid < K) ? 1.f / L[tid + tid * K] : 0.f;
   __syncthreads();
-  if (tid < nrow) {
-    float q[KB];
+  if (!live) return;
+  // forward: q_c = (y_c - sum_{k<c} L(c,k) q_k) / L(c,c)
 #pragma unroll
-    for (int c = 0; c < KB; ++c) q[c] = (c < K) ? tile[tid * pitch + c] : 0.f;
-    // forward: q_c = (y_c - sum_{k<c} L(c,k) q_k) / L(c,c)
+  for (int c = 0; c < KB; ++c) {
+    float s = q[c];
+    const float* lrow = Lr + c * KB;
 #pragma unroll
-    for (int c = 0; c < KB; ++c) {
+    for (int k = 0; k < c; ++k) s = fmaf(-lrow[k], q[k], s);
+    q[c] = s * dinv[c];
+  }
+  if (mode == 1) {
+    // backward: x_c = (q_c - sum_{k>c} L(k,c) x_k) / L(c,c)
+#pragma unroll
+    for (int c = KB - 1; c >= 0; --c) {
       float s = q[c];
-      const float* lrow = Lr + c * KB;
+      const float* lcol = Lc + c * KB;
 #pragma unroll
-      for (int k = 0; k < c; ++k) s = fmaf(-lrow[k], q[k], s);
+      for (int k = c + 1; k < KB; ++k) s = fmaf(-lcol[k], q[k], s);
       q[c] = s * dinv[c];
     }
-    if (mode == 1) {
-      // backward: x_c = (q_c - sum_{k>c} L(k,c) x_k) / L(c,c)
-#pragma unroll
-      for (int c = KB - 1; c >= 0; --c) {
-        float s = q[c];
-        const float* lcol = Lc + c * KB;
-#pragma unroll
-        for (int k = c + 1; k < KB; ++k) s = fmaf(-lcol[k], q[k], s);
-        q[c] = s * dinv[c];
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < KB; ++c)
-      if (c < K) tile[tid * pitch + c] = q[c];
   }
-  __syncthreads();
-  for (int e = tid; e < TR_ROWS * K; e += TR_ROWS) {
-    const int t = e % TR_ROWS, c = e / TR_ROWS;
-    if (t < nrow) Y[(r0 + t) + (int64_t)c * ld] = tile[t * pitch + c];
-  }
+#pragma unroll
+  for (int c = 0; c < KB; ++c)
+    if (c < K) Y[row + (int64_t)c * ld] = q[c];
 }
 
 constexpr int HH_THREADS = 1024;
@@ -320,9 +316,8 @@ cudaError_t launch_chol(const double* G, int K, float* L, float* Minv, int ldm, 
 template <int KB>
 static cudaError_t launch_trsm_kb(float* Y, int64_t m, int K, int64_t ld, const float* L, int mode,
                                   const DevStatus* skip, cudaStream_t stream) {
-  const size_t smem = (2 * (size_t)KB * KB + KB + (size_t)TR_ROWS * (K | 1)) * sizeof(float);
-  cudaError_t e = allow_dynamic_smem((const void*)trsm_rows_kernel<KB>,
-                                     (2 * (size_t)KB * KB + KB + (size_t)TR_ROWS * (KB | 1)) * sizeof(float));
+  const size_t smem = (2 * (size_t)KB * KB + KB) * sizeof(float);
+  cudaError_t e = allow_dynamic_smem((const void*)trsm_rows_kernel<KB>, smem);
   if (e != cudaSuccess) return e;
   const unsigned grid = (unsigned)((m + TR_ROWS - 1) / TR_ROWS);
   trsm_rows_kernel<KB><<<grid, TR_ROWS, smem, stream>>>(Y, m, K, ld, L, mode, skip);

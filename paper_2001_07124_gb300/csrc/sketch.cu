@@ -126,6 +126,7 @@ reduce_partials_kernel(const T* __restrict__ part, int splits, int64_t I, int K,
   const int64_t e = (int64_t)blockIdx.x * 32 + lane;
   T s = 0;
   if (e < n)
+#pragma unroll 4
     for (int t = row; t < splits; t += RD_ROWS) s += part[(int64_t)t * n + e];
   acc[row][lane] = s;
   __syncthreads();
@@ -145,6 +146,7 @@ reduce_d_kernel(const double* __restrict__ part, int splits, int64_t n, double* 
   const int64_t e = (int64_t)blockIdx.x * 32 + lane;
   double s = 0;
   if (e < n)
+#pragma unroll 4
     for (int t = row; t < splits; t += RD_ROWS) s += part[(int64_t)t * n + e];
   acc[row][lane] = s;
   __syncthreads();

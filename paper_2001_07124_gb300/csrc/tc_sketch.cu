@@ -11,12 +11,16 @@
 // chunk), so that every stage still moves 32 KB of X.
 //
 // The contraction over j is split over CTAs (one CTA per SM, persistent); each
-// CTA owns up to 512 rows i (four 128-row MMA tiles) and a contiguous range of
-// j, and writes its partial I x K block for the fixed-order reducer.
+// CTA owns up to 512 rows i (four 128-row MMA tiles) and every gridDim.x-th
+// stage-sized block of j, and writes its partial I x K block for the
+// fixed-order reducer.  Interleaving the blocks keeps the CTAs' concurrent
+// reads within one window of each row of X_(n): for a mode whose rows lie
+// megabytes apart, per-CTA contiguous ranges would make every CTA open its own
+// DRAM page in every row.
 //
 // Data path per 16-column block of j (two MMA K steps of kind::tf32):
 //   * TMA copies the X tile (16 x 512 FP32, two 256-wide boxes) and the raw W
-//     tile (16 x 64) into a 4-stage shared-memory ring (producer warp 8).
+//     tile (16 x NPAD) into a 3- to 6-stage shared-memory ring (producer warp 8).
 //   * Eight transform warps (two warpgroups; warp w owns TMEM lane quadrant
 //     w % 4, warpgroup g the 128-row tiles 2g and 2g+1) read X rows from
 //     shared memory, split every value into TF32 hi + lo (3xTF32) and store
@@ -50,28 +54,32 @@ constexpr uint32_t TMEM_COLS = 512;
 constexpr int D_COLS = 64;                // accumulator columns reserved per tile
 constexpr int A_COL0 = 4 * D_COLS;        // first TMEM column of the A stages
 constexpr int A_STAGE_COLS = 128;         // per stage: 4 slots x (16 hi + 16 lo)
-constexpr int B_TILE = 64 * BJ;           // floats per B tile (N <= 64)
 constexpr int STAGE_FLOATS = 8192;        // X floats per stage (32 KB)
+constexpr size_t kSmemLimit = 232448;     // dynamic shared memory per CTA (227 KB)
 
 // Stage geometry, NC = chunks of 16 j per stage: NC = 1 stages 16 j x 512 rows
 // (four 128-row MMA tiles), NC = 4 stages 64 j x 128 rows (one tile, four
 // chunks) for short modes (I <= 128).  The four TMEM A slots of a stage hold
-// tiles (NC = 1) or chunks (NC = 4).
-template <int NC>
+// tiles (NC = 1) or chunks (NC = 4).  The stream of X is latency-bound (the
+// transform warps wait on the TMA barriers), so the W and B tiles hold only
+// NPAD rows (K padded to 16) and the rest of shared memory deepens the X ring.
+template <int NPAD, int NC>
 struct Geo {
   static constexpr int ROWS = 512 / NC;                   // rows i per CTA
   static constexpr int SBJ = BJ * NC;                     // j per stage
   static constexpr int BOXW = ROWS < 256 ? ROWS : 256;    // rows per TMA box
-  static constexpr int X_STAGES = NC == 1 ? 5 : 3;
+  static constexpr int X_STAGES = NPAD <= 48 ? (NC == 1 ? 6 : 4) : (NC == 1 ? 5 : 3);
+  static constexpr int W_TILE = NPAD * BJ;                // floats per W / B tile
 };
 
-template <int NC>
+template <int NPAD, int NC>
 struct __align__(1024) SketchSmem {
+  using G = Geo<NPAD, NC>;
   // mode 1: boxes [box][jj][BOXW]; strided: boxes [box][i][16] (NC = 1: row boxes, NC = 4: chunk boxes)
-  float x[Geo<NC>::X_STAGES][STAGE_FLOATS];
-  float wraw[Geo<NC>::X_STAGES][NC][B_TILE];   // TMA boxes [n][jj] (64B swizzle), rows n >= K zero-filled
-  float b[A_STAGES][2][NC][B_TILE];            // hi / lo B tiles, canonical K-major layout
-  uint64_t full_x[Geo<NC>::X_STAGES], empty_x[Geo<NC>::X_STAGES];
+  float x[G::X_STAGES][STAGE_FLOATS];
+  float wraw[G::X_STAGES][NC][G::W_TILE];    // TMA boxes [n][jj] (64B swizzle), rows n >= K zero-filled
+  float b[A_STAGES][2][NC][G::W_TILE];       // hi / lo B tiles, canonical K-major layout
+  uint64_t full_x[G::X_STAGES], empty_x[G::X_STAGES];
   uint64_t full_a[A_STAGES], empty_a[A_STAGES];
   uint64_t done;
   uint32_t tmem_base;
@@ -90,12 +98,12 @@ struct __align__(1024) SketchSmem {
 template <int NPAD, bool M1, int NC, bool GEN>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmW, int I,
-                 int64_t L, int64_t J, int K, int64_t jchunk, float* __restrict__ part, uint64_t seed,
+                 int64_t L, int64_t J, int K, float* __restrict__ part, uint64_t seed,
                  uint32_t stream_id, DevStatus* st) {
-  using G = Geo<NC>;
+  using G = Geo<NPAD, NC>;
   constexpr int X_STAGES = G::X_STAGES, ROWS = G::ROWS, SBJ = G::SBJ, BOXW = G::BOXW;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  SketchSmem<NC>& sm = *reinterpret_cast<SketchSmem<NC>*>(
+  SketchSmem<NPAD, NC>& sm = *reinterpret_cast<SketchSmem<NPAD, NC>*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int split = blockIdx.x;
@@ -104,9 +112,10 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
   const int mt = (rows + 127) / 128;                 // MMA tiles in this CTA
   const int nslot = NC == 1 ? mt : NC;               // occupied A slots per stage
   const int nbox = M1 ? (rows + BOXW - 1) / BOXW : (NC == 1 ? (rows + BOXW - 1) / BOXW : NC);
-  const int64_t jb = (int64_t)split * jchunk;
-  const int64_t je = min(J, jb + jchunk);
-  const int nkb = (int)((je - jb + SBJ - 1) / SBJ);
+  // stage kb of this CTA covers j in [(split + kb * nsplit) * SBJ, ... + SBJ) clipped to J
+  const int64_t nblk = (J + SBJ - 1) / SBJ, nsplit = gridDim.x;
+  const int nkb = nblk > split ? (int)((nblk - 1 - split) / nsplit + 1) : 0;
+  auto stage_j = [&](int kb) -> int64_t { return ((int64_t)split + (int64_t)kb * nsplit) * SBJ; };
   constexpr uint32_t idesc = idesc_tf32(128, NPAD);
 
   if (tid == 0) {
@@ -137,13 +146,13 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
       const uint32_t box_bytes = M1 ? (uint32_t)(SBJ * BOXW * 4) : (uint32_t)(BJ * BOXW * 4);
-      const uint32_t bytes = (uint32_t)nbox * box_bytes + (GEN ? 0u : (uint32_t)(NC * B_TILE * 4));
+      const uint32_t bytes = (uint32_t)nbox * box_bytes + (GEN ? 0u : (uint32_t)(NC * G::W_TILE * 4));
       for (int kb = 0; kb < nkb && ok; ++kb) {
         const int s = kb % X_STAGES;
         const uint32_t ph = (uint32_t)(kb / X_STAGES) & 1u;
         if (!mbar_wait(&sm.empty_x[s], ph ^ 1u, abort_flag)) { ok = false; break; }
         mbar_arrive_expect_tx(&sm.full_x[s], bytes);
-        const int jt = (int)(jb + (int64_t)kb * SBJ);
+        const int jt = (int)stage_j(kb);
         if (M1) {
           for (int bx = 0; bx < nbox; ++bx)
             tma_load_2d(sm.x[s] + bx * SBJ * BOXW, &tmX, i0 + bx * BOXW, jt, &sm.full_x[s]);
@@ -194,11 +203,36 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
     for (int kb = 0; kb < nkb && ok; ++kb) {
       const int s = kb % X_STAGES, a = kb % A_STAGES;
       const uint32_t phx = (uint32_t)(kb / X_STAGES) & 1u, pha = (uint32_t)(kb / A_STAGES) & 1u;
-      const int64_t rem = je - (jb + (int64_t)kb * SBJ);
+      const int64_t rem = J - stage_j(kb);
       const int valid = rem < SBJ ? (int)rem : SBJ;   // valid j of this stage
-      if (!mbar_wait(&sm.full_x[s], phx, abort_flag)) { ok = false; break; }
       if (!mbar_wait(&sm.empty_a[a], pha ^ 1u, abort_flag)) { ok = false; break; }
       tc_fence_after();
+      // Generated B tiles need no data from X: they are built before waiting for
+      // the stage's X tile, in the shadow of its TMA copy.
+      if (GEN) {
+        // Omega(j, 4g..4g+3) from one generator call; thread = (jj, g) of a chunk
+        constexpr int NQ = NPAD / 4;
+        const int64_t jt = stage_j(kb);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int vc = valid - BJ * c;
+          for (int q = tid; q < BJ * NQ; q += NUM_XFORM) {
+            const int jj = q % BJ, g = q / BJ;
+            float z[4] = {0.f, 0.f, 0.f, 0.f};
+            if (jj < vc && 4 * g < K) omega_quad(seed, stream_id, (uint64_t)(jt + BJ * c + jj), (uint32_t)g, z);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int n = 4 * g + e;
+              const int w = (n >> 3) * 128 + (jj >> 2) * 32 + (n & 7) * 4 + (jj & 3);
+              uint32_t h, l;
+              split_tf32(n < K ? z[e] : 0.f, h, l);
+              reinterpret_cast<uint32_t*>(sm.b[a][0][c])[w] = h;
+              reinterpret_cast<uint32_t*>(sm.b[a][1][c])[w] = l;
+            }
+          }
+        }
+      }
+      if (!mbar_wait(&sm.full_x[s], phx, abort_flag)) { ok = false; break; }
 #pragma unroll
       for (int uu = 0; uu < 2; ++uu) {
         const int u = 2 * wg + uu;                    // A slot: tile (NC = 1) or chunk (NC = 4)
@@ -232,32 +266,9 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
           tmem_st_x16(col + 16 + lane_base, lo);
         }
       }
-      // B tiles: element (n, jj) of W, split into hi / lo.  Threads walk the
-      // canonical layout word by word (conflict-free stores): word w holds
+      // B tiles from memory: element (n, jj) of W, split into hi / lo.  Threads walk
+      // the canonical layout word by word (conflict-free stores): word w holds
       // n = 8 (w >> 7) + ((w >> 2) & 7), jj = 4 ((w >> 5) & 3) + (w & 3).
-      if (GEN) {
-        // Omega(j, 4g..4g+3) from one generator call; thread = (jj, g) of a chunk
-        constexpr int NQ = NPAD / 4;
-        const int64_t jt = jb + (int64_t)kb * SBJ;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          const int vc = valid - BJ * c;
-          for (int q = tid; q < BJ * NQ; q += NUM_XFORM) {
-            const int jj = q % BJ, g = q / BJ;
-            float z[4] = {0.f, 0.f, 0.f, 0.f};
-            if (jj < vc && 4 * g < K) omega_quad(seed, stream_id, (uint64_t)(jt + BJ * c + jj), (uint32_t)g, z);
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int n = 4 * g + e;
-              const int w = (n >> 3) * 128 + (jj >> 2) * 32 + (n & 7) * 4 + (jj & 3);
-              uint32_t h, l;
-              split_tf32(n < K ? z[e] : 0.f, h, l);
-              reinterpret_cast<uint32_t*>(sm.b[a][0][c])[w] = h;
-              reinterpret_cast<uint32_t*>(sm.b[a][1][c])[w] = l;
-            }
-          }
-        }
-      }
 #pragma unroll
       for (int c = 0; c < (GEN ? 0 : NC); ++c) {
         const int vc = valid - BJ * c;
@@ -332,12 +343,13 @@ struct Gen {
 template <int NPAD, bool M1, int NC, bool GEN>
 cudaError_t launch_k(const CUtensorMap& tmX, const CUtensorMap& tmW, int I, int64_t L, int64_t J, int K,
                      const TcSketchPlan& pl, float* part, const Gen& gen, DevStatus* st, cudaStream_t stream) {
-  const size_t smem = sizeof(SketchSmem<NC>) + 1024;
+  const size_t smem = sizeof(SketchSmem<NPAD, NC>) + 1024;
+  static_assert(sizeof(SketchSmem<NPAD, NC>) + 1024 <= kSmemLimit, "sketch stages exceed shared memory");
   cudaError_t e = allow_dynamic_smem((const void*)tc_sketch_kernel<NPAD, M1, NC, GEN>, smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)pl.splits, (unsigned)pl.mgroups);
-  tc_sketch_kernel<NPAD, M1, NC, GEN><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmW, I, L, J, K, pl.jchunk, part,
-                                                                          gen.seed, gen.stream, st);
+  tc_sketch_kernel<NPAD, M1, NC, GEN><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmW, I, L, J, K, part, gen.seed,
+                                                                          gen.stream, st);
   return cudaGetLastError();
 }
 
@@ -382,11 +394,9 @@ static TcSketchPlan plan_nc(int64_t I, int64_t J, int nc) {
   TcSketchPlan pl;
   const int rows = 512 / nc, sbj = BJ * nc;
   pl.mgroups = (int)((I + rows - 1) / rows);
-  int64_t splits = std::max<int64_t>(1, device_sms() / pl.mgroups);
-  int64_t chunk = (J + splits - 1) / splits;
-  chunk = ((chunk + sbj - 1) / sbj) * sbj;
-  pl.jchunk = chunk;
-  pl.splits = (int)((J + chunk - 1) / chunk);
+  const int64_t nblk = (J + sbj - 1) / sbj;            // stage-sized blocks of j, dealt round-robin
+  pl.splits = (int)std::min<int64_t>(std::max<int64_t>(1, device_sms() / pl.mgroups), nblk);
+  pl.jchunk = sbj;
   return pl;
 }
 
@@ -407,7 +417,7 @@ static cudaError_t tc_sketch_impl(const View& x, const WView& w, int K, float* Y
   if (!gen.on) {
     const uint64_t dims[2] = {(uint64_t)J, (uint64_t)K};
     const uint64_t strides[1] = {(uint64_t)J};
-    const uint32_t box[2] = {BJ, 64};
+    const uint32_t box[2] = {BJ, (uint32_t)(((K + 15) / 16) * 16)};   // NPAD rows, k >= K zero-filled
     if (!make_tmap_f32(&tmW, w.p, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B)) return cudaErrorNotSupported;
   }
   cudaError_t e;
@@ -436,13 +446,19 @@ cudaError_t launch_tc_sketch(const View& x, const WView& w, int K, float* Y, int
   return tc_sketch_impl(x, w, K, Y, ldy, part, Gen{false, 0, 0}, st, stream);
 }
 
-// In-kernel generation pays where a stage needs at most about one generator call
-// per transform thread (512-row stages); with 128-row stages (64 j per stage) the
-// generator would become the slowest stage of the pipeline, so the caller draws
-// Omega into memory first.
+// Where the test matrix is generated in-kernel: the transform warps evaluate the
+// generator for every stage, which costs about one generator call per thread
+// and stage with 512-row stages but four with 128-row stages (64 j per stage),
+// where it becomes the slowest step of the pipeline (measured on 128^4: 450 us
+// per mode against 125 + 240 us for drawing Omega first and sketching from
+// memory).  Short modes therefore generate in-kernel only when the stream of X
+// is itself slow: rows of X_(n) 4 MB or more apart (the last mode of a large
+// tensor), where the TMA copies, not the generator, set the pace (460 us
+// against 125 + 560 us).
 bool tc_sketch_seeded_supported(const View& x, int K) {
   const int64_t J = x.L * x.Rt;
-  return tc_sketch_supported(x, WView{nullptr, x.L, J}, K) && chunks_for(x) == 1;
+  if (!tc_sketch_supported(x, WView{nullptr, x.L, J}, K)) return false;
+  return chunks_for(x) == 1 || x.s_i >= (int64_t(1) << 20);
 }
 
 cudaError_t launch_tc_sketch_seeded(const View& x, int K, uint64_t seed, uint32_t stream_id, float* Y, int64_t ldy,

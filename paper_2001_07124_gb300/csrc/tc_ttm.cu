@@ -7,17 +7,22 @@
 // Out(j, k) is written at Out[l + r*o_r + k*o_k] with j = l + o_L*r (o_L
 // defaults to the input's L).
 //
-// Two tile layouts of the 128 j x 32 i stage:
+// Tile layouts of the 128 j x 32 i stage:
 //   * mode 1 (L = 1, i contiguous): one 2-D box {32 i, 128 j} with 128B swizzle,
 //     each j row holding 32 consecutive i;
-//   * strided (L >= 32): a 3-D box {BL l, 32 i, 128/BL r} over [L, I, Rt]
-//     (BL = 32, 64 or 128), smem [r'][i][l'], so the 32 lanes of a warp (32
-//     consecutive j = consecutive l) read consecutive words for every i.
+//   * strided, L a multiple of 128 (or a single r): a 3-D box {128 l, 32 i, 1 r}
+//     over [L, I, Rt], smem [i][l'], tiles of 128 consecutive j;
+//   * strided, L < 128 (several r): slab tiles, a box {L l, 32 i, TR r} with
+//     TR = floor(128 / L) whole r-slabs, smem [r'][i][l'], the tile's L * TR
+//     rows again consecutive in j (the remaining TMEM lanes idle);
+//   * strided, L > 128 not a multiple of 128 (several r): per-r tiles, see below.
+// In every strided layout the 32 lanes of a warp (consecutive j) read nearly
+// consecutive words for every i.
 //
 // Persistent, warp-specialised: each CTA takes 128-row tiles of j in turn and
 // contracts over all of i in stages of 32:
 //   * warp 12 (producer): TMA copies the X tile (128 rows j x 32 floats i, 128B
-//     swizzle) and the raw M tile (64 x 32) of a stage into a 6-stage ring;
+//     swizzle) and the raw M tile (NPAD x 32) of a stage into a 7- or 8-stage ring;
 //   * warps 0-7 (two transform warpgroups, alternating stages): split X into
 //     TF32 hi/lo and store it in tensor memory as the A operand (thread = row j
 //     = TMEM lane), split M into hi/lo B tiles in the canonical K-major layout;
@@ -28,9 +33,9 @@
 //     the rows of Out, and hand the buffer back while the next tile computes.
 // Requirements (checked by tc_ttm_supported): 16-byte aligned X and M, strides
 // multiple of 4 elements, ldm % 4 == 0, K <= 64, L % 4 == 0.  When 128
-// consecutive j would straddle r (L not a multiple of 128, not 32 or 64, and
-// Rt > 1) the tiles are laid out per r: ceil(L / 128) tiles of 128 l for each
-// r, the rows past L zero-filled by TMA and not written.
+// consecutive j would straddle r with L > 128 (L not a multiple of 128, Rt > 1)
+// the tiles are laid out per r: ceil(L / 128) tiles of 128 l for each r, the
+// rows past L zero-filled by TMA and not written.
 #include <algorithm>
 
 #include "common.cuh"
@@ -44,8 +49,7 @@ using namespace tc;
 
 constexpr int BI = 32;                    // contraction elements per stage (4 MMA K steps)
 constexpr int TILE_J = 128;               // rows j per tile (one MMA M)
-constexpr int X_STAGES = 6;
-constexpr int A_STAGES = 4;
+constexpr int A_STAGES = 2;              // one A slot per transform warpgroup
 constexpr int NUM_XFORM = 256;            // warps 0-7
 constexpr int NUM_EPI = 128;              // warps 8-11
 constexpr int PRODUCER_WARP = 12, MMA_WARP = 13;
@@ -54,9 +58,19 @@ constexpr uint32_t TMEM_COLS = 512;
 constexpr int D_COLS = 64;                // per accumulator buffer
 constexpr int A_COL0 = 2 * D_COLS;        // A stages after the two accumulators
 constexpr int A_STAGE_COLS = 2 * BI;      // 32 hi + 32 lo columns
-constexpr int M_TILE = 64 * BI;           // floats per B tile (N <= 64)
 
+// The stream of X is latency-bound (the transform warps wait on the TMA
+// barriers), so shared memory goes to X stages: the M and B tiles hold NPAD
+// rows (K padded to 16), and the X ring is as deep as 227 KB allows.
+template <int NPAD>
+struct TtmGeo {
+  static constexpr int M_TILE = NPAD * BI;                  // floats per M / B tile
+  static constexpr int X_STAGES = NPAD <= 48 ? 8 : 7;
+};
+
+template <int NPAD>
 struct __align__(1024) TtmSmem {
+  static constexpr int X_STAGES = TtmGeo<NPAD>::X_STAGES, M_TILE = TtmGeo<NPAD>::M_TILE;
   float x[X_STAGES][TILE_J * BI];          // TMA tile: mode 1 [j][i] swizzled, strided [r'][i][l']
   float mraw[X_STAGES][M_TILE];            // TMA tile [k][i] (128B swizzle), rows k >= K zero-filled
   float b[A_STAGES][2][M_TILE];            // hi / lo B tiles, canonical K-major layout
@@ -76,16 +90,22 @@ struct __align__(1024) TtmSmem {
 template <int NPAD, bool M1>
 __global__ void __launch_bounds__(NUM_THREADS, 1)
 tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmM, int I,
-              int64_t L, int64_t J, int bl_bits, int tpr, int K, float* __restrict__ out, int64_t o_k,
+              int64_t L, int64_t J, int bl, int tr, int tpr, int K, float* __restrict__ out, int64_t o_k,
               int64_t o_r, int64_t o_L, const DevStatus* skip, DevStatus* st) {
   if (skip != nullptr && skip->orth_fail) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  TtmSmem& sm = *reinterpret_cast<TtmSmem*>(
+  constexpr int X_STAGES = TtmGeo<NPAD>::X_STAGES, M_TILE = TtmGeo<NPAD>::M_TILE;
+  TtmSmem<NPAD>& sm = *reinterpret_cast<TtmSmem<NPAD>*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // tpr > 0: tiles never straddle r (tpr tiles of 128 l per r, rows l >= L are
-  // zero-filled by TMA and not written); tpr == 0: tiles of 128 consecutive j
-  const int ntiles = tpr > 0 ? (int)(tpr * (J / L)) : (int)((J + TILE_J - 1) / TILE_J);
+  // zero-filled by TMA and not written); slab tiles of tr whole r when L < 128
+  // (rows = L * tr consecutive j); otherwise tiles of 128 consecutive j
+  const int64_t Rt = J / L;
+  const bool slab = !M1 && tpr == 0 && bl < TILE_J;   // tiles of tr whole r-slabs of L < 128 rows each
+  const int ntiles = tpr > 0 ? (int)(tpr * Rt) : slab ? (int)((Rt + tr - 1) / tr) : (int)((J + TILE_J - 1) / TILE_J);
+  const int tile_rows = slab ? bl * tr : TILE_J;     // TMEM lanes holding data
+  const uint32_t xbytes = (uint32_t)((M1 ? TILE_J : bl * tr) * BI * 4);
   const int nst = (I + BI - 1) / BI;                  // stages per tile
   constexpr uint32_t idesc = idesc_tf32(128, NPAD);
 
@@ -121,7 +141,7 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 
   if (warp == PRODUCER_WARP) {
     if (lane == 0) {
-      const uint32_t bytes = (uint32_t)(TILE_J * BI * 4 + M_TILE * 4);
+      const uint32_t bytes = xbytes + (uint32_t)(M_TILE * 4);
       for (int g = 0; g < total && ok; ++g) {
         const int s = g % X_STAGES;
         const uint32_t ph = (uint32_t)(g / X_STAGES) & 1u;
@@ -133,6 +153,8 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           tma_load_2d(sm.x[s], &tmX, ib, tile * TILE_J, &sm.full_x[s]);
         } else if (tpr > 0) {
           tma_load_3d(sm.x[s], &tmX, (tile % tpr) * TILE_J, ib, tile / tpr, &sm.full_x[s]);
+        } else if (slab) {                            // r past Rt in the last slab tile reads zeros
+          tma_load_3d(sm.x[s], &tmX, 0, ib, tile * tr, &sm.full_x[s]);
         } else {
           const int64_t j0 = (int64_t)tile * TILE_J, r0 = j0 / L;
           tma_load_3d(sm.x[s], &tmX, (int)(j0 - r0 * L), ib, (int)r0, &sm.full_x[s]);
@@ -172,6 +194,7 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     const int row = quad * 32 + lane;                 // j within the tile = TMEM lane
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     const int xt = tid & 127;                         // thread index within the warpgroup
+    const int xoff = M1 ? 0 : (row / bl) * BI * bl + row % bl;   // strided: row = l' + bl r' -> [r'][0][l']
     for (int g = wg; g < total && ok; g += 2) {
       const int s = g % X_STAGES, a = g % A_STAGES;
       if (!mbar_wait(&sm.full_x[s], (uint32_t)(g / X_STAGES) & 1u, abort_flag)) { ok = false; break; }
@@ -189,12 +212,14 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           split_tf32(v.z, hi[4 * c + 2], lo[4 * c + 2]);
           split_tf32(v.w, hi[4 * c + 3], lo[4 * c + 3]);
         }
-      } else {
-        // strided tile [r'][i][l']: row = l' + BL r'
-        const int bl = 1 << bl_bits;
-        const float* xr = sm.x[s] + ((row >> bl_bits) * BI) * bl + (row & (bl - 1));
+      } else if (row < tile_rows) {
+        // strided tile [r'][i][l']
+        const float* xr = sm.x[s] + xoff;
 #pragma unroll
         for (int i = 0; i < BI; ++i) split_tf32(xr[i * bl], hi[i], lo[i]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < BI; ++i) hi[i] = lo[i] = 0u;   // idle lane of a slab tile
       }
       const uint32_t col = tmem + (uint32_t)(A_COL0 + a * A_STAGE_COLS) + lane_base;
       uint32_t h16[16], l16[16];
@@ -233,7 +258,9 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       if (!mbar_wait(&sm.d_full[buf], (uint32_t)(tl >> 1) & 1u, abort_flag)) { ok = false; break; }
       tc_fence_after();
       const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
-      int64_t j = (int64_t)tile * TILE_J + quad * 32 + lane;
+      const int64_t tj0 = slab ? (int64_t)tile * tr * L : (int64_t)tile * TILE_J;   // first j of the tile
+      int64_t j = tj0 + quad * 32 + lane;
+      if (quad * 32 + lane >= tile_rows) j = J;
       if (tpr > 0) {                                   // row l of this r's tile; l >= L is padding
         const int64_t l = (int64_t)(tile % tpr) * TILE_J + quad * 32 + lane;
         j = (l < L) ? l + L * (int64_t)(tile / tpr) : J;
@@ -244,7 +271,7 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         // rows of the output are contiguous in k (row j at out + j*o_r): stage 32 rows x
         // 16 columns per warp and store two 64-byte row segments per instruction
         float* stg = sm.ostage[quad];
-        const int64_t jw = (int64_t)tile * TILE_J + quad * 32;   // first row of this warp
+        const int64_t jw = tj0 + quad * 32;                       // first row of this warp
 #pragma unroll
         for (int c0 = 0; c0 < NPAD; c0 += 16) {
           uint32_t v[16];
@@ -257,7 +284,7 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           for (int q = 0; q < 16; ++q) {
             const int rr = 2 * q + (lane >> 4), cc = lane & 15;
             const int64_t jr = jw + rr;
-            if (c0 + cc < K && jr < J) out[jr * o_r + c0 + cc] = stg[rr * 17 + cc];
+            if (c0 + cc < K && jr < J && quad * 32 + rr < tile_rows) out[jr * o_r + c0 + cc] = stg[rr * 17 + cc];
           }
           __syncwarp();
         }
@@ -292,41 +319,50 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
 }
 
 // ---------------------------------------------------------------- host side
-// Tile geometry of a strided view: BL = l per tile row block (0 if unsupported),
-// and whether tiles are laid out per r (tpr = ceil(L / 128) tiles of 128 l for
-// each r, the last one partial) because 128 consecutive j would straddle r.
-int strided_bl(const View& x, int* tpr) {
+// Tile geometry of a strided view: the box's l extent (0 if unsupported; below
+// 128 it selects slab tiles, when L < 128 and Rt > 1), the r-slabs per tile
+// tr = floor(128 / L) of slab tiles, and tpr > 0 when
+// tiles are laid out per r (tpr = ceil(L / 128) tiles of 128 l for each r, the
+// last one partial) because 128 consecutive j would straddle r.
+int strided_bl(const View& x, int* tr, int* tpr) {
   *tpr = 0;
+  *tr = 1;
   if (x.L < 4 || x.L % 4 != 0) return 0;
   if (x.Rt == 1 && x.L >= 128) return 128;
   if (x.L % 128 == 0) return 128;
-  if (x.L == 32 || x.L == 64) return (int)x.L;
+  if (x.L < 128) {
+    *tr = (int)(128 / x.L);
+    return (int)x.L;
+  }
   *tpr = (int)((x.L + TILE_J - 1) / TILE_J);
   return 128;
 }
 
 template <int NPAD, bool M1>
-cudaError_t launch_npad(const CUtensorMap& tmX, const CUtensorMap& tmM, int I, int64_t L, int64_t J, int bl_bits,
+cudaError_t launch_npad(const CUtensorMap& tmX, const CUtensorMap& tmM, int I, int64_t L, int64_t J, int bl, int tr,
                         int tpr, int K, const OView& out, const DevStatus* skip, DevStatus* st, cudaStream_t stream) {
-  const size_t smem = sizeof(TtmSmem) + 1024;
+  const size_t smem = sizeof(TtmSmem<NPAD>) + 1024;
+  static_assert(sizeof(TtmSmem<NPAD>) + 1024 <= 232448, "TTM stages exceed shared memory");
   cudaError_t e = allow_dynamic_smem((const void*)tc_ttm_kernel<NPAD, M1>, smem);
   if (e != cudaSuccess) return e;
-  const int ntiles = tpr > 0 ? (int)(tpr * (J / L)) : (int)((J + TILE_J - 1) / TILE_J);
+  const int64_t Rt = J / L;
+  const bool slab = !M1 && tpr == 0 && bl < TILE_J;
+  const int ntiles = tpr > 0 ? (int)(tpr * Rt) : slab ? (int)((Rt + tr - 1) / tr) : (int)((J + TILE_J - 1) / TILE_J);
   const int grid = std::min(ntiles, device_sms());
   const int64_t o_L = out.o_L > 0 ? out.o_L : L;
-  tc_ttm_kernel<NPAD, M1><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmM, I, L, J, bl_bits, tpr, K, out.p,
+  tc_ttm_kernel<NPAD, M1><<<grid, NUM_THREADS, smem, stream>>>(tmX, tmM, I, L, J, bl, tr, tpr, K, out.p,
                                                                 out.o_k, out.o_r, o_L, skip, st);
   return cudaGetLastError();
 }
 
 template <bool M1>
-cudaError_t launch_m(const CUtensorMap& tmX, const CUtensorMap& tmM, int I, int64_t L, int64_t J, int bl_bits,
+cudaError_t launch_m(const CUtensorMap& tmX, const CUtensorMap& tmM, int I, int64_t L, int64_t J, int bl, int tr,
                      int tpr, int K, const OView& out, const DevStatus* skip, DevStatus* st, cudaStream_t stream) {
   switch (((K + 15) / 16) * 16) {
-    case 16: return launch_npad<16, M1>(tmX, tmM, I, L, J, bl_bits, tpr, K, out, skip, st, stream);
-    case 32: return launch_npad<32, M1>(tmX, tmM, I, L, J, bl_bits, tpr, K, out, skip, st, stream);
-    case 48: return launch_npad<48, M1>(tmX, tmM, I, L, J, bl_bits, tpr, K, out, skip, st, stream);
-    default: return launch_npad<64, M1>(tmX, tmM, I, L, J, bl_bits, tpr, K, out, skip, st, stream);
+    case 16: return launch_npad<16, M1>(tmX, tmM, I, L, J, bl, tr, tpr, K, out, skip, st, stream);
+    case 32: return launch_npad<32, M1>(tmX, tmM, I, L, J, bl, tr, tpr, K, out, skip, st, stream);
+    case 48: return launch_npad<48, M1>(tmX, tmM, I, L, J, bl, tr, tpr, K, out, skip, st, stream);
+    default: return launch_npad<64, M1>(tmX, tmM, I, L, J, bl, tr, tpr, K, out, skip, st, stream);
   }
 }
 
@@ -338,8 +374,8 @@ bool tc_ttm_supported(const View& x, int64_t m_i, int64_t m_k, int K, const OVie
   const int64_t J = x.L * x.Rt;
   if (J < TILE_J || J > (int64_t(1) << 40)) return false;
   if (x.L == 1) return x.s_i == 1 && x.s_r == x.I && x.I % 4 == 0;   // X(i, j) = X[i + I*j]
-  int tpr = 0;
-  if (strided_bl(x, &tpr) == 0 || x.s_i % 4 != 0 || (x.Rt > 1 && x.s_r % 4 != 0)) return false;
+  int tr = 1, tpr = 0;
+  if (strided_bl(x, &tr, &tpr) == 0 || x.s_i % 4 != 0 || (x.Rt > 1 && x.s_r % 4 != 0)) return false;
   if (tpr > 0 && out.o_L > 0 && out.o_L != x.L) return false;     // per-r tiles split j by the input's L
   if (tpr > 0 && (int64_t)tpr * x.Rt >= (int64_t(1) << 31)) return false;
   return x.Rt < (int64_t(1) << 31) && x.L < (int64_t(1) << 31);
@@ -353,7 +389,7 @@ cudaError_t launch_tc_ttm(const View& x, const float* Mp, int64_t m_k, int K, co
   {
     const uint64_t dims[2] = {(uint64_t)I, (uint64_t)K};
     const uint64_t strides[1] = {(uint64_t)m_k};
-    const uint32_t box[2] = {BI, 64};
+    const uint32_t box[2] = {BI, (uint32_t)(((K + 15) / 16) * 16)};   // NPAD rows, k >= K zero-filled
     if (!make_tmap_f32(&tmM, Mp, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorNotSupported;
   }
   if (x.L == 1) {
@@ -361,20 +397,18 @@ cudaError_t launch_tc_ttm(const View& x, const float* Mp, int64_t m_k, int K, co
     const uint64_t strides[1] = {(uint64_t)I};
     const uint32_t box[2] = {BI, TILE_J};
     if (!make_tmap_f32(&tmX, x.p, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B)) return cudaErrorNotSupported;
-    return launch_m<true>(tmX, tmM, (int)I, 1, J, 0, 0, K, out, skip, st, stream);
+    return launch_m<true>(tmX, tmM, (int)I, 1, J, 0, 1, 0, K, out, skip, st, stream);
   }
-  int tpr = 0;
-  const int bl = strided_bl(x, &tpr);
+  int tr = 1, tpr = 0;
+  const int bl = strided_bl(x, &tr, &tpr);
   if (bl == 0) return cudaErrorNotSupported;
-  int bits = 0;
-  while ((1 << bits) < bl) ++bits;
   // always rank 3 (the producer issues 3-D copies); a matrix view gets a unit r extent
   const uint64_t dims[3] = {(uint64_t)x.L, (uint64_t)I, (uint64_t)x.Rt};
   const uint64_t strides[2] = {(uint64_t)x.s_i, x.Rt > 1 ? (uint64_t)x.s_r : (uint64_t)x.s_i * (uint64_t)I};
-  const uint32_t box[3] = {(uint32_t)bl, BI, (uint32_t)(TILE_J / bl)};
+  const uint32_t box[3] = {(uint32_t)bl, BI, (uint32_t)tr};
   const bool okmap = make_tmap_f32(&tmX, x.p, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE);
   if (!okmap) return cudaErrorNotSupported;
-  return launch_m<false>(tmX, tmM, (int)I, x.L, J, bits, tpr, K, out, skip, st, stream);
+  return launch_m<false>(tmX, tmM, (int)I, x.L, J, bl, tr, tpr, K, out, skip, st, stream);
 }
 
 }  // namespace rhosvd

@@ -142,7 +142,11 @@ def test_tc_sketch_mode1_parity(dims, K):
 # short modes (I <= 128, L % 64 == 0) stage 64 j x 128 rows.
 TC_STRIDED_CASES = [((32, 512, 40), 1, 42), ((16, 100, 70), 1, 16), ((128, 300, 9), 1, 33),
                     ((32, 32, 600), 2, 64), ((16, 8, 40, 12), 2, 20), ((32, 16, 8, 36), 3, 7),
-                    ((64, 128, 30), 1, 26)]
+                    ((64, 128, 30), 1, 26),
+                    # more stage blocks than CTAs (blocks dealt round-robin, ragged last block)
+                    ((64, 130, 77), 0, 42), ((64, 40, 200), 1, 26),
+                    # rows of X_(n) far apart (the last mode of a 4-way tensor)
+                    ((16, 16, 16, 64), 3, 26)]
 
 
 @pytest.mark.parametrize("dims,mode,K", TC_STRIDED_CASES)
@@ -158,7 +162,9 @@ def test_tc_sketch_strided_parity(dims, mode, K):
 
 
 @pytest.mark.parametrize("dims,mode,K", [((512, 64, 64), 0, 42), ((128, 36, 111), 0, 7), ((32, 512, 40), 1, 42),
-                                         ((16, 8, 40, 12), 2, 20), ((100, 48, 50), 0, 33)])
+                                         ((16, 8, 40, 12), 2, 20), ((100, 48, 50), 0, 33),
+                                         # short last mode with rows 4 MB apart: 64-j stages generate in-kernel
+                                         ((1024, 1024, 6), 2, 26)])
 def test_seeded_sketch_generates_omega_in_kernel(dims, mode, K):
     """With no explicit Omega the tensor-core sketch draws the test matrix inside
     the kernel; it equals, bit for bit, the sketch with the materialised matrix."""
@@ -208,7 +214,9 @@ TC_TTM_STRIDED_CASES = [((64, 96, 50), 1, 42), ((32, 48, 30), 1, 16), ((256, 40,
                         ((128, 8, 7), 1, 5),
                         # per-r tiles (128 consecutive j would straddle r): L = 40, 200, 720, 12
                         ((40, 96, 12), 1, 40), ((200, 64, 5), 1, 26), ((36, 20, 40, 3), 2, 33),
-                        ((12, 16, 30), 1, 9)]
+                        ((12, 16, 30), 1, 9),
+                        # slab tiles of floor(128 / L) whole r: L = 100 (one), 44 (two), 40 (three, ragged last tile)
+                        ((100, 64, 7), 1, 17), ((44, 24, 50), 1, 20), ((40, 128, 130), 1, 40)]
 
 
 @pytest.mark.parametrize("dims,mode,K", TC_TTM_STRIDED_CASES)
@@ -480,6 +488,44 @@ def test_batch_graph_matches_eager():
     assert batch.device_status() == 0
     for (g_b, u_b), (X, dims, ranks) in zip(batch.results(), items):
         g_e, u_e = R().rhosvd_decompose(X, dims, ranks, p=5, q=1, seed=5)
+        np.testing.assert_array_equal(host(g_b), host(g_e))
+        for a, c in zip(u_b, u_e):
+            np.testing.assert_array_equal(host(a), host(c))
+
+
+def test_rpet_graph_replay_matches_eager():
+    """The captured form of R-PET (test matrices drawn into memory for some modes,
+    generated in-kernel for others) gives bitwise the eager result."""
+    dims, ranks = (96, 80, 64), (8, 7, 6)      # modes 1 and 3 draw Omega into memory, mode 2 in-kernel
+    x = lowrank_tensor(dims, ranks, 43, noise=1e-3)
+    X = dev(x)
+    g_ea, u_ea = R().rhosvd_decompose(X, dims, ranks, algo="rpet", p=5, seed=4)
+    g_ea, u_ea = host(g_ea), [host(u) for u in u_ea]
+    graph = R().DecomposeGraph(X, dims, ranks, algo="rpet", p=5, seed=4)
+    for _ in range(2):
+        graph.replay()
+        torch.cuda.synchronize()
+        g_gr, u_gr = graph.result()
+        np.testing.assert_array_equal(host(g_gr), g_ea)
+        for a, b in zip(u_gr, u_ea):
+            np.testing.assert_array_equal(host(a), b)
+
+
+def test_rpet_batch_graph_matches_eager():
+    """R-PET decompositions on parallel graph branches: each result is bitwise its
+    eager one."""
+    rng = np.random.default_rng(72)
+    items = []
+    for b in range(6):
+        dims = tuple(int(v) for v in rng.integers(40, 110, size=3))
+        ranks = tuple(int(min(r, d)) for r, d in zip(rng.integers(4, 10, size=3), dims))
+        items.append((dev(lowrank_tensor(dims, ranks, 800 + b, noise=1e-3)), dims, ranks))
+    batch = R().BatchGraph(items, branches=3, algo="rpet", p=5, seed=6)
+    batch.replay()
+    torch.cuda.synchronize()
+    assert batch.device_status() == 0
+    for (g_b, u_b), (X, dims, ranks) in zip(batch.results(), items):
+        g_e, u_e = R().rhosvd_decompose(X, dims, ranks, algo="rpet", p=5, seed=6)
         np.testing.assert_array_equal(host(g_b), host(g_e))
         for a, c in zip(u_b, u_e):
             np.testing.assert_array_equal(host(a), host(c))
