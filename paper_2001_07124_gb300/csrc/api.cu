@@ -100,7 +100,7 @@ void op_gram_df(Ctx& c, const View& x, const WView& w, int K, double* Gd) {
 // Gd (K x K, FP64) = A^T A for a tall matrix; exact = FP64-accurate products
 void op_gram_matrix(Ctx& c, const float* A, int64_t m, int K, int64_t ld, double* Gd, bool exact = true) {
   Scope sc(c);
-  GramPlan pl = plan_gram(m, K);
+  GramPlan pl = plan_gram(m, K, exact);
   double* part = c.take<double>((size_t)pl.ctas * K * K);
   c.launches += 2;
   if (!c.dry) c.check(launch_gram(A, m, K, ld, Gd, part, exact, c.s));
@@ -490,15 +490,16 @@ void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const
     const float* om = (Omega_t != nullptr && Omega_t[n] != nullptr) ? Omega_t[n] : Omt[n];
     float* A = Pt[n];
     {
-      // A(s, k) = sum_i Omega~(s, i) Q(i, k)
-      View qv;
-      qv.p = Ys[n];
-      qv.L = 1;
-      qv.I = I;
-      qv.Rt = K;
-      qv.s_i = 1;
-      qv.s_r = I;
-      op_ttm(c, qv, om, S, 1, S, OView{A, 1, S});
+      // A(s, k) = sum_i Omega~(s, i) Q(i, k): the sketch of the S x I matrix
+      // Omega~ (column-major) with W = Q, split over i
+      View ov;
+      ov.p = om;
+      ov.L = 1;
+      ov.I = S;
+      ov.Rt = I;
+      ov.s_i = 1;
+      ov.s_r = S;
+      op_sketch(c, ov, WView{Ys[n], 1, I}, K, A, S);
     }
     op_gram_matrix(c, A, S, K, S, Gd);
     c.launches += 2;

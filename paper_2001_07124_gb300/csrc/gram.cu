@@ -60,6 +60,7 @@ gram_kernel(const float* __restrict__ A, int64_t m, int K, int64_t ld, int64_t r
       tile[c * LD + r] = (r < nrow) ? __ldg(A + (rt + r) + (int64_t)c * ld) : 0.f;
     }
     __syncthreads();
+    const int nr8 = (nrow + 7) & ~7;              // rows past nrow are zero in the tile
 #pragma unroll
     for (int t = 0; t < PT; ++t) {
       if (tid + t * GR_THREADS >= P) break;
@@ -67,13 +68,18 @@ gram_kernel(const float* __restrict__ A, int64_t m, int K, int64_t ld, int64_t r
       const float* cb = tile + (pab[t] >> 16) * LD;
       if (EXACT) {
         df64 acc = xacc[t];
+        if (nrow == GR_TILE) {                      // full tile: compile-time trip count
 #pragma unroll 8
-        for (int r = 0; r < GR_TILE; ++r) df64_fma(acc, ca[r], cb[r]);
+          for (int r = 0; r < GR_TILE; ++r) df64_fma(acc, ca[r], cb[r]);
+        } else {
+#pragma unroll 8
+          for (int r = 0; r < nr8; ++r) df64_fma(acc, ca[r], cb[r]);
+        }
         xacc[t] = acc;
       } else {
         float s = 0.f;
 #pragma unroll 8
-        for (int r = 0; r < GR_TILE; ++r) s = fmaf(ca[r], cb[r], s);
+        for (int r = 0; r < nr8; ++r) s = fmaf(ca[r], cb[r], s);
         dacc[t] += (double)s;
       }
     }
@@ -240,11 +246,14 @@ cudaError_t launch_gram_t(const float* A, int64_t m, int K, int64_t ld, double* 
 
 }  // namespace
 
-GramPlan plan_gram(int64_t m, int K) {
+GramPlan plan_gram(int64_t m, int K, bool exact) {
   GramPlan pl;
-  // enough rows per CTA that the pair bookkeeping amortises, at most ~2 CTAs per SM
+  // enough rows per CTA that the pair bookkeeping amortises, at most ~2 CTAs per SM;
+  // the double-float path, whose cost is its arithmetic, goes down to 16-row
+  // CTAs on short matrices (a 512-row basis is then spread over 32 SMs, not 8)
+  const int64_t step = (exact && m < (int64_t)GR_TARGET_CTAS * GR_TILE) ? 16 : GR_TILE;
   int64_t rows = (m + GR_TARGET_CTAS - 1) / GR_TARGET_CTAS;
-  rows = std::max<int64_t>(GR_TILE, ((rows + GR_TILE - 1) / GR_TILE) * GR_TILE);
+  rows = std::max<int64_t>(step, ((rows + step - 1) / step) * step);
   pl.rows_per_cta = rows;
   pl.ctas = (int)std::max<int64_t>(1, (m + rows - 1) / rows);
   (void)K;
@@ -253,7 +262,7 @@ GramPlan plan_gram(int64_t m, int K) {
 
 cudaError_t launch_gram(const float* A, int64_t m, int K, int64_t ld, double* G, double* part, bool exact,
                         cudaStream_t st) {
-  GramPlan pl = plan_gram(m, K);
+  GramPlan pl = plan_gram(m, K, exact);
   return exact ? launch_gram_t<true>(A, m, K, ld, G, part, pl.ctas, pl.rows_per_cta, st)
                : launch_gram_f32(A, m, K, ld, G, part, pl.ctas, pl.rows_per_cta, st);
 }

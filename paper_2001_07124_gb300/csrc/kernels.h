@@ -42,6 +42,7 @@ struct OView {
 struct SketchPlan {
   int tiles_i, tiles_k, splits;
   int64_t jchunk;
+  int tu;           // outputs per thread and dimension: 16 tu x 16 tu per CTA
 };
 SketchPlan plan_sketch(int64_t I, int K, int64_t J);
 size_t sketch_partial_floats(const SketchPlan& pl, int64_t I, int K);
@@ -103,7 +104,7 @@ struct GramPlan {
   int ctas;
   int64_t rows_per_cta;
 };
-GramPlan plan_gram(int64_t m, int K);
+GramPlan plan_gram(int64_t m, int K, bool exact);
 cudaError_t launch_gram(const float* A, int64_t m, int K, int64_t ld, double* G, double* part, bool exact,
                         cudaStream_t st);
 

@@ -15,8 +15,6 @@ namespace rhosvd {
 
 namespace {
 
-constexpr int SK_BI = 64;    // rows i per CTA
-constexpr int SK_BK = 64;    // columns k per CTA
 constexpr int SK_BJ = 16;    // contraction step
 constexpr int SK_THREADS = 256;
 constexpr int TARGET_CTAS = 608;   // 4 CTAs per SM on 152 SMs
@@ -36,9 +34,14 @@ struct Acc<true> {
   __device__ __forceinline__ double out() const { return df64_to_double(v); }
 };
 
-template <bool DF, typename OutT>
+// Output tile of 16 TU x 16 TU per CTA (TU values per thread in each dimension):
+// TU = 4 in general, TU = 2 when I and K are both at most 64, where one 64 x 64
+// tile would leave the GPU idle and spend its (double-float) multiply-adds on
+// padding.
+template <bool DF, typename OutT, int TU>
 __global__ void __launch_bounds__(SK_THREADS)
 sketch_partial_kernel(View x, WView w, int K, int64_t jchunk, OutT* __restrict__ part) {
+  constexpr int SK_BI = 16 * TU, SK_BK = 16 * TU;
   __shared__ float Xs[SK_BJ][SK_BI + 1];
   __shared__ float Ws[SK_BJ][SK_BK + 1];
   __shared__ int64_t xoff[SK_BJ];
@@ -54,7 +57,7 @@ sketch_partial_kernel(View x, WView w, int K, int64_t jchunk, OutT* __restrict__
   const bool x_i_fast = (x.s_i == 1);
   const bool w_k_fast = (w.w_k == 1);
 
-  Acc<DF> acc[4][4];
+  Acc<DF> acc[TU][TU];
 
   for (int64_t jt = jb; jt < je; jt += SK_BJ) {
     if (tid < SK_BJ) {
@@ -86,25 +89,25 @@ sketch_partial_kernel(View x, WView w, int K, int64_t jchunk, OutT* __restrict__
     __syncthreads();
 #pragma unroll
     for (int jj = 0; jj < SK_BJ; ++jj) {
-      float a[4], b[4];
+      float a[TU], b[TU];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < TU; ++u) {
         a[u] = Xs[jj][tx + 16 * u];
         b[u] = Ws[jj][ty + 16 * u];
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < TU; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v].fma(a[u], b[v]);
+        for (int v = 0; v < TU; ++v) acc[u][v].fma(a[u], b[v]);
     }
     __syncthreads();
   }
   OutT* dst = part + (int64_t)blockIdx.z * x.I * K;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
+  for (int u = 0; u < TU; ++u) {
     const int64_t i = i0 + tx + 16 * u;
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
+    for (int v = 0; v < TU; ++v) {
       const int k = k0 + ty + 16 * v;
       if (i < x.I && k < K) dst[(int64_t)k * x.I + i] = (OutT)acc[u][v].out();
     }
@@ -246,6 +249,15 @@ ttm_kernel(View x, const float* __restrict__ M, int64_t m_i, int64_t m_k, int K,
   }
 }
 
+template <bool DF, typename OutT>
+void launch_partials(const SketchPlan& pl, const View& x, const WView& w, int K, OutT* part, cudaStream_t st) {
+  const dim3 grid(pl.tiles_i, pl.tiles_k, pl.splits);
+  if (pl.tu == 2)
+    sketch_partial_kernel<DF, OutT, 2><<<grid, SK_THREADS, 0, st>>>(x, w, K, pl.jchunk, part);
+  else
+    sketch_partial_kernel<DF, OutT, 4><<<grid, SK_THREADS, 0, st>>>(x, w, K, pl.jchunk, part);
+}
+
 }  // namespace
 
 cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes) {
@@ -272,13 +284,15 @@ cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes) {
 
 SketchPlan plan_sketch(int64_t I, int K, int64_t J) {
   SketchPlan pl;
-  pl.tiles_i = (int)((I + SK_BI - 1) / SK_BI);
-  pl.tiles_k = (K + SK_BK - 1) / SK_BK;
+  pl.tu = (I <= 64 && K <= 64) ? 2 : 4;         // small outputs: four times the CTAs, less padding
+  const int tile = 16 * pl.tu;
+  pl.tiles_i = (int)((I + tile - 1) / tile);
+  pl.tiles_k = (K + tile - 1) / tile;
   const int64_t tiles = (int64_t)pl.tiles_i * pl.tiles_k;
   int64_t want = std::max<int64_t>(1, TARGET_CTAS / std::max<int64_t>(1, tiles));
   int64_t chunk = (J + want - 1) / want;
   chunk = ((chunk + SK_BJ - 1) / SK_BJ) * SK_BJ;
-  chunk = std::max<int64_t>(chunk, 4 * SK_BJ);
+  chunk = std::max<int64_t>(chunk, (J > 4096 ? 4 : 1) * SK_BJ);   // short contractions: one step per CTA
   pl.jchunk = chunk;
   pl.splits = (int)std::max<int64_t>(1, (J + chunk - 1) / chunk);
   return pl;
@@ -292,8 +306,7 @@ cudaError_t launch_sketch(const View& x, const WView& w, int K, float* Y, int64_
                           cudaStream_t st) {
   const int64_t J = x.L * x.Rt;
   SketchPlan pl = plan_sketch(x.I, K, J);
-  dim3 grid(pl.tiles_i, pl.tiles_k, pl.splits);
-  sketch_partial_kernel<false, float><<<grid, SK_THREADS, 0, st>>>(x, w, K, pl.jchunk, ws_part);
+  launch_partials<false, float>(pl, x, w, K, ws_part, st);
   const int64_t n = x.I * K;
   reduce_partials_kernel<float, float><<<(unsigned)((n + 31) / 32), 32 * RD_ROWS, 0, st>>>(
       ws_part, pl.splits, x.I, K, Y, ldy);
@@ -342,8 +355,7 @@ cudaError_t launch_sketch_capped(const View& x, const WView& w, int K, float* Y,
     pl.jchunk = ((chunk + SK_BJ - 1) / SK_BJ) * SK_BJ;
     pl.splits = (int)std::max<int64_t>(1, (J + pl.jchunk - 1) / pl.jchunk);
   }
-  dim3 grid(pl.tiles_i, pl.tiles_k, pl.splits);
-  sketch_partial_kernel<false, float><<<grid, SK_THREADS, 0, st>>>(x, w, K, pl.jchunk, part);
+  launch_partials<false, float>(pl, x, w, K, part, st);
   const int64_t n = x.I * K;
   reduce_partials_kernel<float, float><<<(unsigned)((n + 31) / 32), 32 * RD_ROWS, 0, st>>>(
       part, pl.splits, x.I, K, Y, ldy);
@@ -354,8 +366,7 @@ cudaError_t launch_sketch_df(const View& x, const WView& w, int K, double* Gd, i
                              double* ws_part, cudaStream_t st) {
   const int64_t J = x.L * x.Rt;
   SketchPlan pl = plan_sketch(x.I, K, J);
-  dim3 grid(pl.tiles_i, pl.tiles_k, pl.splits);
-  sketch_partial_kernel<true, double><<<grid, SK_THREADS, 0, st>>>(x, w, K, pl.jchunk, ws_part);
+  launch_partials<true, double>(pl, x, w, K, ws_part, st);
   const int64_t n = x.I * K;
   reduce_partials_kernel<double, double><<<(unsigned)((n + 31) / 32), 32 * RD_ROWS, 0, st>>>(
       ws_part, pl.splits, x.I, K, Gd, ldg);
