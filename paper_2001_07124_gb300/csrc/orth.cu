@@ -8,7 +8,7 @@
 // close to I; Y R^-1 is applied by row-parallel forward substitution.
 // The first pass only rejects pivots that are numerically non-positive
 // (<= K * 1e-15 * max diag): for larger condition numbers Q1 = Y R^-1 is still
-// formed and the second pass judges it; a second-pass pivot below 1e-4 * max
+// formed and the second pass assesses it; a second-pass pivot below 1e-4 * max
 // diag (cond(Q1) above 100, so Q2 would not be orthonormal to FP32 accuracy)
 // or a non-finite value marks a breakdown; the later kernels of the sequence
 // then skip and a Householder QR

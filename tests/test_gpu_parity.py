@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, element by element or by subspace, through the C ABI.
 
-Tolerances (derived in the design doc):
+Tolerances (FP32 arithmetic against an FP64 reference):
 * sketches / TTMs (FP32 arithmetic, long sums): |gpu - oracle| <= 1e-5 * (|A| |B|)
   elementwise, i.e. relative to the sum of absolute products;
 * Gaussian test matrices: |gpu - oracle| <= 2^-21 max(1, |z|) (FP32 logf/sincospi
