@@ -161,24 +161,45 @@ trsm_rows_kernel(float* __restrict__ Y, int64_t m, int K, int64_t ld, const floa
   if (tid < KB) dinv[tid] = (tid < K) ? 1.f / L[tid + tid * K] : 0.f;
   __syncthreads();
   if (!live) return;
-  // forward: q_c = (y_c - sum_{k<c} L(c,k) q_k) / L(c,c)
+  // forward: q_c = (y_c - sum_{k<c} L(c,k) q_k) / L(c,c); up to KB = 64 each dot
+  // product runs as two interleaved partial sums, halving the dependent
+  // multiply-add chain (wider rows would spill the second accumulator)
+  constexpr bool two = KB <= 64;
 #pragma unroll
   for (int c = 0; c < KB; ++c) {
-    float s = q[c];
+    float s0 = q[c], s1 = 0.f;
     const float* lrow = Lr + c * KB;
+    if (two) {
 #pragma unroll
-    for (int k = 0; k < c; ++k) s = fmaf(-lrow[k], q[k], s);
-    q[c] = s * dinv[c];
+      for (int k = 0; k + 1 < c; k += 2) {
+        s0 = fmaf(-lrow[k], q[k], s0);
+        s1 = fmaf(-lrow[k + 1], q[k + 1], s1);
+      }
+      if (c & 1) s0 = fmaf(-lrow[c - 1], q[c - 1], s0);
+    } else {
+#pragma unroll
+      for (int k = 0; k < c; ++k) s0 = fmaf(-lrow[k], q[k], s0);
+    }
+    q[c] = (s0 + s1) * dinv[c];
   }
   if (mode == 1) {
     // backward: x_c = (q_c - sum_{k>c} L(k,c) x_k) / L(c,c)
 #pragma unroll
     for (int c = KB - 1; c >= 0; --c) {
-      float s = q[c];
+      float s0 = q[c], s1 = 0.f;
       const float* lcol = Lc + c * KB;
+      if (two) {
 #pragma unroll
-      for (int k = c + 1; k < KB; ++k) s = fmaf(-lcol[k], q[k], s);
-      q[c] = s * dinv[c];
+        for (int k = c + 1; k + 1 < KB; k += 2) {
+          s0 = fmaf(-lcol[k], q[k], s0);
+          s1 = fmaf(-lcol[k + 1], q[k + 1], s1);
+        }
+        if ((KB - 1 - c) & 1) s0 = fmaf(-lcol[KB - 1], q[KB - 1], s0);
+      } else {
+#pragma unroll
+        for (int k = c + 1; k < KB; ++k) s0 = fmaf(-lcol[k], q[k], s0);
+      }
+      q[c] = (s0 + s1) * dinv[c];
     }
   }
 #pragma unroll
