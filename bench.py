@@ -202,7 +202,7 @@ def run_serving(args):
     pkg.build()
     rng = np.random.default_rng(1005)
     n = args.serve
-    rate = 200.0
+    rate = float(args.serve_rate)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
     sizes = np.clip(np.rint(np.exp(rng.uniform(np.log(64), np.log(768), size=n)) / 64) * 64, 64, 768).astype(int)
     ranks = np.minimum(rng.integers(8, 65, size=n), sizes)
@@ -372,6 +372,7 @@ def main():
     ap.add_argument("--mode", type=int, default=1, help="mode (1-based) of --primitive sketch/power/orth")
     ap.add_argument("--no-graph", action="store_true", help="launch the decomposition kernel by kernel")
     ap.add_argument("--serve", type=int, default=0, metavar="N", help="serving run with N requests")
+    ap.add_argument("--serve-rate", type=float, default=200.0, metavar="R", help="Poisson arrival rate (req/s)")
     ap.add_argument("--batch", type=int, default=0, metavar="N", help="batched run with N small tensors")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
