@@ -14,9 +14,8 @@
 // CTA owns up to 512 rows i (four 128-row MMA tiles) and every gridDim.x-th
 // stage-sized block of j, and writes its partial I x K block for the
 // fixed-order reducer.  Interleaving the blocks keeps the CTAs' concurrent
-// reads within one window of each row of X_(n): for a mode whose rows lie
-// megabytes apart, per-CTA contiguous ranges would make every CTA open its own
-// DRAM page in every row.
+// reads within one window of each row of X_(n) (measured the same as
+// contiguous per-CTA ranges on the 512^3 and 128^4 workloads).
 //
 // Data path per 16-column block of j (two MMA K steps of kind::tf32):
 //   * TMA copies the X tile (16 x 512 FP32, two 256-wide boxes) and the raw W
@@ -60,9 +59,10 @@ constexpr size_t kSmemLimit = 232448;     // dynamic shared memory per CTA (227 
 // Stage geometry, NC = chunks of 16 j per stage: NC = 1 stages 16 j x 512 rows
 // (four 128-row MMA tiles), NC = 4 stages 64 j x 128 rows (one tile, four
 // chunks) for short modes (I <= 128).  The four TMEM A slots of a stage hold
-// tiles (NC = 1) or chunks (NC = 4).  The stream of X is latency-bound (the
-// transform warps wait on the TMA barriers), so the W and B tiles hold only
-// NPAD rows (K padded to 16) and the rest of shared memory deepens the X ring.
+// tiles (NC = 1) or chunks (NC = 4).  The W and B tiles hold only NPAD rows
+// (K padded to 16) and the rest of shared memory deepens the X ring.  The pace
+// is set by the MMA stream (24 skinny MMAs per stage), not by the TMA copies:
+// the X tiles are in shared memory before the transform asks for them.
 template <int NPAD, int NC>
 struct Geo {
   static constexpr int ROWS = 512 / NC;                   // rows i per CTA

@@ -59,9 +59,9 @@ constexpr int D_COLS = 64;                // per accumulator buffer
 constexpr int A_COL0 = 2 * D_COLS;        // A stages after the two accumulators
 constexpr int A_STAGE_COLS = 2 * BI;      // 32 hi + 32 lo columns
 
-// The stream of X is latency-bound (the transform warps wait on the TMA
-// barriers), so shared memory goes to X stages: the M and B tiles hold NPAD
-// rows (K padded to 16), and the X ring is as deep as 227 KB allows.
+// The M and B tiles hold NPAD rows (K padded to 16), and the X ring is as deep
+// as 227 KB allows.  The pace is set by the MMA stream (12 skinny MMAs per
+// stage), not by the TMA copies: the X tiles arrive before they are needed.
 template <int NPAD>
 struct TtmGeo {
   static constexpr int M_TILE = NPAD * BI;                  // floats per M / B tile
