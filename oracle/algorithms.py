@@ -17,7 +17,7 @@ Readings taken where the paper is silent or garbled:
 """
 from __future__ import annotations
 
-from typing import Sequence
+from typing import Callable, Sequence
 
 import numpy as np
 
@@ -134,6 +134,93 @@ def rsthosvd(x: np.ndarray, ranks: Sequence[int], q: int, omegas: Sequence[np.nd
         s = fold(sn, n, dims)
         us.append(u)
     return s, us
+
+
+def randqb_ei(a: np.ndarray, tol: float, block: int, k_max: int, omega_block: Callable[[int, int, int], np.ndarray],
+              q: int = 0):
+    """Fixed-precision range finder (the blocked randomized QB with an error
+    indicator that Secs. 3 and 5 cite for rank-revealing, "fixed-precision"
+    randomized algorithms).
+
+    The basis grows by blocks of `block` columns.  Block i starts from the
+    Gaussian test block omega_block(i, J, b) (J x b, an input like every test
+    matrix here): Y = A Omega_i - Q (B Omega_i) is the part of A Omega_i outside
+    the current basis, optionally refined by q subspace-iteration steps against
+    the same deflated operator, then orthonormalised and orthogonalised once
+    more against Q.  With B_i = Q_i^T A appended to B, the indicator
+    E = ||A||_F^2 - sum_i ||B_i||_F^2 equals ||A - Q B||_F^2 = ||(I - Q Q^T) A||_F^2
+    (Q orthonormal, B = Q^T A).  The loop stops once E <= tol^2 or Q holds k_max
+    columns.  Returns Q (I x K), B (K x J) and the list of indicator values after
+    each block."""
+    a = np.asarray(a, dtype=np.float64)
+    m, j = a.shape
+    k_max = int(min(k_max, m, j))
+    qm = np.zeros((m, 0))
+    bm = np.zeros((0, j))
+    e = float(np.sum(a * a))
+    history = []
+    i = 0
+    while e > tol * tol and qm.shape[1] < k_max:
+        b = int(min(block, k_max - qm.shape[1]))
+        om = np.asarray(omega_block(i, j, b), dtype=np.float64)
+        y = a @ om - qm @ (bm @ om)
+        for _ in range(q):                                  # power steps on (I - QQ^T) A = A - Q B
+            w = orth(y)
+            z = orth(a.T @ w - bm.T @ (qm.T @ w))
+            y = a @ z - qm @ (bm @ z)
+        qi = orth(y)
+        qi = orth(qi - qm @ (qm.T @ qi))                    # re-orthogonalisation
+        bi = qi.T @ a
+        qm = np.hstack([qm, qi])
+        bm = np.vstack([bm, bi])
+        e = e - float(np.sum(bi * bi))
+        history.append(e)
+        i += 1
+    return qm, bm, history
+
+
+def truncation_rank(sigma: np.ndarray, residual: float, tol: float) -> int:
+    """Smallest r with residual + sum_{i > r} sigma_i^2 <= tol^2 (sigma descending):
+    the rank-revealing truncation of B = Ubar Sigma Vbar^T after a QB step."""
+    tail = np.concatenate([np.cumsum((sigma ** 2)[::-1])[::-1], [0.0]])   # tail[r] = sum_{i >= r} sigma_i^2
+    for r in range(len(sigma) + 1):
+        if residual + tail[r] <= tol * tol:
+            return r
+    return len(sigma)
+
+
+def rsthosvd_fixed_accuracy(x: np.ndarray, eps: float, block: int, k_max: Sequence[int],
+                            omega_block: Callable[[int, int, int, int], np.ndarray], q: int = 0):
+    """R-STHOSVD with fixed accuracy (Alg. 8 with the fixed-precision range finder
+    in place of Alg. 1, as Sec. 5 suggests).  Reading of the garbled tolerance
+    split (Eqs. DT1 and SubPro): each mode gets tol = eps ||X||_F / sqrt(N), so
+    that the sequential-truncation error identity gives
+    ||X - X_hat||_F <= eps ||X||_F.  For mode n: S_(n) -> (Q, B, E) by
+    randqb_ei, B = Ubar Sigma Vbar^T, R_n = truncation_rank(Sigma, E, tol),
+    U^(n) = Q Ubar_R, S_(n) <- Ubar_R^T B.  omega_block(n, i, J, b) is block i of
+    mode n.  Returns the core, the factors and the ranks."""
+    s = np.asarray(x, dtype=np.float64)
+    n_modes = s.ndim
+    tol = eps * float(np.linalg.norm(s)) / np.sqrt(n_modes)
+    us, ranks = [], []
+    for n in range(n_modes):
+        a = unfold(s, n)
+        qm, bm, hist = randqb_ei(a, tol, block, k_max[n], lambda i, j, b, n=n: omega_block(n, i, j, b), q=q)
+        e = hist[-1] if hist else float(np.sum(a * a))
+        if qm.shape[1] == 0:                                # the whole mode fits the tolerance at rank 0
+            r = 0
+            ubar = np.zeros((0, 0))
+        else:
+            ubar, sig, _ = np.linalg.svd(bm, full_matrices=False)
+            r = truncation_rank(sig, max(e, 0.0), tol)
+        u = qm @ ubar[:, :r] if r > 0 else np.zeros((a.shape[0], 0))
+        sn = ubar[:, :r].T @ bm if r > 0 else np.zeros((0, a.shape[1]))
+        dims = list(s.shape)
+        dims[n] = r
+        s = fold(sn, n, dims)
+        us.append(u)
+        ranks.append(r)
+    return s, us, ranks
 
 
 def pinv_lstsq(a: np.ndarray) -> np.ndarray:
