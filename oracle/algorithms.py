@@ -13,7 +13,10 @@ Readings taken where the paper is silent or garbled:
   Z = orth(A^T Q), Q = orth(A Z), q times;
 * Alg. 8 starts from S = X (its first line prints S = X_(n));
 * R-PET step 5 ("truncate") is a truncated HOSVD of the small recovered core,
-  whose factors are lifted through Q_n.
+  whose factors are lifted through Q_n;
+* fixed accuracy: the tolerance eps is relative and split evenly over the modes,
+  tol = eps ||X||_F / sqrt(N) per mode (Eqs. DT1 and SubPro disagree on the
+  split), which bounds the ST-HOSVD error by eps ||X||_F.
 """
 from __future__ import annotations
 
