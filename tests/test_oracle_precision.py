@@ -1,0 +1,127 @@
+"""What reduced precision costs R-STHOSVD on the 512^3 workload (FP64 oracle, CPU).
+
+* BF16 power iterates: the products of the power steps computed on a
+  BF16-rounded copy of the unfolding (round to nearest even), first sketch and
+  projection exact.  On mode 1 E stays within 3% (measured +2.2%); on every mode
+  it does not; one exact power step after the BF16 ones restores E.
+* The device's FP32 arithmetic: every large product as a truncating 3xTF32
+  split with FP32 accumulation, and the truncation's eigenvectors from an
+  FP32-rounded square root of B B^T.  E stays within 0.05% of exact (measured
+  +0.015%), so a larger excess on the device is not arithmetic.
+About two minutes of CPU: opt-in with RHOSVD_SLOW=1."""
+import numpy as np
+import pytest
+
+from oracle import algorithms as A
+from oracle import metrics as M
+from oracle import tensor as T
+from workloads import WORKLOADS, gaussian_matrix
+
+
+def bf16_round(a):
+    """Round to the nearest BF16 value (ties to even), returned in FP64."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    return ((u + (((u >> 16) & 1) + 0x7FFF)) & 0xFFFF0000).view(np.float32).astype(np.float64)
+
+
+def test_bf16_round_is_correct():
+    # the BF16 spacing at 1 is 2^-7
+    v = np.array([1.0, 1.0 + 2.0 ** -8, 1.0 + 3 * 2.0 ** -8, 1.0 + 3 * 2.0 ** -9, -3.14159, 1e-30], dtype=np.float32)
+    r = bf16_round(v)
+    assert r[0] == 1.0
+    assert r[1] == 1.0                                  # half a spacing: tie to the even neighbour
+    assert r[2] == 1.0 + 2.0 ** -6                      # 1.5 spacings: tie to the even neighbour above
+    assert r[3] == 1.0 + 2.0 ** -7                      # 0.75 of a spacing: nearest
+    assert r[4] == -3.140625
+    assert abs(r[5] / 1e-30 - 1) <= 2.0 ** -8
+
+
+def _brsvd(a, r, q, omega, bf16_power, exact_refine):
+    ab = bf16_round(a) if bf16_power else a
+    qm = A.orth(a @ omega)
+    for _ in range(q):
+        qm = A.orth(ab @ A.orth(ab.T @ qm))
+    for _ in range(exact_refine):
+        qm = A.orth(a @ A.orth(a.T @ qm))
+    b = qm.T @ a
+    ubar, _, _ = np.linalg.svd(b, full_matrices=False)
+    return qm @ ubar[:, :r], ubar[:, :r].T @ b
+
+
+def _rsthosvd(x, ranks, q, omegas, bf16_modes=(), exact_refine=0):
+    s = x
+    us = []
+    for n in range(s.ndim):
+        u, sn = _brsvd(T.unfold(s, n), ranks[n], q, omegas[n], n in bf16_modes, exact_refine if n in bf16_modes else 0)
+        dims = list(s.shape)
+        dims[n] = ranks[n]
+        s = T.fold(sn, n, dims)
+        us.append(u)
+    return s, us
+
+
+@pytest.mark.slow
+def test_bf16_power_products_on_mode_one_keep_the_error():
+    w = WORKLOADS["decay512_rsthosvd"]
+    x = np.asfortranarray(w.tensor().astype(np.float32).astype(np.float64))
+    shapes = A.omega_shapes(w.algo, w.dims, w.ranks, w.p)
+    omegas = [gaussian_matrix(w.omega_seed + n, r, c).astype(np.float64) for n, (r, c) in enumerate(shapes)]
+    e = {}
+    for label, kw in [("exact", {}), ("mode1", dict(bf16_modes=(0,))), ("all", dict(bf16_modes=(0, 1, 2))),
+                      ("mode1+refine", dict(bf16_modes=(0,), exact_refine=1))]:
+        g, us = _rsthosvd(x, w.ranks, w.q, omegas, **kw)
+        e[label] = M.rel_error(x, g, us)
+    assert e["mode1"] <= 1.03 * e["exact"]
+    assert e["all"] > 2 * e["exact"]
+    assert abs(e["mode1+refine"] - e["exact"]) <= 1e-3 * e["exact"]
+
+
+def _trunc_tf32(a):
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
+    return (u & np.uint32(0xFFFFE000)).view(np.float32)
+
+
+def _mm3(a, b):
+    """3xTF32 product with FP32 accumulation: a_hi b_hi + a_hi b_lo + a_lo b_hi, each
+    part truncated to TF32 as the tensor core reads it."""
+    a32, b32 = np.ascontiguousarray(a, dtype=np.float32), np.ascontiguousarray(b, dtype=np.float32)
+    ah, bh = _trunc_tf32(a32), _trunc_tf32(b32)
+    al, bl = _trunc_tf32(a32 - ah), _trunc_tf32(b32 - bh)
+    return (ah @ bh + (ah @ bl + al @ bh)).astype(np.float64)
+
+
+def test_truncating_tf32_split_is_exact_in_its_parts():
+    x = np.random.default_rng(0).standard_normal(1000).astype(np.float32)
+    hi = _trunc_tf32(x)
+    lo = x - hi
+    assert np.all(hi + lo == x)                        # the remainder is exact in FP32
+    assert np.all(np.abs(lo) < np.abs(x) * 2.0 ** -10)  # and below the TF32 spacing
+
+
+def _brsvd_device(a, r, q, omega):
+    qm = A.orth(_mm3(a, omega))
+    for _ in range(q):
+        qm = A.orth(_mm3(a, A.orth(_mm3(a.T, qm))))
+    b = _mm3(qm.T, a)
+    lam, v = np.linalg.eigh(b @ b.T)
+    root = (v * np.sqrt(np.maximum(lam, 0))).astype(np.float32).astype(np.float64)
+    ubar = np.linalg.svd(root, full_matrices=False)[0].astype(np.float32).astype(np.float64)
+    return qm @ ubar[:, :r], _mm3(ubar[:, :r].T, b)
+
+
+@pytest.mark.slow
+def test_emulated_device_arithmetic_keeps_the_error():
+    w = WORKLOADS["decay512_rsthosvd"]
+    x = np.asfortranarray(w.tensor().astype(np.float32).astype(np.float64))
+    shapes = A.omega_shapes(w.algo, w.dims, w.ranks, w.p)
+    omegas = [gaussian_matrix(w.omega_seed + n, r, c).astype(np.float64) for n, (r, c) in enumerate(shapes)]
+    g, us = _rsthosvd(x, w.ranks, w.q, omegas)
+    e_exact = M.rel_error(x, g, us)
+    s, us = x, []
+    for n in range(3):
+        u, sn = _brsvd_device(T.unfold(s, n), w.ranks[n], w.q, omegas[n])
+        dims = list(s.shape)
+        dims[n] = w.ranks[n]
+        s = T.fold(sn, n, dims)
+        us.append(u)
+    assert M.rel_error(x, s, us) <= 1.0005 * e_exact
