@@ -10,7 +10,7 @@ if ROOT not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a) and the built library")
-    config.addinivalue_line("markers", "slow: long-running CPU test, enabled with RHOSVD_SLOW=1")
+    config.addinivalue_line("markers", "slow: long-running or diagnostic test, enabled with RHOSVD_SLOW=1")
 
 
 def pytest_collection_modifyitems(config, items):
