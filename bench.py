@@ -53,6 +53,29 @@ from workloads import WORKLOADS, device_layout  # noqa: E402
 _ALGO_NAMES = {"rhosvd": "RP-HOSVD", "rsthosvd": "R-STHOSVD", "rpet": "R-PET"}
 
 
+def slowest_rank_ms(local_ms: float, dist=None, device="cpu") -> float:
+    """The timed region's length for the whole job: every rank contributes its own
+    elapsed time and all of them receive the maximum (one all-reduce)."""
+    if dist is None:
+        return float(local_ms)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(steps: int, world: int, elapsed_ms: float) -> float:
+    """Whole-job units per second: every rank's steps over the slowest rank's time
+    (replicas: each rank decomposes its own tensor, so the work grows with N)."""
+    return world * steps / (elapsed_ms / 1e3)
+
+
+def replica_workload(w, rank: int):
+    """The workload a rank decomposes: the same shapes with its own data seed."""
+    import dataclasses
+    return dataclasses.replace(w, seed=w.seed + rank)
+
+
 def _l2_note(w) -> str:
     mib = 4 * int(np.prod(w.dims)) / 2 ** 20
     if mib * 2 ** 20 > 129e6:
@@ -404,8 +427,7 @@ def main():
     R.lib()
 
     # each replica decomposes its own tensor (data seed + rank)
-    import dataclasses
-    wr = dataclasses.replace(w, seed=w.seed + rank)
+    wr = replica_workload(w, rank)
     x = wr.tensor()
     x_host = torch.from_numpy(device_layout(x))
     x32 = None
@@ -453,16 +475,12 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    elapsed_ms = ev0.elapsed_time(ev1)
+    elapsed_ms = slowest_rank_ms(ev0.elapsed_time(ev1), dist, "cuda")
     clocks = clk.summary()
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
     code, _ = R.rhosvd_device_status(ws)
     if code != 0:
         raise RuntimeError(f"device status {code} in timed region")
-    value = world * args.steps / (elapsed_ms / 1e3)
+    value = job_rate(args.steps, world, elapsed_ms)
 
     # ---------------------------------------------------------------- e2e through host buffers
     # Every step copies its tensor from pinned host memory and reads its factors and
@@ -516,12 +534,8 @@ def main():
     ev1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    e2e_ms = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * e2e_steps / (e2e_ms / 1e3)
+    e2e_ms = slowest_rank_ms(ev0.elapsed_time(ev1), dist, "cuda")
+    e2e_value = job_rate(e2e_steps, world, e2e_ms)
     h2d = X.numel() * 4
     d2h = (G.numel() + sum(u.numel() for u in Us)) * 4
 
