@@ -8,7 +8,8 @@
   split with FP32 accumulation, and the truncation's eigenvectors from an
   FP32-rounded square root of B B^T.  E stays within 0.05% of exact (measured
   +0.015%), so a larger excess on the device is not arithmetic.
-About two minutes of CPU: opt-in with RHOSVD_SLOW=1."""
+* R-PET single pass on a BF16 or per-slice e4m3 copy of X: E grows 2x and 25x.
+About five minutes of CPU: opt-in with RHOSVD_SLOW=1."""
 import numpy as np
 import pytest
 
@@ -125,3 +126,57 @@ def test_emulated_device_arithmetic_keeps_the_error():
         s = T.fold(sn, n, dims)
         us.append(u)
     assert M.rel_error(x, s, us) <= 1.0005 * e_exact
+
+
+def e4m3_round(a):
+    """Round to FP8 e4m3 (bias 7, 3 mantissa bits, largest 448, subnormal spacing
+    2^-9), ties to even, saturating at 448."""
+    a = np.asarray(a, dtype=np.float64)
+    m = np.minimum(np.abs(a), 448.0)
+    e = np.maximum(np.floor(np.log2(np.maximum(m, 2.0 ** -9))), -6.0)
+    step = 2.0 ** (e - 3)
+    return np.sign(a) * np.minimum(np.round(m / step) * step, 448.0)
+
+
+def test_e4m3_round_is_correct():
+    v = np.array([1.0, 1.0625, 1.1875, 3.3, 448.0, 500.0, 2.0 ** -9, 3 * 2.0 ** -10, -0.3])
+    r = e4m3_round(v)
+    assert r[0] == 1.0
+    assert r[1] == 1.0                 # halfway between 1 and 1.125: tie to even
+    assert r[2] == 1.25                # halfway between 1.125 and 1.25: tie to even
+    assert r[3] == 3.25                # spacing 0.25 in [2, 4)
+    assert r[4] == 448.0 and r[5] == 448.0
+    assert r[6] == 2.0 ** -9           # smallest subnormal
+    assert r[7] == 2.0 ** -8           # 1.5 subnormal spacings: tie to even (2)
+    assert r[8] == -0.3125             # spacing 2^-5 in [0.25, 0.5)
+
+
+def _per_slice(x, fn):
+    out = np.empty_like(x)
+    for k in range(x.shape[-1]):
+        sl = x[..., k]
+        sc = 448.0 / np.abs(sl).max()
+        out[..., k] = fn(sl * sc) / sc
+    return out
+
+
+@pytest.mark.slow
+def test_reduced_precision_single_pass_loses_accuracy():
+    """R-PET on the 128^4 workload (noise 1e-3) with the single pass reading a BF16
+    or a per-slice-scaled e4m3 copy of X: the quantisation noise (1.7e-3 and
+    2.7e-2 relative) exceeds the data's, and E grows 2x and 25x; an exact FP32
+    core pass over the found factors does not bring it back."""
+    w = WORKLOADS["lowrank128x4_rpet"]
+    x = np.asfortranarray(w.tensor().astype(np.float32).astype(np.float64))
+    n_modes = x.ndim
+    om = [gaussian_matrix(w.omega_seed + n, int(np.prod(w.dims)) // w.dims[n], w.K[n]).astype(np.float64)
+          for n in range(n_modes)]
+    ot = [gaussian_matrix(w.omega_seed + 100 + n, w.S[n], w.dims[n]).astype(np.float64) for n in range(n_modes)]
+    e = {}
+    for label, xq in [("fp32", x), ("bf16", bf16_round(x).reshape(x.shape, order="A")),
+                      ("e4m3", _per_slice(x, e4m3_round))]:
+        g, us, _ = A.rpet(np.asfortranarray(xq), w.ranks, om, ot)
+        e[label] = M.rel_error(x, g, us)
+        e[label + "+core"] = M.rel_error(x, T.multi_ttm(x, us, transpose=True), us)
+    assert e["bf16"] > 1.5 * e["fp32"] and e["bf16+core"] > 1.5 * e["fp32+core"]
+    assert e["e4m3"] > 10 * e["fp32"] and e["e4m3+core"] > 10 * e["fp32+core"]
