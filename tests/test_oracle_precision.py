@@ -1,4 +1,4 @@
-"""What reduced precision costs R-STHOSVD on the 512^3 workload (FP64 oracle, CPU).
+"""What reduced precision costs the randomized decompositions (FP64 oracle, CPU).
 
 * BF16 power iterates: the products of the power steps computed on a
   BF16-rounded copy of the unfolding (round to nearest even), first sketch and
@@ -8,7 +8,8 @@
   split with FP32 accumulation, and the truncation's eigenvectors from an
   FP32-rounded square root of B B^T.  E stays within 0.05% of exact (measured
   +0.015%), so a larger excess on the device is not arithmetic.
-* R-PET single pass on a BF16 or per-slice e4m3 copy of X: E grows 2x and 25x.
+* R-PET on the 128^4 workload, the single pass reading a BF16 or a per-slice
+  e4m3 copy of X: E grows 2x and 25x, with or without an exact core pass.
 About five minutes of CPU: opt-in with RHOSVD_SLOW=1."""
 import numpy as np
 import pytest
