@@ -1,15 +1,14 @@
 """What reduced precision costs the randomized decompositions (FP64 oracle, CPU).
 
-* R-STHOSVD on the 512^3 workload with BF16 power iterates: the products of
-  the power steps computed on a
-  BF16-rounded copy of the unfolding (round to nearest even), first sketch and
-  projection exact.  On mode 1 E stays within 3% (measured +2.2%); on every mode
-  it does not; one exact power step after the BF16 ones restores E.
-* The same workload under the device's FP32 arithmetic: every large product
-  as a truncating 3xTF32
-  split with FP32 accumulation, and the truncation's eigenvectors from an
-  FP32-rounded square root of B B^T.  E stays within 0.05% of exact (measured
-  +0.015%), so a larger excess on the device is not arithmetic.
+* R-STHOSVD on the 512^3 workload with BF16 power iterates: the products of the
+  power steps computed on a BF16-rounded copy of the unfolding (round to nearest
+  even), first sketch and projection exact.  On mode 1 E stays within 3%
+  (measured +2.2%); on every mode it does not; one exact power step after the
+  BF16 ones restores E.
+* The same workload under the device's FP32 arithmetic: every large product as a
+  truncating 3xTF32 split with FP32 accumulation, and the truncation's
+  eigenvectors from an FP32-rounded square root of B B^T.  E stays within 0.05%
+  of exact (measured +0.015%), so a larger excess on the device is not arithmetic.
 * R-PET on the 128^4 workload, the single pass reading a BF16 or a per-slice
   e4m3 copy of X: E grows 2x and 25x, with or without an exact core pass.
 About five minutes of CPU: opt-in with RHOSVD_SLOW=1."""
