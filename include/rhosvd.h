@@ -194,10 +194,11 @@ rhosvd_status rhosvd_decompose(const float* X, const rhosvd_shape* shape, const 
                                const float* const* Omega_tilde, float* const* U, float* G,
                                void* ws, size_t ws_bytes, void* stream);
 
-/* Synchronise `stream`, read the device status word kept at the start of `ws`
- * and return the first error recorded there by earlier calls (RHOSVD_OK if
- * none); `flags` (nullable) receives the RHOSVD_FLAG_* bits.  The word is
- * cleared at the start of every rhosvd_decompose and primitive call. */
+/* Read the device status word kept at the start of `ws` with a copy ordered
+ * on `stream`, wait for that stream (and no other), and return the first error
+ * recorded there by earlier calls (RHOSVD_OK if none); `flags` (nullable)
+ * receives the RHOSVD_FLAG_* bits.  The word is cleared at the start of every
+ * rhosvd_decompose and primitive call. */
 rhosvd_status rhosvd_device_status(const void* ws, size_t ws_bytes, void* stream, int32_t* flags);
 
 /* Static description of a status code. */

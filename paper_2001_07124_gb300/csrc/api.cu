@@ -847,9 +847,12 @@ rhosvd_status rhosvd_decompose(const float* X, const rhosvd_shape* shape, const 
 rhosvd_status rhosvd_device_status(const void* ws, size_t ws_bytes, void* stream, int32_t* flags) {
   if (ws == nullptr || ws_bytes < sizeof(DevStatus)) return RHOSVD_EINVAL;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return RHOSVD_ECUDA;
+  // The copy is ordered on the caller's stream and only that stream is waited
+  // for: a plain cudaMemcpy would run on the legacy default stream, which waits
+  // for every blocking stream of the device (other requests in flight).
   DevStatus h;
-  if (cudaMemcpy(&h, ws, sizeof(DevStatus), cudaMemcpyDeviceToHost) != cudaSuccess) return RHOSVD_ECUDA;
+  if (cudaMemcpyAsync(&h, ws, sizeof(DevStatus), cudaMemcpyDeviceToHost, s) != cudaSuccess) return RHOSVD_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return RHOSVD_ECUDA;
   if (flags) *flags = h.flags;
   return static_cast<rhosvd_status>(h.code);
 }
