@@ -561,11 +561,14 @@ def test_workload_full_size_parity(name):
 
 @pytest.mark.slow
 def test_decay512_error_split_core_vs_factors():
-    """Diagnostic for the 512^3 workload, where E_gpu exceeds E_oracle by about 2%:
-    recomputes the optimal core for the device's factors in FP64 and measures the
-    factors' orthonormality, so that an excess in the device's own core and one in
-    its factors can be told apart.  Opt-in (RHOSVD_SLOW=1): it reports the split
-    and checks only that both parts are finite."""
+    """Diagnostic for the 512^3 workload, where E_gpu exceeds E_oracle by about 2%.
+    Two FP64 cores for the device's factors tell the causes apart:
+    X x_n pinv(U_n) depends only on the factors' subspaces, and X x_n U_n^T is
+    what the device's chain computes in exact arithmetic, so it also carries
+    the factors' departure from orthonormality.  E_lsq near E_oracle clears the
+    subspaces; E_transpose near E_gpu then blames the orthonormality, and
+    E_transpose near E_oracle blames the device's core.  Opt-in (RHOSVD_SLOW=1):
+    it reports the split and checks only that every part is finite."""
     w = WORKLOADS["decay512_rsthosvd"]
     x = w.tensor()
     x32 = f32(x)
@@ -576,8 +579,9 @@ def test_decay512_error_split_core_vs_factors():
     # least-squares core for the device's factors: X x_n pinv(U_n)
     g_ls = T.multi_ttm(x32, [np.linalg.pinv(v) for v in u])
     e_ls = M.rel_error(x32, g_ls, u)
-    orth = max(M.orthonormality(v) for v in u)
-    sine = max(M.max_principal_sine(a, b) for a, b in zip(u, u_or))
-    print(f"\nE_gpu {e_gpu:.6e}  E_oracle {e_or:.6e}  E with FP64 core for the device factors {e_ls:.6e}  "
-          f"factor orthonormality {orth:.2e}  max sine {sine:.2e}")
-    assert np.isfinite(e_gpu) and np.isfinite(e_ls)
+    e_tr = M.rel_error(x32, T.multi_ttm(x32, u, transpose=True), u)
+    orth = [M.orthonormality(v) for v in u]
+    sine = [M.max_principal_sine(a, b) for a, b in zip(u, u_or)]
+    print(f"\nE_gpu {e_gpu:.6e}  E_oracle {e_or:.6e}  E_lsq {e_ls:.6e}  E_transpose {e_tr:.6e}\n"
+          f"orthonormality per mode {['%.2e' % o for o in orth]}  sine per mode {['%.2e' % v for v in sine]}")
+    assert np.isfinite(e_gpu) and np.isfinite(e_ls) and np.isfinite(e_tr)

@@ -7,8 +7,11 @@
   BF16 ones restores E.
 * The same workload under the device's FP32 arithmetic: every large product as a
   truncating 3xTF32 split with FP32 accumulation, and the truncation's
-  eigenvectors from an FP32-rounded square root of B B^T.  E stays within 0.05%
-  of exact (measured +0.015%), so a larger excess on the device is not arithmetic.
+  eigenvectors by the device's route (Cholesky factor of B B^T, then FP32
+  one-sided Jacobi that stops once no column cosine exceeds 2e-6).  E stays
+  within 0.3% of exact (measured +0.17%; with exact eigenvectors +0.015%, so
+  the stopping threshold costs most of it).  A larger excess on the device is
+  not arithmetic.
 * R-PET on the 128^4 workload, the single pass reading a BF16 or a per-slice
   e4m3 copy of X: E grows 2x and 25x, with or without an exact core pass.
 About five minutes of CPU: opt-in with RHOSVD_SLOW=1."""
@@ -101,15 +104,64 @@ def test_truncating_tf32_split_is_exact_in_its_parts():
     assert np.all(np.abs(lo) < np.abs(x) * 2.0 ** -10)  # and below the TF32 spacing
 
 
+def _jacobi_columns_f32(l, jtol=2e-6, max_sweeps=30):
+    """One-sided Jacobi (Hestenes 1958) on the columns of l in FP32: round-robin
+    (circle) pairs, the rotation that zeroes a pair's inner product, and a stop
+    once no pair's cosine exceeds jtol in a whole sweep. Returns the columns
+    normalised and ordered by decreasing norm, and the number of sweeps."""
+    f = np.float32
+    x = np.array(l, dtype=f)
+    k = x.shape[1]
+    n = k + (k & 1)
+    w = np.arange(n // 2)
+    for sweep in range(max_sweeps):
+        norms = np.einsum("ij,ij->j", x, x)
+        rotated = False
+        for s in range(n - 1):
+            a = np.where(w == 0, 0, (w - 1 + s) % (n - 1) + 1)
+            b = (n - 2 - w + s) % (n - 1) + 1
+            p, q = np.minimum(a, b), np.maximum(a, b)
+            p, q = p[q < k], q[q < k]
+            gamma = np.einsum("ij,ij->j", x[:, p], x[:, q])
+            alpha, beta = norms[p], norms[q]
+            hit = (gamma != 0) & (np.abs(gamma) > f(jtol) * np.sqrt(alpha) * np.sqrt(beta))
+            if not hit.any():
+                continue
+            p, q, gamma, alpha, beta = p[hit], q[hit], gamma[hit], alpha[hit], beta[hit]
+            zeta = (beta - alpha) / (f(2) * gamma)
+            t = np.copysign(f(1) / (np.abs(zeta) + np.sqrt(zeta * zeta + f(1))), zeta).astype(f)
+            c = (f(1) / np.sqrt(t * t + f(1))).astype(f)
+            sn = c * t
+            xp, xq = x[:, p].copy(), x[:, q].copy()
+            x[:, p], x[:, q] = c * xp - sn * xq, sn * xp + c * xq
+            norms[p], norms[q] = np.maximum(alpha - t * gamma, f(0)), beta + t * gamma
+            rotated = True
+        if not rotated:
+            break
+    nc = np.sqrt(np.einsum("ij,ij->j", x, x))
+    order = np.argsort(-nc, kind="stable")
+    return (x[:, order] / nc[order]).astype(np.float64), sweep + 1
+
+
+def test_jacobi_columns_gives_the_left_singular_vectors():
+    rng = np.random.default_rng(3)
+    u0, _ = np.linalg.qr(rng.standard_normal((20, 20)))
+    sig = 0.7 ** np.arange(20)
+    l = np.linalg.cholesky((u0 * sig ** 2) @ u0.T)     # L L^T = U S^2 U^T: left vectors of L are U
+    u, sweeps = _jacobi_columns_f32(l)
+    assert sweeps < 30
+    assert np.abs(np.abs(np.sum(u[:, :10] * u0[:, :10], axis=0)) - 1).max() < 1e-5
+    assert np.abs(u.T @ u - np.eye(20)).max() < 5e-6
+
+
 def _brsvd_device(a, r, q, omega):
     qm = A.orth(_mm3(a, omega))
     for _ in range(q):
         qm = A.orth(_mm3(a, A.orth(_mm3(a.T, qm))))
+    qm = qm.astype(np.float32).astype(np.float64)
     b = _mm3(qm.T, a)
-    lam, v = np.linalg.eigh(b @ b.T)
-    root = (v * np.sqrt(np.maximum(lam, 0))).astype(np.float32).astype(np.float64)
-    ubar = np.linalg.svd(root, full_matrices=False)[0].astype(np.float32).astype(np.float64)
-    return qm @ ubar[:, :r], _mm3(ubar[:, :r].T, b)
+    ubar = _jacobi_columns_f32(np.linalg.cholesky(b @ b.T))[0][:, :r]
+    return _mm3(qm, ubar), _mm3(ubar.T, b)
 
 
 @pytest.mark.slow
@@ -127,7 +179,9 @@ def test_emulated_device_arithmetic_keeps_the_error():
         dims[n] = w.ranks[n]
         s = T.fold(sn, n, dims)
         us.append(u)
-    assert M.rel_error(x, s, us) <= 1.0005 * e_exact
+    e_dev = M.rel_error(x, s, us)
+    print(f"E exact {e_exact:.6e}, emulated device {e_dev:.6e} ({e_dev / e_exact - 1:+.3%})")
+    assert e_dev <= 1.003 * e_exact
 
 
 def e4m3_round(a):
