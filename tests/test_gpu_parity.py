@@ -572,7 +572,11 @@ def test_decay512_error_split_core_vs_factors():
     w = WORKLOADS["decay512_rsthosvd"]
     x = w.tensor()
     x32 = f32(x)
-    g, u = _run(x, w.dims, w.ranks, w.algo, w.p, w.q, seed=w.omega_seed)
+    ws = R().Workspace(R().rhosvd_workspace_size(w.dims, w.ranks, w.algo, w.p, w.q))
+    G, U = R().rhosvd_decompose(dev(x), w.dims, w.ranks, algo=w.algo, p=w.p, q=w.q, seed=w.omega_seed, ws=ws)
+    g, u = host(G), [host(v) for v in U]
+    # the status block: code, flags, orth_fail, fallbacks, fallback_rows, eig_sweeps
+    status = ws.buf[:24].cpu().view(torch.int32).tolist()
     g_or, u_or = _oracle_seeded(w.algo, x32, w.dims, w.ranks, w.p, w.q, w.omega_seed)
     e_gpu = M.rel_error(x32, g, u)
     e_or = M.rel_error(x32, g_or, u_or)
@@ -583,5 +587,46 @@ def test_decay512_error_split_core_vs_factors():
     orth = [M.orthonormality(v) for v in u]
     sine = [M.max_principal_sine(a, b) for a, b in zip(u, u_or)]
     print(f"\nE_gpu {e_gpu:.6e}  E_oracle {e_or:.6e}  E_lsq {e_ls:.6e}  E_transpose {e_tr:.6e}\n"
-          f"orthonormality per mode {['%.2e' % o for o in orth]}  sine per mode {['%.2e' % v for v in sine]}")
+          f"orthonormality per mode {['%.2e' % o for o in orth]}  sine per mode {['%.2e' % v for v in sine]}\n"
+          f"status (code, flags, orth_fail, fallbacks, fallback_rows, eig_sweeps) {status}")
     assert np.isfinite(e_gpu) and np.isfinite(e_ls) and np.isfinite(e_tr)
+
+
+@pytest.mark.slow
+def test_decay512_mode1_stages():
+    """Diagnostic for the same workload, mode 1 step by step through the
+    primitives (seeded sketch, orthonormalisation, one power step,
+    orthonormalisation, projection B = Q^T X_(1)). The oracle takes each step from
+    the device's own previous output, so every printed figure isolates one step:
+    the norm-wise relative error of a product, and the orthonormality and
+    principal sine of a basis. Opt-in (RHOSVD_SLOW=1); it checks only that the
+    steps stay within the parity tolerances of a single product."""
+    w = WORKLOADS["decay512_rsthosvd"]
+    x32 = f32(w.tensor())
+    X = dev(x32)
+    K = w.ranks[0] + w.p
+    a = T.unfold(x32, 0)
+    om = philox.omega(w.omega_seed, 0, a.shape[1], K).astype(np.float64)
+
+    def rel(got, want):
+        return float(np.linalg.norm(got - want) / np.linalg.norm(want))
+
+    y = R().rhosvd_sketch(X, w.dims, 0, K, seed=w.omega_seed)
+    yh = host(y)
+    e_y = rel(yh, a @ om)
+    q0, fb0 = R().rhosvd_orth(y, report_fallback=True)
+    q0h = host(q0)
+    y1 = R().rhosvd_power(X, w.dims, 0, q0)
+    y1h = host(y1)
+    z_or = A.orth(a.T @ q0h)
+    sine_y1 = M.max_principal_sine(y1h, a @ z_or)
+    q1, fb1 = R().rhosvd_orth(y1, report_fallback=True)
+    q1h = host(q1)
+    b = host(R().rhosvd_core(X, w.dims, [q1, None, None])).reshape(K, -1, order="F")
+    b_or = q1h.T @ a
+    e_b = rel(b, b_or)
+    bias_b = float(np.sum(b * b_or) / np.sum(b_or * b_or) - 1)
+    print(f"\nsketch rel {e_y:.2e} | orth(Y): orth {M.orthonormality(q0h):.2e} sine {M.max_principal_sine(q0h, yh):.2e}"
+          f" fallback {fb0} | power: sine vs X orth(X^T Q0) {sine_y1:.2e} | orth(Y1): orth {M.orthonormality(q1h):.2e}"
+          f" sine {M.max_principal_sine(q1h, y1h):.2e} fallback {fb1} | B = Q^T X_(1): rel {e_b:.2e} scale {bias_b:+.2e}")
+    assert e_y <= 1e-5 and e_b <= 1e-5
