@@ -174,6 +174,27 @@ def _traffic_for(kernel_src: str, key: str):
     return ent.get("bytes_per_launch")
 
 
+def accuracy_report(x32, g_gpu, u_gpu, g_or, u_or, tol=1e-5, max_sine=1e-4) -> dict:
+    """The error gate of a bench line: E_gpu against E_oracle (explicit FP64
+    residuals on the same FP32 input) and the largest principal-angle sine between
+    the two sets of factors. Beside it, what separates the causes of an excess:
+    per mode the factors' orthonormality and sine, and E for two FP64 cores of the
+    device's factors, X x_n pinv(U_n) (subspaces only) and X x_n U_n^T (what the
+    device's projection computes in exact arithmetic)."""
+    from oracle import metrics as M
+    from oracle import tensor as T
+    e_gpu = M.rel_error(x32, g_gpu, u_gpu)
+    e_or = M.rel_error(x32, g_or, u_or)
+    sines = [M.max_principal_sine(a, b) for a, b in zip(u_gpu, u_or)]
+    sine = max(sines)
+    return {"E_gpu": e_gpu, "E_oracle": e_or, "max_principal_sine": sine,
+            "pass": bool(abs(e_gpu - e_or) <= tol and sine <= max_sine),
+            "sine_per_mode": sines,
+            "orthonormality_per_mode": [M.orthonormality(u) for u in u_gpu],
+            "E_lsq_core": M.rel_error(x32, T.multi_ttm(x32, [np.linalg.pinv(u) for u in u_gpu]), u_gpu),
+            "E_transpose_core": M.rel_error(x32, T.multi_ttm(x32, u_gpu, transpose=True), u_gpu)}
+
+
 def oracle_decompose(w, x32):
     """Time one oracle decomposition (FP64 NumPy) with the generator's own test matrices."""
     from oracle import algorithms as A
@@ -458,7 +479,8 @@ def main():
     code, flags = R.rhosvd_device_status(ws)
     if code != 0:
         raise RuntimeError(f"device status {code} after warm-up")
-    st_words = ws.buf[:16].view(torch.int32).cpu().tolist()   # code, flags, orth_fail, fallbacks
+    # code, flags, orth_fail, fallbacks, fallback_rows, eig_sweeps
+    st_words = ws.buf[:24].view(torch.int32).cpu().tolist()
 
     def barrier():
         if dist is not None:
@@ -573,15 +595,10 @@ def main():
     cpu = None
     accuracy = None
     if rank == 0 and x32 is not None:
-        from oracle import metrics as M
         t_or, g_or, u_or = oracle_decompose(w, x32)
         g_gpu = R.fortran_view(G, ranks).cpu().numpy().astype(np.float64)
         u_gpu = [R.matrix(u, dims[n], ranks[n]).cpu().numpy().astype(np.float64) for n, u in enumerate(Us)]
-        e_gpu = M.rel_error(x32, g_gpu, u_gpu)
-        e_or = M.rel_error(x32, g_or, u_or)
-        sine = max(M.max_principal_sine(a, b) for a, b in zip(u_gpu, u_or))
-        accuracy = {"E_gpu": e_gpu, "E_oracle": e_or, "max_principal_sine": sine,
-                    "pass": bool(abs(e_gpu - e_or) <= 1e-5 and sine <= 1e-4)}
+        accuracy = accuracy_report(x32, g_gpu, u_gpu, g_or, u_or)
         cpu = {"value": 1.0 / t_or, "unit": UNIT, "cores": _CORES, "kind": "oracle",
                "sample": f"one full decomposition of the {w.name} workload in FP64 NumPy (seeded Philox test matrices)"}
 
@@ -603,6 +620,7 @@ def main():
             "cpu_baseline": cpu,
             "accuracy": accuracy,
             "householder_fallbacks_per_step": st_words[3],
+            "max_jacobi_sweeps": st_words[5],
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -42,3 +42,33 @@ def test_reference_arm_is_silent_on_other_ranks():
     r = _bench({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, "--gpus", "2")
     assert r.returncode == 0, r.stderr[-2000:]
     assert not [l for l in r.stdout.splitlines() if l.strip().startswith("{")], r.stdout
+
+
+def test_accuracy_report_separates_subspace_and_orthonormality():
+    """The error gate on a small decomposition: the oracle's own result passes with
+    zero sines, and factors scaled off orthonormality (same subspaces) keep
+    E_lsq_core at the oracle's E while E_transpose_core grows."""
+    import numpy as np
+    if ROOT not in sys.path:
+        sys.path.insert(0, ROOT)
+    import bench
+    from oracle import algorithms as A
+    from oracle import tensor as T
+    from workloads import gaussian_matrix, lowrank_tensor
+    dims, ranks = (14, 12, 10), (3, 4, 2)
+    x = lowrank_tensor(dims, ranks, 5, noise=1e-3)
+    om = [gaussian_matrix(40 + n, r, c).astype(np.float64)
+          for n, (r, c) in enumerate(A.omega_shapes("rsthosvd", dims, ranks, 4))]
+    g, us = A.rsthosvd(x, ranks, 1, om)
+    rep = bench.accuracy_report(x, g, us, g, us)
+    assert rep["pass"] and rep["E_gpu"] == rep["E_oracle"]
+    assert max(rep["sine_per_mode"]) < 1e-7 and max(rep["orthonormality_per_mode"]) < 1e-12
+    assert abs(rep["E_lsq_core"] - rep["E_oracle"]) < 1e-9 and abs(rep["E_transpose_core"] - rep["E_oracle"]) < 1e-9
+    bent = [u * (1 + 1e-3 * np.arange(u.shape[1])) for u in us]       # same columns' directions, wrong lengths
+    rep = bench.accuracy_report(x, T.multi_ttm(x, bent, transpose=True), bent, g, us)
+    assert max(rep["sine_per_mode"]) < 1e-7
+    # column k of mode n has length 1 + 1e-3 k: the largest departure is mode 2's last column
+    assert abs(max(rep["orthonormality_per_mode"]) - (1.003 ** 2 - 1)) < 1e-9
+    assert abs(rep["E_lsq_core"] - rep["E_oracle"]) < 1e-10
+    assert rep["E_transpose_core"] > 1.5 * rep["E_oracle"]
+    assert rep["E_gpu"] == rep["E_transpose_core"] and not rep["pass"]
