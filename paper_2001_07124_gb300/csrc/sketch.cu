@@ -7,6 +7,7 @@
 // X[l + i*s_i + r*s_r].  The sketch splits the long contraction j over CTAs
 // and reduces the per-CTA partials in a fixed order (deterministic results).
 #include <algorithm>
+#include <mutex>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -261,14 +262,18 @@ void launch_partials(const SketchPlan& pl, const View& x, const WView& w, int K,
 }  // namespace
 
 cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes) {
-  // one flag per (device, kernel) pair; a handful of kernels use this
+  // One flag per (device, kernel) pair; a handful of kernels use this.  The
+  // table is shared by every host thread, so it is read and written under a
+  // lock (a slot taken by one thread must not be reused for another kernel).
   constexpr int kMaxDev = 64, kMaxKern = 64;
+  static std::mutex mu;
   static const void* kernels[kMaxKern] = {nullptr};
   static bool done[kMaxKern][kMaxDev] = {{false}};
   static int nk = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
   int slot = -1;
   for (int i = 0; i < nk; ++i)
     if (kernels[i] == kernel) slot = i;
