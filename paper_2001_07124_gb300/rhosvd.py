@@ -238,10 +238,12 @@ def rhosvd_primitive_workspace_size(dims, Kmax) -> int:
 def rhosvd_omega(seed: int, stream_id: int, rows: int, cols: int, out=None, stream=None):
     """rows x cols Gaussian test matrix; returns the (rows, cols) column-major view."""
     import torch
-    if out is None:
+    own = out is None
+    if own:
         out = torch.empty(int(rows) * int(cols), dtype=torch.float32, device="cuda")
     _check(lib().rhosvd_omega(int(seed), int(stream_id), int(rows), int(cols), _dptr(out), int(rows),
                               _stream(stream)), "rhosvd_omega")
+    _hold(stream, out if own else None)
     return matrix(out, rows, cols)
 
 
@@ -251,15 +253,37 @@ def _ws_for(ws, nbytes):
     return ws.ensure(nbytes)
 
 
+def _hold(stream, *tensors, current=None):
+    """Keep buffers this binding allocated alive for work on another stream.
+
+    The buffers come from torch's caching allocator on the current stream. When
+    the library's work goes to a different ``stream``, freeing them at return
+    would let a later allocation on the current stream reuse the memory while
+    the kernels still use it; ``record_stream`` defers the reuse until the work
+    enqueued on ``stream`` so far has finished. ``None`` entries are skipped."""
+    if stream is None:
+        return
+    if current is None:
+        import torch
+        current = torch.cuda.current_stream()
+    if stream == current:
+        return
+    for t in tensors:
+        if t is not None:
+            t.record_stream(stream)
+
+
 def rhosvd_sketch(X, dims, mode: int, K: int, seed: int = 0, Omega=None, Y=None, ws=None, stream=None):
     """Y = X_(mode) Omega (I_mode x K)."""
     X = colmajor(X, dims)
     I = int(dims[mode])
+    own_y, own_ws = Y is None, ws is None
     Y = empty_colmajor((I, K)) if Y is None else Y
     ws = _ws_for(ws, rhosvd_primitive_workspace_size(dims, K))
     om = None if Omega is None else _dptr(Omega)
     _check(lib().rhosvd_sketch(_dptr(X), ctypes.byref(make_shape(dims)), int(mode), int(K), int(seed), om,
                                _dptr(Y), ws.ptr, ws.nbytes, _stream(stream)), "rhosvd_sketch")
+    _hold(stream, Y if own_y else None, ws.buf if own_ws else None)
     return matrix(Y, I, K)
 
 
@@ -270,9 +294,11 @@ def rhosvd_sketch_noalloc(X, dims, mode: int, K: int, Omega, Y=None, stream=None
     Calls that overlap on the GPU share that array and race; order them."""
     X = colmajor(X, dims)
     I = int(dims[mode])
+    own_y = Y is None
     Y = empty_colmajor((I, K)) if Y is None else Y
     _check(lib().rhosvd_sketch_noalloc(_dptr(X), ctypes.byref(make_shape(dims)), int(mode), int(K), _dptr(Omega),
                                        _dptr(Y), _stream(stream)), "rhosvd_sketch_noalloc")
+    _hold(stream, Y if own_y else None)
     return matrix(Y, I, K)
 
 
@@ -293,11 +319,13 @@ def rhosvd_sketch_all(X, dims, K, S=None, seed: int = 0, Omega=None, Omega_tilde
             mt = max(mt, int(np.prod(t)))
             om += S[n] * dims[n] * 4 + 256
         need += 2 * (mt * 4 + 256) + om
+    own_ws = ws is None
     ws = _ws_for(ws, need)
     _check(lib().rhosvd_sketch_all(_dptr(X), ctypes.byref(make_shape(dims)), _i32(K),
                                    _i32(S) if S is not None else None, int(seed), _ptrs(Omega),
                                    _ptrs(Omega_tilde), _ptrs(Ys), None if H is None else _dptr(H), ws.ptr,
                                    ws.nbytes, _stream(stream)), "rhosvd_sketch_all")
+    _hold(stream, H, ws.buf if own_ws else None, *Ys)
     Ys = [matrix(Ys[n], dims[n], K[n]) for n in range(N)]
     return Ys, (None if H is None else fortran_view(H, S))
 
@@ -307,9 +335,11 @@ def rhosvd_power(X, dims, mode: int, Q, ws=None, stream=None):
     X = colmajor(X, dims)
     I, K = int(Q.shape[0]), int(Q.shape[1])
     buf = Q.t().contiguous().reshape(-1).clone()
+    own_ws = ws is None
     ws = _ws_for(ws, rhosvd_primitive_workspace_size(dims, K))
     _check(lib().rhosvd_power(_dptr(X), ctypes.byref(make_shape(dims)), int(mode), K, _dptr(buf), ws.ptr,
                               ws.nbytes, _stream(stream)), "rhosvd_power")
+    _hold(stream, buf, ws.buf if own_ws else None)
     return matrix(buf, I, K)
 
 
@@ -317,10 +347,12 @@ def rhosvd_orth(Y, ws=None, stream=None, report_fallback=False):
     """Orthonormalise the columns of Y (m x K, given as an (m, K) tensor); returns (Q, fallback)."""
     m, K = int(Y.shape[0]), int(Y.shape[1])
     buf = Y.t().contiguous().reshape(-1).clone()
+    own_ws = ws is None
     ws = _ws_for(ws, rhosvd_primitive_workspace_size((m, K), K))
     fb = ctypes.c_int32(0)
     _check(lib().rhosvd_orth(_dptr(buf), m, K, m, ctypes.byref(fb) if report_fallback else None, ws.ptr,
                              ws.nbytes, _stream(stream)), "rhosvd_orth")
+    _hold(stream, buf, ws.buf if own_ws else None)
     return matrix(buf, m, K), (bool(fb.value) if report_fallback else None)
 
 
@@ -336,9 +368,11 @@ def rhosvd_core(X, dims, Qs, ws=None, stream=None):
     for n in range(N):
         t[n] = K[n]
         mt = max(mt, int(np.prod(t)))
+    own_ws = ws is None
     ws = _ws_for(ws, 256 + 2 * (mt * 4 + 256))
     _check(lib().rhosvd_core(_dptr(X), ctypes.byref(make_shape(dims)), _ptrs(qbufs), _i32(K), _dptr(G),
                              ws.ptr, ws.nbytes, _stream(stream)), "rhosvd_core")
+    _hold(stream, G, ws.buf if own_ws else None, *qbufs)
     return fortran_view(G, K)
 
 
@@ -362,10 +396,15 @@ def rhosvd_decompose(X, dims, ranks, algo="rsthosvd", p=10, q=1, seed=0, Omega=N
     need = int(lib().rhosvd_workspace_size(ctypes.byref(shape), r, ctypes.byref(opts)))
     if need == 0:
         _check(1, "rhosvd_workspace_size")
+    own_ws = ws is None
     ws = _ws_for(ws, need)
     code = lib().rhosvd_decompose(_dptr(X), ctypes.byref(shape), r, ctypes.byref(opts), _ptrs(Omega),
                                   _ptrs(Omega_tilde), _ptrs(Us), _dptr(G), ws.ptr, ws.nbytes, _stream(stream))
     _check(code, "rhosvd_decompose")
+    if out is None:
+        _hold(stream, G, *Us)
+    if own_ws:
+        _hold(stream, ws.buf)
     if check:
         dev, _ = rhosvd_device_status(ws, stream)
         _check(dev, "rhosvd_decompose (device)")

@@ -98,3 +98,29 @@ def test_primitive_argument_checks(lib):
     assert lib.rhosvd_omega(0, 0, 10, 4, ctypes.c_void_p(4096), 5, None) == 1                   # ld < rows
     assert lib.rhosvd_omega(0, 0, 0, 4, None, 0, None) == 0                                     # empty is a no-op
     assert lib.rhosvd_device_status(None, 0, None, None) == 1
+
+
+class _FakeStream:
+    def __init__(self, sid):
+        self.sid = sid
+
+    def __eq__(self, other):
+        return isinstance(other, _FakeStream) and other.sid == self.sid
+
+
+class _FakeTensor:
+    def __init__(self):
+        self.recorded = []
+
+    def record_stream(self, s):
+        self.recorded.append(s.sid)
+
+
+def test_binding_holds_its_buffers_only_for_another_stream():
+    cur, other = _FakeStream(0), _FakeStream(1)
+    a, b = _FakeTensor(), _FakeTensor()
+    R._hold(None, a, current=cur)                    # the current stream: nothing to do
+    R._hold(_FakeStream(0), a, current=cur)
+    assert a.recorded == []
+    R._hold(other, a, None, b, current=cur)          # another stream: every buffer, None skipped
+    assert a.recorded == [1] and b.recorded == [1]

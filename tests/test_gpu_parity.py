@@ -176,6 +176,23 @@ def test_seeded_sketch_generates_omega_in_kernel(dims, mode, K):
     np.testing.assert_array_equal(y_gen, y_mat)
 
 
+def test_side_stream_call_keeps_its_temporaries():
+    """A primitive called with another stream than the current one: the binding's
+    own workspace and output come from the current stream's pool, and the result
+    must not change when the current stream allocates and writes right after the
+    call (the freed workspace is held for the side stream)."""
+    dims, K = (64, 40, 30), 12
+    X = dev(random_tensor(dims, 31))
+    want = host(R().rhosvd_sketch(X, dims, 1, K, seed=5))
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    got = R().rhosvd_sketch(X, dims, 1, K, seed=5, stream=side)
+    junk = torch.full((1 << 22,), float("nan"), device="cuda")
+    side.synchronize()
+    np.testing.assert_array_equal(host(got), want)
+    del junk
+
+
 def test_tc_sketch_is_deterministic():
     dims, K = (512, 64, 64), 42
     X = dev(random_tensor(dims, 23))
