@@ -53,7 +53,7 @@ constexpr int A_STAGES = 2;              // one A slot per transform warpgroup
 constexpr int NUM_XFORM = 256;            // warps 0-7
 constexpr int NUM_EPI = 128;              // warps 8-11
 constexpr int PRODUCER_WARP = 12, MMA_WARP = 13;
-constexpr int NUM_THREADS = 448;
+constexpr int NUM_THREADS = NUM_XFORM + NUM_EPI + 64;   // + the producer and MMA warps
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int D_COLS = 64;                // per accumulator buffer
 constexpr int A_COL0 = 2 * D_COLS;        // A stages after the two accumulators
