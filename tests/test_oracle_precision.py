@@ -12,6 +12,9 @@
   within 0.3% of exact (measured +0.17%; with exact eigenvectors +0.015%, so
   the stopping threshold costs most of it).  A larger excess on the device is
   not arithmetic.
+* The same workload with both tall Grams of a mode in FP32 (a shifted FP32
+  CholeskyQR for the intermediate basis Z, an FP32 B B^T for the truncation):
+  E agrees with the exact run to 1e-6 relative.
 * R-PET on the 128^4 workload, the single pass reading a BF16 or a per-slice
   e4m3 copy of X: E grows 2x and 25x, with or without an exact core pass.
 About five minutes of CPU: opt-in with RHOSVD_SLOW=1."""
@@ -182,6 +185,54 @@ def test_emulated_device_arithmetic_keeps_the_error():
     e_dev = M.rel_error(x, s, us)
     print(f"E exact {e_exact:.6e}, emulated device {e_dev:.6e} ({e_dev / e_exact - 1:+.3%})")
     assert e_dev <= 1.003 * e_exact
+
+
+def _shifted_cholqr_range(z, c):
+    """One CholeskyQR pass from an FP32 Gram with a diagonal shift c u tr(G):
+    the shift keeps the Cholesky from breaking down at any condition number,
+    and the result keeps range(Z) (R is invertible), which is all an
+    intermediate basis of the power iteration needs."""
+    z32 = np.asarray(z, dtype=np.float32)
+    g = (z32.T @ z32).astype(np.float64)
+    r = np.linalg.cholesky(g + c * 2.0 ** -24 * np.trace(g) * np.eye(g.shape[0])).T.astype(np.float32)
+    return np.linalg.solve(r.T.astype(np.float64), z32.T.astype(np.float64)).T.astype(np.float32).astype(np.float64)
+
+
+@pytest.mark.slow
+def test_fp32_grams_keep_the_error():
+    """The 512^3 workload with the two tall Grams of a mode in FP32 instead of
+    FP64-accurate: the intermediate basis Z by a shifted FP32 CholeskyQR, and the
+    truncation's B B^T accumulated in FP32. E agrees with the exact run to
+    1e-6 relative, so both Grams could run at FP32 speed on this workload.
+    (The truncation Gram still needs FP64 accuracy when lambda_R / lambda_1
+    approaches the FP32 unit roundoff.)"""
+    w = WORKLOADS["decay512_rsthosvd"]
+    x = np.asfortranarray(w.tensor().astype(np.float32).astype(np.float64))
+    shapes = A.omega_shapes(w.algo, w.dims, w.ranks, w.p)
+    omegas = [gaussian_matrix(w.omega_seed + n, r, c).astype(np.float64) for n, (r, c) in enumerate(shapes)]
+    e = {}
+    for label in ("exact", "fp32"):
+        s, us = x, []
+        for n in range(3):
+            a = T.unfold(s, n)
+            qm = A.orth(a @ omegas[n])
+            for _ in range(w.q):
+                z = a.T @ qm
+                qm = A.orth(a @ (A.orth(z) if label == "exact" else _shifted_cholqr_range(z, 100.0)))
+            b = qm.T @ a
+            if label == "exact":
+                g = b @ b.T
+            else:
+                b32 = b.astype(np.float32)
+                g = (b32 @ b32.T).astype(np.float64)
+            ub = np.linalg.eigh(g)[1][:, ::-1][:, :w.ranks[n]]
+            dims = list(s.shape)
+            dims[n] = w.ranks[n]
+            s = T.fold(ub.T @ b, n, dims)
+            us.append(qm @ ub)
+        e[label] = M.rel_error(x, s, us)
+    print(f"E exact {e['exact']:.7e}, with FP32 Grams {e['fp32']:.7e}")
+    assert abs(e["fp32"] - e["exact"]) <= 1e-6 * e["exact"]
 
 
 def e4m3_round(a):
