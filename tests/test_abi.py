@@ -3,6 +3,7 @@ exports every entry point include/rhosvd.h declares, plans the same sketch
 widths as the oracle's independent rule, and rejects invalid requests before
 touching the device."""
 import ctypes
+import os
 
 import pytest
 
@@ -124,3 +125,28 @@ def test_binding_holds_its_buffers_only_for_another_stream():
     assert a.recorded == []
     R._hold(other, a, None, b, current=cur)          # another stream: every buffer, None skipped
     assert a.recorded == [1] and b.recorded == [1]
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/rhosvd.h is a C header: a C11 translation unit that includes it and
+    calls the decomposition entry points compiles without warnings."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use.c"
+    src.write_text(
+        '#include "rhosvd.h"\n'
+        "int use(const float* X, float* U[3], float* G, void* ws, void* stream) {\n"
+        "  rhosvd_shape shape = {3, {40, 50, 60}};\n"
+        "  int32_t ranks[3] = {5, 6, 7};\n"
+        "  rhosvd_opts opts = {.algo = RHOSVD_ALGO_RSTHOSVD, .p = 5, .q = 1, .seed = 7};\n"
+        "  size_t n = rhosvd_workspace_size(&shape, ranks, &opts);\n"
+        "  rhosvd_status s = rhosvd_decompose(X, &shape, ranks, &opts, 0, 0, U, G, ws, n, stream);\n"
+        "  return s == RHOSVD_OK ? (int)rhosvd_device_status(ws, n, stream, 0) : (int)s;\n"
+        "}\n")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    r = subprocess.run([gcc, "-std=c11", "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I", inc, str(src)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
