@@ -193,7 +193,12 @@ def matrix(buf, rows: int, cols: int):
 
 
 class Workspace:
-    """Caller-owned device workspace (the library itself never allocates)."""
+    """Caller-owned device workspace (the library itself never allocates).
+
+    ``ensure`` replaces the buffer when a call needs more bytes than it holds.
+    The old buffer goes back to torch's allocator for the current stream, so a
+    workspace must not grow while work that uses it is still in flight on
+    another stream (size it with the workspace query first)."""
 
     def __init__(self, nbytes: int, device=None):
         import torch
