@@ -167,6 +167,22 @@ def test_exact_recovery_four_way():
         assert M.rel_error(x, g, us) <= 1e-12
 
 
+def test_exact_recovery_eight_way():
+    """The largest order the library accepts (8 modes), including modes kept
+    whole (R_n = I_n) and a rank-1 mode: all three algorithms recover a
+    noise-free tensor of exact multilinear rank."""
+    dims, ranks = (4, 3, 5, 2, 3, 4, 2, 3), (2, 3, 2, 1, 2, 2, 2, 2)
+    x = lowrank_tensor(dims, ranks, 19, noise=0.0, factors="gaussian")
+    for algo in ("rhosvd", "rsthosvd"):
+        g, us = getattr(A, algo)(x, ranks, 1, _omegas(algo, dims, ranks, 1))
+        assert M.rel_error(x, g, us) <= 1e-12
+    rng = np.random.default_rng(19)
+    om = [rng.standard_normal((int(np.prod(dims)) // d, min(r + 1, d))) for d, r in zip(dims, ranks)]
+    ot = [rng.standard_normal((min(r + 1, d) + 1, d)) for d, r in zip(dims, ranks)]
+    g, us, _ = A.rpet(x, ranks, om, ot)
+    assert M.rel_error(x, g, us) <= 1e-10
+
+
 def test_full_width_sketch_equals_deterministic():
     """K_n >= I_n: range(X_(n) Omega) = range(X_(n)) a.s., so RP-HOSVD = truncated HOSVD
     and R-STHOSVD = STHOSVD (same subspaces, same error)."""
