@@ -178,21 +178,26 @@ def accuracy_report(x32, g_gpu, u_gpu, g_or, u_or, tol=1e-5, max_sine=1e-4) -> d
     """The error gate of a bench line: E_gpu against E_oracle (explicit FP64
     residuals on the same FP32 input) and the largest principal-angle sine between
     the two sets of factors. Beside it, what separates the causes of an excess:
-    per mode the factors' orthonormality and sine, and E for two FP64 cores of the
-    device's factors, X x_n pinv(U_n) (subspaces only) and X x_n U_n^T (what the
-    device's projection computes in exact arithmetic)."""
+    per mode the factors' orthonormality, mean column length and sine; the scale
+    of the device's core against X x_n U_n^T (a systematic shortening of the
+    products shows there); and E for two FP64 cores of the device's factors,
+    X x_n pinv(U_n) (subspaces only) and X x_n U_n^T (what the device's
+    projection computes in exact arithmetic)."""
     from oracle import metrics as M
     from oracle import tensor as T
     e_gpu = M.rel_error(x32, g_gpu, u_gpu)
     e_or = M.rel_error(x32, g_or, u_or)
     sines = [M.max_principal_sine(a, b) for a, b in zip(u_gpu, u_or)]
     sine = max(sines)
+    g_t = T.multi_ttm(x32, u_gpu, transpose=True)
     return {"E_gpu": e_gpu, "E_oracle": e_or, "max_principal_sine": sine,
             "pass": bool(abs(e_gpu - e_or) <= tol and sine <= max_sine),
             "sine_per_mode": sines,
             "orthonormality_per_mode": [M.orthonormality(u) for u in u_gpu],
+            "column_norm_minus_1_per_mode": [float(np.mean(np.linalg.norm(u, axis=0)) - 1) for u in u_gpu],
+            "core_scale_minus_1": float(np.sum(g_gpu * g_t) / np.sum(g_t * g_t) - 1),
             "E_lsq_core": M.rel_error(x32, T.multi_ttm(x32, [np.linalg.pinv(u) for u in u_gpu]), u_gpu),
-            "E_transpose_core": M.rel_error(x32, T.multi_ttm(x32, u_gpu, transpose=True), u_gpu)}
+            "E_transpose_core": M.rel_error(x32, g_t, u_gpu)}
 
 
 def oracle_decompose(w, x32):

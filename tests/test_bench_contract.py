@@ -64,6 +64,9 @@ def test_accuracy_report_separates_subspace_and_orthonormality():
     assert rep["pass"] and rep["E_gpu"] == rep["E_oracle"]
     assert max(rep["sine_per_mode"]) < 1e-7 and max(rep["orthonormality_per_mode"]) < 1e-12
     assert abs(rep["E_lsq_core"] - rep["E_oracle"]) < 1e-9 and abs(rep["E_transpose_core"] - rep["E_oracle"]) < 1e-9
+    assert abs(rep["core_scale_minus_1"]) < 1e-12 and max(map(abs, rep["column_norm_minus_1_per_mode"])) < 1e-12
+    short = bench.accuracy_report(x, g * (1 - 1e-3), us, g, us)          # a uniformly shortened core
+    assert abs(short["core_scale_minus_1"] + 1e-3) < 1e-12
     bent = [u * (1 + 1e-3 * np.arange(u.shape[1])) for u in us]       # same columns' directions, wrong lengths
     rep = bench.accuracy_report(x, T.multi_ttm(x, bent, transpose=True), bent, g, us)
     assert max(rep["sine_per_mode"]) < 1e-7

@@ -600,11 +600,15 @@ def test_decay512_error_split_core_vs_factors():
     # least-squares core for the device's factors: X x_n pinv(U_n)
     g_ls = T.multi_ttm(x32, [np.linalg.pinv(v) for v in u])
     e_ls = M.rel_error(x32, g_ls, u)
-    e_tr = M.rel_error(x32, T.multi_ttm(x32, u, transpose=True), u)
+    g_t = T.multi_ttm(x32, u, transpose=True)
+    e_tr = M.rel_error(x32, g_t, u)
+    scale = float(np.sum(g * g_t) / np.sum(g_t * g_t) - 1)       # a systematic shortening shows here
+    lengths = [float(np.mean(np.linalg.norm(v, axis=0)) - 1) for v in u]
     orth = [M.orthonormality(v) for v in u]
     sine = [M.max_principal_sine(a, b) for a, b in zip(u, u_or)]
     print(f"\nE_gpu {e_gpu:.6e}  E_oracle {e_or:.6e}  E_lsq {e_ls:.6e}  E_transpose {e_tr:.6e}\n"
           f"orthonormality per mode {['%.2e' % o for o in orth]}  sine per mode {['%.2e' % v for v in sine]}\n"
+          f"core scale - 1 {scale:+.2e}  mean column length - 1 per mode {['%+.1e' % v for v in lengths]}\n"
           f"status (code, flags, orth_fail, fallbacks, fallback_rows, eig_sweeps) {status}")
     assert np.isfinite(e_gpu) and np.isfinite(e_ls) and np.isfinite(e_tr)
 
