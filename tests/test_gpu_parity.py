@@ -614,6 +614,27 @@ def test_decay512_error_split_core_vs_factors():
 
 
 @pytest.mark.slow
+def test_tensor_core_accumulation_is_unbiased():
+    """Diagnostic: does the tensor-core sketch round its FP32 accumulation without
+    bias?  X and Omega hold positive values exactly representable in TF32, so
+    every product is exact and the split's low parts are zero; the only rounding
+    left is the accumulation of 8-element partial sums over the long j range.
+    Round-to-nearest leaves a mean relative error near zero (about 1e-9 here);
+    rounding toward zero would shorten every sum by about (steps) u / 2, near
+    -1e-5.  Opt-in (RHOSVD_SLOW=1)."""
+    rng = np.random.default_rng(41)
+    I, J, K = 512, 262144, 42
+    x = (rng.integers(512, 1024, size=(I, J)) * 2.0 ** -9).astype(np.float32)      # 10-bit mantissas
+    om = (rng.integers(512, 1024, size=(J, K)) * 2.0 ** -9).astype(np.float32)
+    X = torch.from_numpy(np.asfortranarray(x).ravel(order="F")).cuda()
+    Y = host(R().rhosvd_sketch(X, (I, J), 0, K, Omega=dev_mat(om)))
+    want = x.astype(np.float64) @ om.astype(np.float64)
+    rel = (Y - want) / want
+    print(f"\nmean relative error {rel.mean():+.3e}, max |relative error| {np.abs(rel).max():.3e}")
+    assert abs(rel.mean()) <= 1e-7
+
+
+@pytest.mark.slow
 def test_decay512_mode1_stages():
     """Diagnostic for the same workload, mode 1 step by step through the
     primitives (seeded sketch, orthonormalisation, one power step,
