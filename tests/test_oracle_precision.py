@@ -21,7 +21,7 @@
   E agrees with the exact run to 1e-6 relative.
 * R-PET on the 128^4 workload, the single pass reading a BF16 or a per-slice
   e4m3 copy of X: E grows 2x and 25x, with or without an exact core pass.
-About five minutes of CPU: opt-in with RHOSVD_SLOW=1."""
+About twelve minutes of CPU: opt-in with RHOSVD_SLOW=1."""
 import numpy as np
 import pytest
 
