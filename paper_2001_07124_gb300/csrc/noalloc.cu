@@ -55,11 +55,16 @@ extern "C" rhosvd_status rhosvd_sketch_noalloc(const float* X, const rhosvd_shap
   if (X == nullptr || Omega == nullptr || Y == nullptr || mode < 0 || mode >= shape->N || K < 1 ||
       K > RHOSVD_MAX_K)
     return RHOSVD_EINVAL;
-  int64_t L = 1, Rt = 1;
+  // same shape rules as every other entry point: each size in [1, 2^40] and
+  // the element count below 2^62, so that no product of sizes overflows
+  int64_t L = 1, Rt = 1, tot = 1;
   for (int k = 0; k < shape->N; ++k) {
-    if (shape->dims[k] < 1 || shape->dims[k] > (int64_t(1) << 40)) return RHOSVD_EINVAL;
-    if (k < mode) L *= shape->dims[k];
-    if (k > mode) Rt *= shape->dims[k];
+    const int64_t d = shape->dims[k];
+    if (d < 1 || d > (int64_t(1) << 40)) return RHOSVD_EINVAL;
+    if (tot > (int64_t(1) << 62) / d) return RHOSVD_EINVAL;
+    tot *= d;
+    if (k < mode) L *= d;
+    if (k > mode) Rt *= d;
   }
   const int64_t I = shape->dims[mode];
   // one split needs I*K floats of scratch; larger sketches are rejected

@@ -6,7 +6,8 @@ cudaMalloc's implicit synchronisation is not allowed): its split-K scratch is a
 fixed device array inside the library.  The test calls it through the C ABI
 twice in a row, on different inputs, and checks each result against the
 existing rhosvd_sketch entry point within the sketch tolerance used by the
-parity tests.  This file is collected last so that a stop-at-first-failure run
+parity tests, and against the oracle's product of the same unfolding and
+test matrix in FP64.  This file is collected last so that a stop-at-first-failure run
 has already run every other test; it also passes on its own in a fresh process.
 """
 import ctypes
@@ -16,6 +17,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle import tensor as T  # noqa: E402
 from workloads import device_layout, gaussian_matrix, random_tensor  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -52,9 +54,12 @@ def test_noalloc_sketch_matches_workspace_sketch_twice(R, dims, mode, K):
         Y = torch.full((dims[mode] * K,), float("nan"), device="cuda")
         got = _noalloc(R, X, dims, mode, K, om, Y)
         want = R.rhosvd_sketch(X, dims, mode, K, Omega=om).cpu().numpy().astype(np.float64)
-        a = np.reshape(np.moveaxis(x.astype(np.float32).astype(np.float64), mode, 0), (dims[mode], -1), order="F")
-        bound = np.abs(a) @ np.abs(om_h.astype(np.float64))
+        a = T.unfold(x.astype(np.float32).astype(np.float64), mode)
+        om64 = om_h.astype(np.float64)
+        exact = a @ om64                               # the oracle's Y = X_(n) Omega in FP64
+        bound = np.abs(a) @ np.abs(om64)
         assert np.all(np.isfinite(got))
+        assert np.all(np.abs(got - exact) <= 1e-5 * bound + 1e-30)
         assert np.all(np.abs(got - want) <= 1e-5 * bound + 1e-30)
 
 
@@ -69,3 +74,7 @@ def test_noalloc_rejects_oversized_requests(R):
     code = R.lib().rhosvd_sketch_noalloc(X.data_ptr(), ctypes.byref(R.make_shape(dims)), 0, 4, None,
                                          Y.data_ptr(), None)
     assert code == 1   # Omega is required
+    # sizes whose product overflows 64-bit arithmetic are rejected like everywhere else
+    big = R.make_shape((1, 2 ** 40, 2 ** 40))
+    code = R.lib().rhosvd_sketch_noalloc(X.data_ptr(), ctypes.byref(big), 0, 1, om.data_ptr(), Y.data_ptr(), None)
+    assert code == 1
