@@ -205,6 +205,17 @@ class Workspace:
         self.nbytes = int(max(nbytes, 256))
         self.buf = torch.empty(self.nbytes, dtype=torch.uint8, device=device or "cuda")
 
+    @classmethod
+    def wrap(cls, buf):
+        """A workspace over an existing uint8 CUDA buffer (256-byte aligned), for
+        callers that carve it from memory they manage themselves."""
+        import torch
+        if buf.dtype != torch.uint8 or not buf.is_cuda or buf.data_ptr() % 256 != 0:
+            raise ValueError("expected a 256-byte aligned uint8 CUDA buffer")
+        ws = cls.__new__(cls)
+        ws.nbytes, ws.buf = int(buf.numel()), buf
+        return ws
+
     @property
     def ptr(self) -> int:
         return self.buf.data_ptr()

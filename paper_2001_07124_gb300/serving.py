@@ -3,8 +3,10 @@
 Requests (a tensor in pinned host memory, its dims, target ranks and the
 algorithm options) arrive over time.  The scheduler admits them in arrival
 order whenever a slot (a CUDA stream with its own workspace) is free and the
-device-memory budget covers the request's tensor, workspace and outputs (the
-library's own workspace query sizes it exactly). An admitted request copies
+device-memory budget covers what the slots hold: each slot keeps one device
+arena (workspace, tensor and outputs, sized by the library's own workspace
+query) and one pinned host buffer between requests, so steady-state requests
+allocate nothing. An admitted request copies
 its tensor to the device, runs rhosvd_decompose on its slot's stream and
 copies the core and factors back; completion is observed through a CUDA event.
 Requests that are on the device at the same time overlap there: one request's
@@ -55,14 +57,47 @@ class Result:
 class Scheduler:
     """FIFO admission under a slot count and a device-memory budget.
 
+    A slot keeps its device buffers between requests (so that a request does
+    not pay for an allocation), which makes the memory a slot holds, not the
+    memory its current request needs, the quantity the budget has to cover.
+    The scheduler therefore charges every slot what it holds: admitting a
+    request of ``bytes_needed`` b on a slot that holds h raises the slot's
+    holding to max(h, b), and idle slots hold their buffers until the head of
+    the queue needs the room, at which point the largest idle holdings are
+    released first.  The sum of all holdings never exceeds the budget.
+
     executor.bytes_needed(req) -> int, executor.start(req, slot) -> handle,
-    executor.done(handle) -> bool, executor.finish(handle) -> (G, Us) are the
-    only operations it uses; clock() returns seconds since the run started."""
+    executor.done(handle) -> bool, executor.finish(handle) -> (G, Us) and
+    executor.release(slot) are the only operations it uses; clock() returns
+    seconds since the run started."""
 
     def __init__(self, executor, slots: int, budget_bytes: int, clock: Callable[[], float]):
         if slots < 1 or budget_bytes <= 0:
             raise ValueError("need at least one slot and a positive budget")
         self.ex, self.slots, self.budget, self.clock = executor, slots, int(budget_bytes), clock
+        self.held = [0] * slots                       # bytes each slot holds (grows, or drops on release)
+        self.peak_held = 0
+
+    def _fit(self, need: int, free_slots: List[int]) -> Optional[int]:
+        """A free slot for a request of `need` bytes, releasing idle holdings
+        if the budget requires it; None when the request has to wait."""
+        # best fit: the smallest idle holding that already covers the request, else the largest one
+        covering = [s for s in free_slots if self.held[s] >= need]
+        slot = min(covering, key=lambda s: self.held[s]) if covering else max(free_slots, key=lambda s: self.held[s])
+        total = sum(self.held) - self.held[slot] + max(self.held[slot], need)
+        if total > self.budget:
+            for other in sorted((s for s in free_slots if s != slot and self.held[s] > 0),
+                                key=lambda s: -self.held[s]):
+                self.ex.release(other)
+                total -= self.held[other]
+                self.held[other] = 0
+                if total <= self.budget:
+                    break
+        if total > self.budget:
+            return None
+        self.held[slot] = max(self.held[slot], need)
+        self.peak_held = max(self.peak_held, sum(self.held))
+        return slot
 
     def run(self, requests: Sequence[Request], idle: Callable[[], None] = lambda: None) -> List[Result]:
         pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
@@ -70,86 +105,110 @@ class Scheduler:
             if self.ex.bytes_needed(r) > self.budget:
                 raise ValueError(f"request {r.rid} needs more device memory than the whole budget")
         free_slots = list(range(self.slots))
-        used = 0
-        active = []                                   # (req, slot, handle, bytes, admitted)
+        active = []                                   # (req, slot, handle, admitted)
         results: List[Result] = []
         head = 0
         while head < len(pending) or active:
             now = self.clock()
             still = []
-            for req, slot, h, nb, adm in active:       # retire finished requests
+            for req, slot, h, adm in active:           # retire finished requests
                 if self.ex.done(h):
                     G, Us = self.ex.finish(h)
                     results.append(Result(req.rid, req.arrival, adm, self.clock(), G, Us))
                     free_slots.append(slot)
-                    used -= nb
                 else:
-                    still.append((req, slot, h, nb, adm))
+                    still.append((req, slot, h, adm))
             active = still
             # admit in arrival order; the head of the queue waits until it fits
             while head < len(pending) and pending[head].arrival <= now and free_slots:
                 req = pending[head]
-                nb = self.ex.bytes_needed(req)
-                if used + nb > self.budget:
+                slot = self._fit(self.ex.bytes_needed(req), free_slots)
+                if slot is None:
                     break
-                slot = free_slots.pop(0)
+                free_slots.remove(slot)
                 h = self.ex.start(req, slot)
-                active.append((req, slot, h, nb, self.clock()))
-                used += nb
+                active.append((req, slot, h, self.clock()))
                 head += 1
             idle()
         return results
 
 
+def _align(n: int, a: int = 256) -> int:
+    return (int(n) + a - 1) // a * a
+
+
 class GpuExecutor:
-    """Runs requests on CUDA streams through the library (one workspace per slot)."""
+    """Runs requests on CUDA streams through the library.
+
+    Each slot owns one device arena, carved per request into the workspace,
+    the tensor and the outputs, and one pinned host buffer for the outputs.
+    Both are reused by the slot's next request and only grow (or are dropped
+    by ``release``), so a request in steady state allocates nothing."""
 
     def __init__(self, slots: int):
         import torch
         from . import rhosvd as R
         self.torch, self.R = torch, R
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
-        self.ws = [None] * slots
+        self.arena = [None] * slots                  # device uint8 buffers
+        self.host = [None] * slots                   # pinned float32 output buffers
+
+    def _layout(self, req: Request):
+        """Byte offsets (ws, X, G, U_1..U_N) of a request inside its slot's arena and the total."""
+        R = self.R
+        ws = _align(R.rhosvd_workspace_size(req.dims, req.ranks, req.algo, req.p, req.q))
+        sizes = [4 * int(np.prod(req.dims)), 4 * int(np.prod(req.ranks))] + \
+                [4 * int(d) * int(r) for d, r in zip(req.dims, req.ranks)]
+        offs, off = [0], ws
+        for sz in sizes:
+            offs.append(off)
+            off += _align(sz)
+        return offs, sizes, off
 
     def bytes_needed(self, req: Request) -> int:
-        R = self.R
-        n = int(np.prod(req.dims))
-        need = R.rhosvd_workspace_size(req.dims, req.ranks, req.algo, req.p, req.q)
-        out = int(np.prod(req.ranks)) + sum(int(d) * int(r) for d, r in zip(req.dims, req.ranks))
-        return 4 * (n + out) + int(need)
+        return self._layout(req)[2]
+
+    def release(self, slot: int):
+        self.arena[slot] = None
 
     def start(self, req: Request, slot: int):
         torch, R = self.torch, self.R
         s = self.streams[slot]
-        need = R.rhosvd_workspace_size(req.dims, req.ranks, req.algo, req.p, req.q)
+        offs, sizes, total = self._layout(req)
+        if self.arena[slot] is None or self.arena[slot].numel() < total:
+            self.arena[slot] = None
+            self.arena[slot] = torch.empty(total, dtype=torch.uint8, device="cuda")
+        nout = sum(sizes[1:]) // 4
+        if self.host[slot] is None or self.host[slot].numel() < nout:
+            self.host[slot] = torch.empty(nout, dtype=torch.float32).pin_memory()
+        a = self.arena[slot]
+        ws = R.Workspace.wrap(a[:offs[1]])
+        views = [a[o:o + sz].view(torch.float32) for o, sz in zip(offs[1:], sizes)]
+        X, G, Us = views[0], views[1], views[2:]
+        hv, off = [], 0
+        for sz in sizes[1:]:
+            hv.append(self.host[slot][off:off + sz // 4])
+            off += sz // 4
         with torch.cuda.stream(s):
-            if self.ws[slot] is None or self.ws[slot].nbytes < need:
-                self.ws[slot] = R.Workspace(need)
-            X = torch.empty(int(np.prod(req.dims)), dtype=torch.float32, device="cuda")
             X.copy_(req.x_host, non_blocking=True)
-            G = R.empty_colmajor(req.ranks)                               # flat column-major buffers
-            Us = [R.empty_colmajor((d, r)) for d, r in zip(req.dims, req.ranks)]
             R.rhosvd_decompose(X, req.dims, req.ranks, algo=req.algo, p=req.p, q=req.q, seed=req.seed,
-                               ws=self.ws[slot], out=(G, Us), stream=s, check=False)
-            gh = torch.empty(G.numel(), dtype=torch.float32).pin_memory()
-            uh = [torch.empty(u.numel(), dtype=torch.float32).pin_memory() for u in Us]
-            gh.copy_(G, non_blocking=True)
-            for a, b in zip(uh, Us):
-                a.copy_(b, non_blocking=True)
+                               ws=ws, out=(G, Us), stream=s, check=False)
+            for hbuf, dbuf in zip(hv, [G] + Us):
+                hbuf.copy_(dbuf, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)
-        return (req, slot, X, G, Us, gh, uh, ev)
+        return (req, slot, ws, hv, ev)
 
     def done(self, h) -> bool:
         return h[-1].query()
 
     def finish(self, h):
-        req, slot, X, G, Us, gh, uh, ev = h
+        req, slot, ws, hv, ev = h
         ev.synchronize()
-        code, _ = self.R.rhosvd_device_status(self.ws[slot], self.streams[slot])
+        code, _ = self.R.rhosvd_device_status(ws, self.streams[slot])
         if code != 0:
             raise RuntimeError(f"request {req.rid}: device status {code}")
-        return gh.numpy().copy(), [u.numpy().copy() for u in uh]
+        return hv[0].numpy().copy(), [u.numpy().copy() for u in hv[1:]]
 
 
 def serve(requests: Sequence[Request], slots: int = 4, budget_bytes: int = 150 * 10 ** 9) -> List[Result]:
