@@ -1,8 +1,8 @@
 // Tensor-core (tcgen05) n-mode product on a strided unfolding:
 //   Out(j, k) = sum_i X_(n)(i, j) M(i, k),   M(i, k) = Mp[i + ldm*k],
 //   X_(n)(i, j = l + L*r) = X[l + s_i*i + s_r*r]   (Sec. 2, Eq. for the n-mode product)
-// i.e. Z = X_(n)^T Q (the power-iteration TTM of Alg. 1 step 2), B^T = X_(n)^T Q
-// (the projection B = Q^T X_(n), Alg. 1 step 4) and, with X a tall matrix seen
+// i.e. Z = X_(n)^T Q (the power-iteration TTM of Alg. 1), B^T = X_(n)^T Q
+// (the projection B = Q^T X_(n) of Alg. 1) and, with X a tall matrix seen
 // as L = rows, Y R^-1 (the CholeskyQR apply) and the refold Ubar^T B.
 // Out(j, k) is written at Out[l + r*o_r + k*o_k] with j = l + o_L*r (o_L
 // defaults to the input's L).
@@ -27,10 +27,12 @@
 //     TF32 hi/lo and store it in tensor memory as the A operand (thread = row j
 //     = TMEM lane), split M into hi/lo B tiles in the canonical K-major layout;
 //   * warp 13 (one thread): per stage, four K steps of the three MMAs
-//     A_hi*B_hi + A_hi*B_lo + A_lo*B_hi into a double-buffered FP32 TMEM
-//     accumulator, committing the tile when its last stage is issued;
-//   * warps 8-11 (epilogue): read a finished accumulator (tcgen05.ld), write
-//     the rows of Out, and hand the buffer back while the next tile computes.
+//     A_hi*B_hi + A_hi*B_lo + A_lo*B_hi into an FP32 TMEM accumulator; every
+//     SEG stages of a tile form a segment with its own accumulator buffer (four
+//     buffers in turn), committed when the segment's last stage is issued;
+//   * warps 8-11 (epilogue): read each finished segment (tcgen05.ld), add it
+//     into FP32 registers, hand the buffer back, and write the rows of Out
+//     once the tile's last segment is in.
 // Requirements (checked by tc_ttm_supported): 16-byte aligned X and M, strides
 // multiple of 4 elements, ldm % 4 == 0, K <= 64, L % 4 == 0.  When 128
 // consecutive j would straddle r with L > 128 (L not a multiple of 128, Rt > 1)
@@ -56,8 +58,16 @@ constexpr int PRODUCER_WARP = 12, MMA_WARP = 13;
 constexpr int NUM_THREADS = NUM_XFORM + NUM_EPI + 64;   // + the producer and MMA warps
 constexpr uint32_t TMEM_COLS = 512;
 constexpr int D_COLS = 64;                // per accumulator buffer
-constexpr int A_COL0 = 2 * D_COLS;        // A stages after the two accumulators
+constexpr int NBUF = 4;                   // accumulator buffers, cycled per segment
+constexpr int A_COL0 = NBUF * D_COLS;     // A stages after the accumulators
 constexpr int A_STAGE_COLS = 2 * BI;      // 32 hi + 32 lo columns
+// The tensor core rounds its FP32 accumulation toward zero, so a long
+// accumulation in tensor memory drifts toward zero by about half an ulp per
+// MMA (measured -1e-5 relative over a 512^3 sketch).  Each output tile is
+// therefore accumulated in tensor memory only over segments of SEG stages
+// (SEG * 4 K steps, 3 MMAs each); the epilogue adds the segments in FP32
+// registers with round-to-nearest, in segment order (deterministic).
+constexpr int SEG = 2;
 
 // The M and B tiles hold NPAD rows (K padded to 16), and the X ring is as deep
 // as 227 KB allows.  The pace is set by the MMA stream (12 skinny MMAs per
@@ -77,7 +87,8 @@ struct __align__(1024) TtmSmem {
   float ostage[4][32 * 17];                // per epilogue warp: 32 rows x 16 columns (+1 pad)
   uint64_t full_x[X_STAGES], empty_x[X_STAGES];
   uint64_t full_a[A_STAGES], empty_a[A_STAGES];
-  uint64_t d_full[2], d_empty[2];
+  uint64_t d_full[NBUF], d_empty[NBUF];
+  uint64_t drain;                          // arrives when every MMA this CTA issued has completed
   uint32_t tmem_base;
   int abort_flag;
 };
@@ -107,6 +118,7 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   const int tile_rows = slab ? bl * tr : TILE_J;     // TMEM lanes holding data
   const uint32_t xbytes = (uint32_t)((M1 ? TILE_J : bl * tr) * BI * 4);
   const int nst = (I + BI - 1) / BI;                  // stages per tile
+  const int nseg = (nst + SEG - 1) / SEG;             // accumulation segments per tile
   constexpr uint32_t idesc = idesc_tf32(128, NPAD);
 
   if (tid == 0) {
@@ -118,10 +130,11 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
       mbar_init(&sm.full_a[a], 128);
       mbar_init(&sm.empty_a[a], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NBUF; ++b) {
       mbar_init(&sm.d_full[b], 1);
       mbar_init(&sm.d_empty[b], NUM_EPI);
     }
+    mbar_init(&sm.drain, 1);
     sm.abort_flag = 0;
     mbar_fence_init();
   }
@@ -139,6 +152,7 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   const int my_tiles = (ntiles > (int)blockIdx.x) ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int total = my_tiles * nst;                   // stages of this CTA
 
+  int issued = 0;                                     // stages the producer has put in flight
   if (warp == PRODUCER_WARP) {
     if (lane == 0) {
       const uint32_t bytes = xbytes + (uint32_t)(M_TILE * 4);
@@ -148,6 +162,7 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         if (!mbar_wait(&sm.empty_x[s], ph ^ 1u, abort_flag)) { ok = false; break; }
         const int tile = (int)blockIdx.x + (g / nst) * (int)gridDim.x;
         const int ib = (g % nst) * BI;
+        issued = g + 1;
         mbar_arrive_expect_tx(&sm.full_x[s], bytes);
         if (M1) {
           tma_load_2d(sm.x[s], &tmX, ib, tile * TILE_J, &sm.full_x[s]);
@@ -166,9 +181,11 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     if (lane == 0) {
       for (int g = 0; g < total && ok; ++g) {
         const int tl = g / nst, ks0 = g % nst;
-        const int buf = tl & 1;
-        if (ks0 == 0) {                                // accumulator buffer must be drained
-          if (!mbar_wait(&sm.d_empty[buf], ((uint32_t)(tl >> 1) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+        const int gs = tl * nseg + ks0 / SEG;          // segment of this stage, counted over the CTA
+        const int buf = gs % NBUF;
+        const bool seg_first = (ks0 % SEG) == 0, seg_last = (ks0 % SEG) == SEG - 1 || ks0 == nst - 1;
+        if (seg_first) {                               // the segment's buffer must have been drained
+          if (!mbar_wait(&sm.d_empty[buf], ((uint32_t)(gs / NBUF) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
         }
         const int a = g % A_STAGES;
         if (!mbar_wait(&sm.full_a[a], (uint32_t)(g / A_STAGES) & 1u, abort_flag)) { ok = false; break; }
@@ -180,13 +197,14 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         for (int ks = 0; ks < BI / 8; ++ks) {
           const uint64_t dbh = smem_desc_kmajor_nosw(bhi + ks * 256, 128, 1024);
           const uint64_t dbl = smem_desc_kmajor_nosw(blo + ks * 256, 128, 1024);
-          mma_tf32_ts(d, ahi + ks * 8, dbh, idesc, (ks0 > 0 || ks > 0) ? 1u : 0u);
+          mma_tf32_ts(d, ahi + ks * 8, dbh, idesc, (!seg_first || ks > 0) ? 1u : 0u);
           mma_tf32_ts(d, ahi + ks * 8, dbl, idesc, 1u);
           mma_tf32_ts(d, ahi + BI + ks * 8, dbh, idesc, 1u);
         }
         mma_commit(&sm.empty_a[a]);
-        if (ks0 == nst - 1) mma_commit(&sm.d_full[buf]);
+        if (seg_last) mma_commit(&sm.d_full[buf]);
       }
+      mma_commit(&sm.drain);
     }
   } else if (warp < 8) {
     // ------------------------------------------------------------ transform
@@ -254,9 +272,26 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     const int quad = warp & 3;
     const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
     for (int tl = 0; tl < my_tiles && ok; ++tl) {
-      const int buf = tl & 1;
-      if (!mbar_wait(&sm.d_full[buf], (uint32_t)(tl >> 1) & 1u, abort_flag)) { ok = false; break; }
-      tc_fence_after();
+      // the tile's segments, summed in FP32 registers in segment order
+      float acc[NPAD];
+#pragma unroll
+      for (int c = 0; c < NPAD; ++c) acc[c] = 0.f;
+      for (int sg = 0; sg < nseg && ok; ++sg) {
+        const int gs = tl * nseg + sg, buf = gs % NBUF;
+        if (!mbar_wait(&sm.d_full[buf], (uint32_t)(gs / NBUF) & 1u, abort_flag)) { ok = false; break; }
+        tc_fence_after();
+#pragma unroll
+        for (int c0 = 0; c0 < NPAD / 16; ++c0) {
+          uint32_t v[16];
+          tmem_ld_x16(tmem + lane_base + (uint32_t)(buf * D_COLS + 16 * c0), v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int c = 0; c < 16; ++c) acc[16 * c0 + c] += __uint_as_float(v[c]);
+        }
+        tc_fence_before();
+        mbar_arrive(&sm.d_empty[buf]);
+      }
+      if (!ok) break;
       const int tile = (int)blockIdx.x + tl * (int)gridDim.x;
       const int64_t tj0 = slab ? (int64_t)tile * tr * L : (int64_t)tile * TILE_J;   // first j of the tile
       int64_t j = tj0 + quad * 32 + lane;
@@ -274,11 +309,8 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         const int64_t jw = tj0 + quad * 32;                       // first row of this warp
 #pragma unroll
         for (int c0 = 0; c0 < NPAD; c0 += 16) {
-          uint32_t v[16];
-          tmem_ld_x16(tmem + lane_base + (uint32_t)(buf * D_COLS + c0), v);
-          tmem_wait_ld();
 #pragma unroll
-          for (int c = 0; c < 16; ++c) stg[lane * 17 + c] = __uint_as_float(v[c]);
+          for (int c = 0; c < 16; ++c) stg[lane * 17 + c] = acc[c0 + c];
           __syncwarp();
 #pragma unroll
           for (int q = 0; q < 16; ++q) {
@@ -289,21 +321,10 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           __syncwarp();
         }
       } else {
-        // all accumulator columns of the row in flight at once, one wait
-        uint32_t v[NPAD / 16][16];
 #pragma unroll
-        for (int c0 = 0; c0 < NPAD / 16; ++c0) tmem_ld_x16(tmem + lane_base + (uint32_t)(buf * D_COLS + 16 * c0), v[c0]);
-        tmem_wait_ld();
-#pragma unroll
-        for (int c0 = 0; c0 < NPAD / 16; ++c0)
-#pragma unroll
-          for (int c = 0; c < 16; ++c) {
-            const int k = 16 * c0 + c;
-            if (k < K && j < J) orow[(int64_t)k * o_k] = __uint_as_float(v[c0][c]);
-          }
+        for (int k = 0; k < NPAD; ++k)
+          if (k < K && j < J) orow[(int64_t)k * o_k] = acc[k];
       }
-      tc_fence_before();
-      mbar_arrive(&sm.d_empty[buf]);
     }
   }
   if (!ok) {
@@ -311,7 +332,24 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     set_error(st, RHOSVD_ETIMEOUT);
   }
   __syncthreads();
+  if (sm.abort_flag && warp == PRODUCER_WARP && lane == 0) {
+    // copies the producer issued may still be writing into the ring: wait
+    // (bounded) for the last phase of every stage it used before the CTA exits
+    for (int s = 0; s < X_STAGES && s < issued; ++s) {
+      const int g_last = s + X_STAGES * ((issued - 1 - s) / X_STAGES);
+      const uint64_t t0 = globaltimer_ns();
+      while (!mbar_try_wait(&sm.full_x[s], (uint32_t)(g_last / X_STAGES) & 1u) &&
+             globaltimer_ns() - t0 < kWaitLimitNs) {
+      }
+    }
+  }
   if (warp == MMA_WARP) {
+    if (sm.abort_flag && lane == 0) {
+      // MMAs already issued must finish before tensor memory is released
+      const uint64_t t0 = globaltimer_ns();
+      while (!mbar_try_wait(&sm.drain, 0) && globaltimer_ns() - t0 < kWaitLimitNs) {
+      }
+    }
     __syncwarp();
     tc_fence_after();
     tmem_dealloc(tmem, TMEM_COLS);
