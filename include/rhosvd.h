@@ -107,7 +107,7 @@ size_t rhosvd_primitive_workspace_size(const rhosvd_shape* shape, int32_t Kmax);
 
 /* ---------------------------------------------------------------- primitives */
 
-/* Gaussian test matrix (Alg. 1 step 1; Omega_n of Alg. 6 and Alg. 9):
+/* Gaussian test matrix (Omega of Alg. 1; Omega_n of Alg. 6 and Alg. 9):
  * Omega(j, k), j < rows, k < cols, written at Omega[j + k*ld] (ld >= rows).
  * Entry (j,k) is a deterministic function of (seed, stream_id, j, k):
  * Philox4x32-10 (Salmon et al. 2011) on counter (j mod 2^32, j div 2^32,
@@ -118,8 +118,8 @@ size_t rhosvd_primitive_workspace_size(const rhosvd_shape* shape, int32_t Kmax);
 rhosvd_status rhosvd_omega(uint64_t seed, uint32_t stream_id, int64_t rows, int32_t cols,
                            float* Omega, int64_t ld, void* stream);
 
-/* Mode-n sketch Y = X_(n) Omega (Alg. 1 step 2 with q = 0; Alg. 6 line 3;
- * Alg. 9 line 1).  Omega is J_n x K with leading dimension J_n
+/* Mode-n sketch Y = X_(n) Omega (the first product of Alg. 1,
+ * the factor sketches of Alg. 6 and Alg. 9).  Omega is J_n x K with leading dimension J_n
  * (J_n = prod_{k != mode} I_k); if Omega is NULL it is drawn from
  * (seed, stream_id = mode) as in rhosvd_omega.  Y is I_mode x K, ld = I_mode. */
 rhosvd_status rhosvd_sketch(const float* X, const rhosvd_shape* shape, int32_t mode, int32_t K,
@@ -146,7 +146,7 @@ rhosvd_status rhosvd_sketch(const float* X, const rhosvd_shape* shape, int32_t m
 rhosvd_status rhosvd_sketch_noalloc(const float* X, const rhosvd_shape* shape, int32_t mode, int32_t K,
                                     const float* Omega, float* Y, void* stream);
 
-/* Every sketch R-PET needs (Alg. 9 lines 1 and 3): Y[n] = X_(n) Omega_n
+/* Every sketch R-PET needs (Alg. 9: factor and core sketches): Y[n] = X_(n) Omega_n
  * (I_n x K[n], ld = I_n) for all n, and, if H is not NULL, the core sketch
  * H = X x_1 Omega~_1 ... x_N Omega~_N (S[0] x ... x S[N-1], column-major) with
  * Omega~_n of size S[n] x I_n (ld = S[n]).  NULL Omega / Omega_tilde arrays
@@ -156,14 +156,14 @@ rhosvd_status rhosvd_sketch_all(const float* X, const rhosvd_shape* shape, const
                                 const float* const* Omega, const float* const* Omega_tilde,
                                 float* const* Y, float* H, void* ws, size_t ws_bytes, void* stream);
 
-/* One power iteration of Alg. 1 step 2 in its stable form (the remark after
+/* One power iteration of Alg. 1 in its stable form (the remark after
  * Alg. 1): on entry Y_inout holds an I_n x K matrix Q with orthonormal
  * columns; the call forms Z = orth(X_(n)^T Q) (J_n x K) and writes the new
  * sketch X_(n) Z into Y_inout (not orthonormalised; call rhosvd_orth). */
 rhosvd_status rhosvd_power(const float* X, const rhosvd_shape* shape, int32_t mode, int32_t K,
                            float* Y_inout, void* ws, size_t ws_bytes, void* stream);
 
-/* Thin orthonormalisation Y = QR, Q overwriting Y (Alg. 1 step 3).  Y is
+/* Thin orthonormalisation Y = QR, Q overwriting Y (the orthonormal basis of Alg. 1).  Y is
  * m x K, leading dimension ld >= m, K <= RHOSVD_MAX_K, m >= K.  Method:
  * CholeskyQR2 (Yamamoto et al. 2015) with an FP64-accurate Gram; if a
  * Cholesky pivot is non-positive or too small, a Householder QR (the LAPACK
@@ -172,8 +172,8 @@ rhosvd_status rhosvd_power(const float* X, const rhosvd_shape* shape, int32_t mo
 rhosvd_status rhosvd_orth(float* Y, int64_t m, int32_t K, int64_t ld, int32_t* fallback_used,
                           void* ws, size_t ws_bytes, void* stream);
 
-/* Core projection G = X x_1 Q_1^T x_2 ... x_N Q_N^T (Eq. "Core"; Alg. 6
- * line 5).  Q[n] is I_n x K[n] with ld = I_n; a NULL Q[n] skips mode n
+/* Core projection G = X x_1 Q_1^T x_2 ... x_N Q_N^T (Eq. "Core"; the core of
+ * Alg. 6).  Q[n] is I_n x K[n] with ld = I_n; a NULL Q[n] skips mode n
  * (requires K[n] == I_n, the small-mode remark of Sec. 4).  G is
  * K[0] x ... x K[N-1], column-major. */
 rhosvd_status rhosvd_core(const float* X, const rhosvd_shape* shape, const float* const* Q,

@@ -8,11 +8,11 @@ GPU path and this oracle can be run on identical Omegas.
 Readings taken where the paper is silent or garbled:
 * sketch width K_n = min(R_n + p, I_n, J_n) with J_n the number of columns of
   the unfolding being sketched (oversampling of Remark 1 applied to Alg. 6);
-* the power iteration of Alg. 1 step 2 is evaluated as subspace iteration with
+* the power iteration of Alg. 1 is evaluated as subspace iteration with
   an orthonormalisation after every product (the stability note after Alg. 1):
   Z = orth(A^T Q), Q = orth(A Z), q times;
-* Alg. 8 starts from S = X (its first line prints S = X_(n));
-* R-PET step 5 ("truncate") is a truncated HOSVD of the small recovered core,
+* Alg. 8 starts from S = X (it prints S = X_(n));
+* the final truncation of R-PET is a truncated HOSVD of the small recovered core,
   whose factors are lifted through Q_n;
 * fixed accuracy: the tolerance eps is relative and split evenly over the modes,
   tol = eps ||X||_F / sqrt(N) per mode (Eqs. DT1 and SubPro disagree on the
@@ -44,22 +44,22 @@ def brsvd(a: np.ndarray, r: int, q: int, omega: np.ndarray, return_q: bool = Fal
     a      I x J data matrix
     r      target rank R
     q      number of power iterations
-    omega  J x K Gaussian test matrix, K = R + p (step 1, drawn by the caller)
+    omega  J x K Gaussian test matrix, K = R + p (drawn by the caller)
 
     Returns U = Q Ubar(:, 1:R) (I x R) and Ubar(:, 1:R)^T B = S V^T (R x J),
     the latter being the projected unfolding used by STHOSVD (the shortcut
     stated after Alg. 4).
     """
     a = np.asarray(a, dtype=np.float64)
-    y = a @ np.asarray(omega, dtype=np.float64)          # step 2, q = 0 part
-    qm = orth(y)                                         # step 3
-    for _ in range(q):                                   # step 2, (A A^T)^q A Omega
+    y = a @ np.asarray(omega, dtype=np.float64)          # sketch A Omega
+    qm = orth(y)                                         # its orthonormal basis
+    for _ in range(q):                                   # power iteration, (A A^T)^q A Omega
         z = orth(a.T @ qm)
         qm = orth(a @ z)
-    b = qm.T @ a                                         # step 4
-    ubar, _, _ = np.linalg.svd(b, full_matrices=False)   # step 5
+    b = qm.T @ a                                         # projection B = Q^T A
+    ubar, _, _ = np.linalg.svd(b, full_matrices=False)   # SVD of the small B
     ubar_r = ubar[:, :r]
-    u = qm @ ubar_r                                      # steps 6-7
+    u = qm @ ubar_r                                      # lift: U = Q Ubar_R
     out = (u, ubar_r.T @ b)
     if return_q:
         out = out + (qm,)
@@ -89,8 +89,8 @@ def sthosvd(x: np.ndarray, ranks: Sequence[int]):
     s = np.asarray(x, dtype=np.float64)
     us = []
     for n in range(s.ndim):
-        u = leading_left_singular_vectors(unfold(s, n), ranks[n])   # line 3
-        s = ttm(s, u.T, n)                                           # line 4
+        u = leading_left_singular_vectors(unfold(s, n), ranks[n])   # factor of the current core
+        s = ttm(s, u.T, n)                                           # shrink mode n
         us.append(u)
     return s, us
 

@@ -1,6 +1,6 @@
 """Counter-based Gaussian test matrices: Philox4x32-10 + Box-Muller.
 
-The paper draws Omega_n from a Gaussian distribution (Alg. 1 step 1, Alg. 6,
+The paper draws Omega_n from a Gaussian distribution (Alg. 1, Alg. 6,
 Alg. 9) and leaves the generator open.  This project fixes one so that a
 decomposition is reproducible from a 64-bit seed; the GPU library implements the
 same definition independently in CUDA.

@@ -114,7 +114,7 @@ void op_ttm(Ctx& c, const View& x, const float* M, int64_t m_i, int64_t m_k, int
 
 // CholeskyQR with device-side Householder fallback, in place on Y (m x K, ld).
 // passes = 2 is CholeskyQR2 (Q orthonormal to FP32 accuracy); passes = 1 is
-// used for the intermediate bases of the power iteration (Alg. 1 step 2),
+// used for the intermediate bases of the power iteration (Alg. 1),
 // where only range(Q) matters: a second pass would re-orthonormalise Q1 within
 // range(Q1) without changing it, and Q1 from the FP64-accurate first pass is
 // well conditioned whenever that pass succeeds.  The apply Y R^-1 runs as a
@@ -162,7 +162,7 @@ void op_omega(Ctx& c, uint64_t seed, uint32_t stream_id, int64_t rows, int cols,
 }
 
 // Y = X_(n) Omega with Omega the seeded Gaussian test matrix of (seed, stream_id)
-// (J x K, Alg. 1 step 1).  Where the tensor-core sketch can generate it (modes
+// (J x K, Alg. 1).  Where the tensor-core sketch can generate it (modes
 // with I > 128), Omega is computed inside the sketch kernel and never stored;
 // otherwise it is drawn into Om (J x K, caller's buffer) and sketched from memory.
 void op_sketch_seeded(Ctx& c, const View& x, int K, uint64_t seed, uint32_t stream_id, float* Y, int64_t ldy,
@@ -392,7 +392,7 @@ void run_rhosvd(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, con
     c.check(cudaMemcpyAsync(G, chain, sizeof(float) * t.numel(), cudaMemcpyDeviceToDevice, c.s));
 }
 
-// Core sketch chain H = X x_1 Omega~_1 ... x_N Omega~_N (Alg. 9 line 3).
+// Core sketch chain H = X x_1 Omega~_1 ... x_N Omega~_N (the core sketch of Alg. 9).
 void core_sketch_chain(Ctx& c, const float* X, const Geom& g, const int* S, uint64_t seed,
                        const float* const* Om_t, float* const* om_t_buf, float* H) {
   size_t max_t = 1, max_m = 1;
@@ -465,7 +465,9 @@ void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const
   double* Gd = c.take<double>(max_kk);
   float* Lf = c.take<float>(max_kk);
 
-  // lines 1-2: factor sketches and their orthonormal bases
+  // R-PET (Alg. 9, Sec. 5.1): factor sketches and their bases, the core
+  // sketch, recovery of the core by pseudo-inverses, truncation.
+  // Factor sketches Y_n = X_(n) Omega_n and their orthonormal bases Q_n
   for (int n = 0; n < N; ++n) {
     const float* W = (Omega != nullptr) ? Omega[n] : nullptr;
     if (W != nullptr)
@@ -474,11 +476,11 @@ void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const
       op_sketch_seeded(c, mode_view(X, g, n), pl.K[n], seed, (uint32_t)n, Ys[n], g.d[n], Om);
     op_orth(c, Ys[n], g.d[n], pl.K[n], g.d[n]);
   }
-  // line 3: core sketch
+  // core sketch H
   for (int n = 0; n < N; ++n)
     if (Omt[n] != nullptr) op_omega(c, seed, (uint32_t)(N + n), pl.S[n], (int)g.d[n], Omt[n]);
   core_sketch_chain(c, X, g, pl.S, seed, Omega_t, Omt, H);
-  // line 4: C = H x_n (Omega~_n Q_n)^+ with the pseudo-inverse from the normal
+  // recovered core C = H x_n (Omega~_n Q_n)^+ with the pseudo-inverse from the normal
   // equations (Omega~_n Q_n is a well-conditioned Gaussian-times-orthonormal
   // matrix): P^T = A (A^T A)^-1 = (A R^-1) R^-T, R^T R = A^T A
   Geom t = hs;
@@ -511,7 +513,7 @@ void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const
     cur = dst;
     ping ^= 1;
   }
-  // line 5: truncated HOSVD of the recovered core C (K_1 x ... x K_N)
+  // truncation: a truncated HOSVD of the recovered core C (K_1 x ... x K_N)
   for (int n = 0; n < N; ++n) {
     const int K = pl.K[n], R = ranks[n];
     const int64_t L = cs.L(n), Rt = cs.Rt(n);

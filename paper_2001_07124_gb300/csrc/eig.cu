@@ -1,6 +1,6 @@
 // Leading eigenvectors of a small symmetric positive semidefinite Gram matrix
-// G = B B^T (K x K, FP64): the "SVD of B" step of Alg. 1 (steps 5-7) and the
-// truncation of R-PET's recovered core (Alg. 9 line 5), where only the left
+// G = B B^T (K x K, FP64): the SVD of the small projected matrix B in Alg. 1
+// and the truncation of R-PET's recovered core (Alg. 9), where only the left
 // singular vectors of B are needed (the EVD route of Sec. 4).
 //
 // Rotating G itself in FP32 would limit eigenvector accuracy by

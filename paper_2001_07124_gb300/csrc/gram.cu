@@ -1,6 +1,6 @@
 // Gram matrix G = A^T A of a tall column-major matrix A (m x K, leading
-// dimension ld), reduced to FP64: the "small Gram" of CholeskyQR2 (Alg. 1
-// step 3) and of the truncation step (B B^T, Alg. 1 step 5).
+// dimension ld), reduced to FP64: the "small Gram" of CholeskyQR2 (the orthonormal
+// basis of Alg. 1) and of the truncation (B B^T, the SVD of B in Alg. 1).
 //
 // Only the upper triangle a <= b is accumulated (K(K+1)/2 pairs per row); each
 // CTA owns a contiguous block of rows, stages 64-row tiles in shared memory and

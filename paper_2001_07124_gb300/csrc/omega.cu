@@ -1,4 +1,4 @@
-// Gaussian test matrices Omega (Alg. 1 step 1) drawn from a counter-based
+// Gaussian test matrices Omega (the test matrices of Alg. 1) drawn from a counter-based
 // generator: entry (j, k) depends only on (seed, stream_id, j, k), so any
 // block of Omega can be produced by any thread in any order.
 #include "common.cuh"

@@ -1,5 +1,5 @@
-// Thin orthonormalisation of a tall m x K matrix (Alg. 1 step 3, Alg. 6 line 4,
-// Alg. 9 line 2): CholeskyQR2 with a Householder fallback.
+// Thin orthonormalisation of a tall m x K matrix (the orth steps of
+// Alg. 1, Alg. 6 and Alg. 9): CholeskyQR2 with a Householder fallback.
 //
 // CholeskyQR2 (Fukaya, Nakatsukasa, Yanagisawa, Yamamoto 2014; Yamamoto et al.
 // 2015): G = Y^T Y, R = chol(G), Q1 = Y R^-1, repeated once on Q1.  The Gram is

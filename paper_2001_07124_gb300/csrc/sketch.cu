@@ -1,6 +1,6 @@
 // SIMT contraction kernels on strided unfoldings (Sec. 2):
-//   sketch  Y(i,k) = sum_j X_(n)(i,j) W(j,k)   (Alg. 1 step 2, Alg. 6 line 3,
-//           Alg. 9 line 1; also the Gram A^T A of a tall matrix)
+//   sketch  Y(i,k) = sum_j X_(n)(i,j) W(j,k)   (the sketches of Alg. 1, Alg. 6
+//           and Alg. 9; also the Gram A^T A of a tall matrix)
 //   ttm     T(j,k) = sum_i X_(n)(i,j) M(i,k)    (n-mode product, power step
 //           Z = X_(n)^T Q, projection B = Q^T X_(n), core chain, Y <- Y R^-1)
 // The unfolding is never materialised: column j = l + L*r of X_(n) is read at

@@ -1,6 +1,6 @@
 // Tensor-core (tcgen05) sketch Y = X_(n) W on a strided unfolding:
 // Y(i,k) = sum_j X_(n)(i,j) W[j + J*k], X_(n)(i, j = l + L*r) = X[l + s_i*i + s_r*r]
-// (Alg. 1 step 2, Alg. 6 line 3, Alg. 9 line 1; for n = 1 the dominant pass of
+// (the sketches of Alg. 1, Alg. 6 and Alg. 9; for n = 1 the dominant pass of
 // R-STHOSVD).  Two stage layouts of the 16 j x 512 i X tile:
 //   * mode 1 (L = 1): 2-D boxes {256 i, 16 j}, smem [jj][256 i];
 //   * strided (L % 16 == 0): 3-D boxes {16 l, 256 i, 1 r} over [L, I, Rt] with

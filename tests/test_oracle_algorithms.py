@@ -48,7 +48,7 @@ def _decaying_matrix(m, n, seed, decay=0.7):
 
 @pytest.mark.parametrize("q", [1, 2])
 def test_power_iteration_spans_explicit_power(q):
-    """Alg. 1 step 2: range(Q) = range((A A^T)^q A Omega) (Remark 1 closed form)."""
+    """Power iteration of Alg. 1: range(Q) = range((A A^T)^q A Omega) (Remark 1 closed form)."""
     a, _ = _decaying_matrix(60, 40, 2, decay=0.9)
     om = np.random.default_rng(3).standard_normal((40, 8))
     _, _, qm = A.brsvd(a, 5, q, om, return_q=True)
@@ -253,7 +253,7 @@ def test_planted_mistakes_fail_exact_recovery(monkeypatch):
     monkeypatch.setattr(A.np.linalg, "svd", real_svd)
     assert M.rel_error(x, g, us) > 1e-3
 
-    # transposed operand instead of the pseudo-inverse in R-PET step 4
+    # transposed operand instead of the pseudo-inverse in R-PET's core recovery
     K = tuple(r + 2 for r in ranks)
     omf, omt = _omegas("rpet", dims, ranks, 2, K=K, S=tuple(2 * k + 1 for k in K))
     monkeypatch.setattr(A, "pinv_lstsq", lambda a: np.asarray(a).T)
