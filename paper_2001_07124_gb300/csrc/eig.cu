@@ -211,6 +211,45 @@ small_eig_kernel(const double* __restrict__ G, int K, int R, float* __restrict__
       }
     }
   }
+  // ------------------------------------------------ orthonormality polish
+  // The Jacobi stop (column cosines <= jtol) leaves the columns orthonormal to
+  // about 2e-6.  One first-order step of U <- U (U^T U)^(-1/2), namely
+  // U <- U - U D / 2 with D = U^T U - I, brings that to FP32 rounding level; it
+  // multiplies U from the right by an invertible R x R matrix, so range(U)
+  // (the truncation's subspace) is unchanged.  D is formed with compensated
+  // dot products (Ogita, Rump & Oishi 2005, Dot2) since its entries are
+  // differences from 1 far below the FP32 unit roundoff of the diagonal.
+  __syncthreads();
+  float* Us = X;                                            // K x R copy of the columns (X is free now)
+  float* D = reinterpret_cast<float*>(Gs);                 // R x R, fits in the K x K FP64 region
+  for (int e = tid; e < K * R; e += blockDim.x) {
+    const int r = e % K, a = e / K;
+    Us[r + a * K] = Ub[r + a * ldu];
+  }
+  __syncthreads();
+  for (int e = tid; e < R * R; e += blockDim.x) {
+    const int a = e % R, b = e / R;
+    const float* ua = Us + a * K;
+    const float* ub = Us + b * K;
+    float sum = 0.f, comp = 0.f;
+    for (int r = 0; r < K; ++r) {
+      // _rn intrinsics: never contracted into FMAs, so the error terms stay exact
+      const float p = __fmul_rn(ua[r], ub[r]);
+      const float pe = fmaf(ua[r], ub[r], -p);             // exact product error
+      const float t = __fadd_rn(sum, p);                    // two-sum of sum and p
+      const float bv = __fsub_rn(t, sum);
+      comp += __fadd_rn(__fsub_rn(sum, __fsub_rn(t, bv)), __fsub_rn(p, bv)) + pe;
+      sum = t;
+    }
+    D[a + b * R] = (sum - (a == b ? 1.f : 0.f)) + comp;
+  }
+  __syncthreads();
+  for (int e = tid; e < K * R; e += blockDim.x) {
+    const int r = e % K, a = e / K;
+    float corr = 0.f;
+    for (int b = 0; b < R; ++b) corr = fmaf(Us[r + b * K], D[b + a * R], corr);
+    Ub[r + a * ldu] = fmaf(-0.5f, corr, Us[r + a * K]);
+  }
 }
 
 template <int KB>

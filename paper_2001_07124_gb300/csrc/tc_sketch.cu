@@ -1,35 +1,39 @@
 // Tensor-core (tcgen05) sketch Y = X_(n) W on a strided unfolding:
 // Y(i,k) = sum_j X_(n)(i,j) W[j + J*k], X_(n)(i, j = l + L*r) = X[l + s_i*i + s_r*r]
 // (the sketches of Alg. 1, Alg. 6 and Alg. 9; for n = 1 the dominant pass of
-// R-STHOSVD).  Two stage layouts of the 16 j x 512 i X tile:
-//   * mode 1 (L = 1): 2-D boxes {256 i, 16 j}, smem [jj][256 i];
-//   * strided (L % 16 == 0): 3-D boxes {16 l, 256 i, 1 r} over [L, I, Rt] with
-//     64-byte swizzle, smem [i][16 l], each lane reading its own 64-byte row as
-//     four float4 (16-byte chunk c of row i sits at chunk c ^ ((i >> 1) & 3)).
-// Short modes (I <= 128) stage 64 j x 128 rows instead (four 16-j chunks of
-// one MMA tile, mode-1 box {128 i, 64 j}, strided boxes {16 l, 128 i, 1 r} per
-// chunk), so that every stage still moves 32 KB of X.
+// R-STHOSVD).  A stage holds 32 KB of X: 32 j x 256 rows i (two 128-row MMA
+// tiles, two 16-j chunks) for modes with I > 128, 64 j x 128 rows (one tile,
+// four chunks) for short modes.  Layouts in shared memory:
+//   * mode 1 (L = 1): one 2-D box {rows i, stage j}, smem [jj][rows];
+//   * strided (L % 16 == 0): one 3-D box {16 l, rows i, 1 r} per 16-j chunk
+//     over [L, I, Rt] with 64-byte swizzle, smem [chunk][i][16 l], each lane
+//     reading its own 64-byte row as four float4 (16-byte piece q of row i
+//     sits at piece q ^ ((i >> 1) & 3)).
 //
 // The contraction over j is split over CTAs (one CTA per SM, persistent); each
-// CTA owns up to 512 rows i (four 128-row MMA tiles) and every gridDim.x-th
-// stage-sized block of j, and writes its partial I x K block for the
-// fixed-order reducer.  Interleaving the blocks keeps the CTAs' concurrent
-// reads within one window of each row of X_(n) (measured the same as
-// contiguous per-CTA ranges on the 512^3 and 128^4 workloads).
+// CTA owns up to 256 rows i and every gridDim.x-th stage-sized block of j, and
+// writes its partial I x K block for the fixed-order reducer.  Interleaving
+// the blocks keeps the CTAs' concurrent reads within one window of each row
+// of X_(n), and CTAs of different row groups read the same W block at about
+// the same time (its second read comes from L2).
 //
-// Data path per 16-column block of j (two MMA K steps of kind::tf32):
-//   * TMA copies the X tile (16 x 512 FP32, two 256-wide boxes) and the raw W
-//     tile (16 x NPAD) into a 3- to 6-stage shared-memory ring (producer warp 8).
-//   * Eight transform warps (two warpgroups; warp w owns TMEM lane quadrant
-//     w % 4, warpgroup g the 128-row tiles 2g and 2g+1) read X rows from
-//     shared memory, split every value into TF32 hi + lo (3xTF32) and store
-//     both into tensor memory as the A operand (tcgen05.st), so the skinny
-//     N <= 64 GEMM never re-reads A from shared memory; they also split the W
-//     tile into hi/lo B tiles in the canonical no-swizzle K-major layout.
-//   * One thread of warp 9 issues, per 128-row tile and K step, the three MMAs
-//     A_hi*B_hi + A_hi*B_lo + A_lo*B_hi into FP32 accumulators in TMEM.
-//   * At the end the transform warps read the accumulators (tcgen05.ld) and
-//     write the partial sums.
+// Products in 3xTF32 (each FP32 value split into a TF32 part hi and an exact
+// remainder lo, Ootomo & Yokota 2022): X_hi W_hi + X_hi W_lo + X_lo W_hi.  The
+// B operand of a chunk is the stacked [W_hi; W_lo] (N = 2 NPAD rows), so each
+// K step of a tile takes two MMAs instead of three skinny ones:
+//   D[:, 0:2NPAD)  += X_hi [W_hi W_lo]     (N = 2 NPAD)
+//   D[:, 0:NPAD)   += X_lo W_hi            (N = NPAD)
+// and Y = D[:, 0:NPAD) + D[:, NPAD:2NPAD).  Roles:
+//   * TMA producer (warp 8): the X tile and the raw W tiles (16 x NPAD per
+//     chunk) of a stage into a shared-memory ring;
+//   * eight transform warps (two warpgroups; warp w owns TMEM lane quadrant
+//     w % 4; warpgroup g fills A slots 2g and 2g+1, slot u = (tile u / NC,
+//     chunk u % NC)) split X into hi and lo and store both into tensor memory
+//     as the A operand (tcgen05.st), and build the hi/lo B tiles in the
+//     canonical no-swizzle K-major layout;
+//   * one thread of warp 9 issues the MMAs into FP32 accumulators in TMEM;
+//   * at the end the transform warps read the accumulators (tcgen05.ld), add
+//     the two halves and write the partial sums.
 // Requirements (checked by tc_sketch_supported): K <= 64, J >= 1024, W a
 // plain J x K matrix with J % 4 == 0, 16-byte aligned pointers; mode 1 needs
 // I % 4 == 0, a strided view L % 16 == 0 and strides that are multiples of 4.
@@ -50,35 +54,37 @@ constexpr int A_STAGES = 2;
 constexpr int NUM_XFORM = 256;            // warps 0-7
 constexpr int NUM_THREADS = NUM_XFORM + 64;   // + warp 8 producer, warp 9 MMA issuer
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int D_COLS = 64;                // accumulator columns reserved per tile
-constexpr int A_COL0 = 4 * D_COLS;        // first TMEM column of the A stages
+constexpr int D_COLS = 128;               // accumulator columns per tile: the hi and lo halves (<= 64 each)
 constexpr int A_STAGE_COLS = 128;         // per stage: 4 slots x (16 hi + 16 lo)
 constexpr int STAGE_FLOATS = 8192;        // X floats per stage (32 KB)
 constexpr size_t kSmemLimit = 232448;     // dynamic shared memory per CTA (227 KB)
 
-// Stage geometry, NC = chunks of 16 j per stage: NC = 1 stages 16 j x 512 rows
-// (four 128-row MMA tiles), NC = 4 stages 64 j x 128 rows (one tile, four
-// chunks) for short modes (I <= 128).  The four TMEM A slots of a stage hold
-// tiles (NC = 1) or chunks (NC = 4).  The W and B tiles hold only NPAD rows
-// (K padded to 16) and the rest of shared memory deepens the X ring.  The pace
-// is set by the MMA stream (24 skinny MMAs per stage), not by the TMA copies:
-// the X tiles are in shared memory before the transform asks for them.
+// Stage geometry, NC = chunks of 16 j per stage: NC = 2 stages 32 j x 256 rows
+// (two 128-row tiles), NC = 4 stages 64 j x 128 rows (one tile) for short modes
+// (I <= 128).  The four TMEM A slots of a stage hold (tile, chunk) pairs.  The W
+// and B tiles hold only NPAD rows (K padded to 16) and the rest of shared memory
+// deepens the X ring.
 template <int NPAD, int NC>
 struct Geo {
-  static constexpr int ROWS = 512 / NC;                   // rows i per CTA
+  static constexpr int TILES = 4 / NC;                    // 128-row tiles per CTA
+  static constexpr int ROWS = 128 * TILES;                // rows i per CTA (one TMA box)
   static constexpr int SBJ = BJ * NC;                     // j per stage
-  static constexpr int BOXW = ROWS < 256 ? ROWS : 256;    // rows per TMA box
-  static constexpr int X_STAGES = NPAD <= 48 ? (NC == 1 ? 6 : 4) : (NC == 1 ? 5 : 3);
   static constexpr int W_TILE = NPAD * BJ;                // floats per W / B tile
+  static constexpr int A_COL0 = TILES * D_COLS;           // first TMEM column of the A stages
+  static constexpr size_t FIXED = (size_t)A_STAGES * NC * 2 * W_TILE * 4 + 2048;
+  static constexpr size_t PER_STAGE = (size_t)STAGE_FLOATS * 4 + (size_t)NC * W_TILE * 4;
+  static constexpr int X_STAGES_FIT = (int)((kSmemLimit - 1024 - FIXED) / PER_STAGE);
+  static constexpr int X_STAGES = X_STAGES_FIT < 6 ? X_STAGES_FIT : 6;
+  static_assert(A_COL0 + A_STAGES * A_STAGE_COLS <= (int)TMEM_COLS, "tensor memory overflow");
+  static_assert(2 * NPAD <= D_COLS, "accumulator halves exceed the tile's columns");
 };
 
 template <int NPAD, int NC>
 struct __align__(1024) SketchSmem {
   using G = Geo<NPAD, NC>;
-  // mode 1: boxes [box][jj][BOXW]; strided: boxes [box][i][16] (NC = 1: row boxes, NC = 4: chunk boxes)
-  float x[G::X_STAGES][STAGE_FLOATS];
+  float x[G::X_STAGES][STAGE_FLOATS];        // mode 1: [jj][rows]; strided: [chunk][i][16]
   float wraw[G::X_STAGES][NC][G::W_TILE];    // TMA boxes [n][jj] (64B swizzle), rows n >= K zero-filled
-  float b[A_STAGES][2][NC][G::W_TILE];       // hi / lo B tiles, canonical K-major layout
+  float b[A_STAGES][NC][2][G::W_TILE];       // per chunk the hi tile, then the lo tile (one N = 2 NPAD operand)
   uint64_t full_x[G::X_STAGES], empty_x[G::X_STAGES];
   uint64_t full_a[A_STAGES], empty_a[A_STAGES];
   uint64_t done;
@@ -89,7 +95,8 @@ struct __align__(1024) SketchSmem {
 // B tiles (N x 16 K elements, K-major, no swizzle): element (n, kk) sits at
 // byte (n >> 3) * 512 + (kk >> 2) * 128 + (n & 7) * 16 + (kk & 3) * 4, i.e.
 // 8-row x 16-byte core matrices with LBO = 128 (K direction) and SBO = 512
-// (N direction); the second MMA K step starts 256 bytes in.
+// (N direction); the second MMA K step starts 256 bytes in.  The lo tile
+// follows the hi tile directly, so rows NPAD.. of the stacked operand are lo.
 
 // GEN: W is the seeded Gaussian test matrix Omega(j, k) of (seed, stream),
 // computed in the transform warps from the counter-based generator (the same
@@ -101,7 +108,7 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
                  int64_t L, int64_t J, int K, float* __restrict__ part, uint64_t seed,
                  uint32_t stream_id, DevStatus* st) {
   using G = Geo<NPAD, NC>;
-  constexpr int X_STAGES = G::X_STAGES, ROWS = G::ROWS, SBJ = G::SBJ, BOXW = G::BOXW;
+  constexpr int X_STAGES = G::X_STAGES, ROWS = G::ROWS, SBJ = G::SBJ, A_COL0 = G::A_COL0;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   SketchSmem<NPAD, NC>& sm = *reinterpret_cast<SketchSmem<NPAD, NC>*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -110,13 +117,11 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
   const int i0 = blockIdx.y * ROWS;
   const int rows = min(ROWS, I - i0);
   const int mt = (rows + 127) / 128;                 // MMA tiles in this CTA
-  const int nslot = NC == 1 ? mt : NC;               // occupied A slots per stage
-  const int nbox = M1 ? (rows + BOXW - 1) / BOXW : (NC == 1 ? (rows + BOXW - 1) / BOXW : NC);
   // stage kb of this CTA covers j in [(split + kb * nsplit) * SBJ, ... + SBJ) clipped to J
   const int64_t nblk = (J + SBJ - 1) / SBJ, nsplit = gridDim.x;
   const int nkb = nblk > split ? (int)((nblk - 1 - split) / nsplit + 1) : 0;
   auto stage_j = [&](int kb) -> int64_t { return ((int64_t)split + (int64_t)kb * nsplit) * SBJ; };
-  constexpr uint32_t idesc = idesc_tf32(128, NPAD);
+  constexpr uint32_t idesc2 = idesc_tf32(128, 2 * NPAD), idesc1 = idesc_tf32(128, NPAD);
 
   if (tid == 0) {
     for (int s = 0; s < X_STAGES; ++s) {
@@ -141,31 +146,31 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
   const uint32_t tmem = sm.tmem_base;
   volatile int* abort_flag = &sm.abort_flag;
   bool ok = true;
+  int issued = 0;                                    // stages the producer has put in flight
 
   if (warp == 8) {
     // ------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      const uint32_t box_bytes = M1 ? (uint32_t)(SBJ * BOXW * 4) : (uint32_t)(BJ * BOXW * 4);
-      const uint32_t bytes = (uint32_t)nbox * box_bytes + (GEN ? 0u : (uint32_t)(NC * G::W_TILE * 4));
+      const uint32_t bytes = (uint32_t)(STAGE_FLOATS * 4) + (GEN ? 0u : (uint32_t)(NC * G::W_TILE * 4));
       for (int kb = 0; kb < nkb && ok; ++kb) {
         const int s = kb % X_STAGES;
         const uint32_t ph = (uint32_t)(kb / X_STAGES) & 1u;
         if (!mbar_wait(&sm.empty_x[s], ph ^ 1u, abort_flag)) { ok = false; break; }
+        issued = kb + 1;
         mbar_arrive_expect_tx(&sm.full_x[s], bytes);
         const int jt = (int)stage_j(kb);
         if (M1) {
-          for (int bx = 0; bx < nbox; ++bx)
-            tma_load_2d(sm.x[s] + bx * SBJ * BOXW, &tmX, i0 + bx * BOXW, jt, &sm.full_x[s]);
+          tma_load_2d(sm.x[s], &tmX, i0, jt, &sm.full_x[s]);
         } else {
-          const int64_t rj = (int64_t)jt / L;
-          const int lj = (int)((int64_t)jt - rj * L);
-          for (int bx = 0; bx < nbox; ++bx) {
-            const int li = NC == 1 ? lj : lj + BJ * bx;          // chunk boxes walk l
-            const int ii = NC == 1 ? i0 + bx * BOXW : i0;         // row boxes walk i
-            tma_load_3d(sm.x[s] + bx * BJ * BOXW, &tmX, li, ii, (int)rj, &sm.full_x[s]);
+          // one box per 16-j chunk; a chunk never crosses r since L % 16 == 0
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const int64_t jc = (int64_t)jt + BJ * c, rc = jc / L;
+            tma_load_3d(sm.x[s] + c * BJ * ROWS, &tmX, (int)(jc - rc * L), i0, (int)rc, &sm.full_x[s]);
           }
         }
         if (!GEN)
+#pragma unroll
           for (int c = 0; c < NC; ++c) tma_load_2d(sm.wraw[s][c], &tmW, jt + BJ * c, 0, &sm.full_x[s]);
       }
     }
@@ -177,18 +182,18 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
         const uint32_t ph = (uint32_t)(kb / A_STAGES) & 1u;
         if (!mbar_wait(&sm.full_a[a], ph, abort_flag)) { ok = false; break; }
         tc_fence_after();
-        for (int u = 0; u < nslot; ++u) {
-          const int t = NC == 1 ? u : 0, c = NC == 1 ? 0 : u;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int t = u / NC, c = u % NC;
+          if (t >= mt) continue;
           const uint32_t d = tmem + (uint32_t)(t * D_COLS);
           const uint32_t ahi = tmem + (uint32_t)(A_COL0 + a * A_STAGE_COLS + u * 32);
-          const uint32_t bhi = smem_u32(sm.b[a][0][c]), blo = smem_u32(sm.b[a][1][c]);
+          const uint32_t bhl = smem_u32(sm.b[a][c][0]);
 #pragma unroll
           for (int ks = 0; ks < 2; ++ks) {
-            const uint64_t dbh = smem_desc_kmajor_nosw(bhi + ks * 256, 128, 512);
-            const uint64_t dbl = smem_desc_kmajor_nosw(blo + ks * 256, 128, 512);
-            mma_tf32_ts(d, ahi + ks * 8, dbh, idesc, (kb > 0 || c > 0 || ks > 0) ? 1u : 0u);
-            mma_tf32_ts(d, ahi + ks * 8, dbl, idesc, 1u);
-            mma_tf32_ts(d, ahi + 16 + ks * 8, dbh, idesc, 1u);
+            const uint64_t db = smem_desc_kmajor_nosw(bhl + ks * 256, 128, 512);
+            mma_tf32_ts(d, ahi + ks * 8, db, idesc2, (kb > 0 || c > 0 || ks > 0) ? 1u : 0u);
+            mma_tf32_ts(d, ahi + 16 + ks * 8, db, idesc1, 1u);
           }
         }
         mma_commit(&sm.empty_a[a]);
@@ -226,8 +231,8 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
               const int w = (n >> 3) * 128 + (jj >> 2) * 32 + (n & 7) * 4 + (jj & 3);
               uint32_t h, l;
               split_tf32(n < K ? z[e] : 0.f, h, l);
-              reinterpret_cast<uint32_t*>(sm.b[a][0][c])[w] = h;
-              reinterpret_cast<uint32_t*>(sm.b[a][1][c])[w] = l;
+              reinterpret_cast<uint32_t*>(sm.b[a][c][0])[w] = h;
+              reinterpret_cast<uint32_t*>(sm.b[a][c][1])[w] = l;
             }
           }
         }
@@ -235,26 +240,24 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
       if (!mbar_wait(&sm.full_x[s], phx, abort_flag)) { ok = false; break; }
 #pragma unroll
       for (int uu = 0; uu < 2; ++uu) {
-        const int u = 2 * wg + uu;                    // A slot: tile (NC = 1) or chunk (NC = 4)
-        if (u < nslot) {
-          const int t = NC == 1 ? u : 0, c = NC == 1 ? 0 : u;
+        const int u = 2 * wg + uu;                    // A slot: (tile, chunk)
+        const int t = u / NC, c = u % NC;
+        if (t < mt) {
           const int r = t * 128 + row_in_tile;       // row within the CTA's block
           const int vc = valid - BJ * c;              // valid j of this chunk (may be <= 0)
           uint32_t hi[16], lo[16];
           if (M1) {
-            const float* xb = sm.x[s] + (r / BOXW) * SBJ * BOXW + (r % BOXW) + BJ * c * BOXW;
+            const float* xb = sm.x[s] + BJ * c * ROWS + r;
 #pragma unroll
             for (int jj = 0; jj < BJ; ++jj) {
-              const float v = (jj < vc && r < rows) ? xb[jj * BOXW] : 0.f;
+              const float v = (jj < vc && r < rows) ? xb[jj * ROWS] : 0.f;
               split_tf32(v, hi[jj], lo[jj]);
             }
           } else {
-            const int bx = NC == 1 ? r / BOXW : c;
-            const int rr = NC == 1 ? r % BOXW : r;
-            const float4* xr = reinterpret_cast<const float4*>(sm.x[s] + bx * BJ * BOXW + rr * BJ);
+            const float4* xr = reinterpret_cast<const float4*>(sm.x[s] + c * BJ * ROWS + r * BJ);
 #pragma unroll
             for (int q = 0; q < BJ / 4; ++q) {
-              float4 v = xr[q ^ ((rr >> 1) & 3)];
+              float4 v = xr[q ^ ((r >> 1) & 3)];
               if (r >= rows) v = make_float4(0.f, 0.f, 0.f, 0.f);
               const float e[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
@@ -276,13 +279,13 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
         for (int u = 0; u < NPAD * BJ / NUM_XFORM; ++u) {
           const int w = tid + u * NUM_XFORM;
           const int n = 8 * (w >> 7) + ((w >> 2) & 7), jj = 4 * ((w >> 5) & 3) + (w & 3);
-          // raw W tile rows are 64-byte swizzled: 16-byte chunk q of row n sits at q ^ ((n >> 1) & 3)
+          // raw W tile rows are 64-byte swizzled: 16-byte piece q of row n sits at q ^ ((n >> 1) & 3)
           const float v =
               (jj < vc && n < K) ? sm.wraw[s][c][n * BJ + (((jj >> 2) ^ ((n >> 1) & 3)) << 2) + (jj & 3)] : 0.f;
           uint32_t h, l;
           split_tf32(v, h, l);
-          reinterpret_cast<uint32_t*>(sm.b[a][0][c])[w] = h;
-          reinterpret_cast<uint32_t*>(sm.b[a][1][c])[w] = l;
+          reinterpret_cast<uint32_t*>(sm.b[a][c][0])[w] = h;
+          reinterpret_cast<uint32_t*>(sm.b[a][c][1])[w] = l;
         }
       }
       fence_proxy_async_smem();
@@ -295,20 +298,20 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
     if (ok && nkb > 0) ok = mbar_wait(&sm.done, 0, abort_flag);
     if (ok) {
       tc_fence_after();
-#pragma unroll
-      for (int tt = 0; tt < 2; ++tt) {
-        const int t = 2 * wg + tt;
-        if (t >= mt) continue;
+      for (int t = wg; t < mt; t += 2) {
         const int64_t i = i0 + t * 128 + row_in_tile;
 #pragma unroll
         for (int c0 = 0; c0 < NPAD; c0 += 16) {
-          uint32_t v[16];
-          tmem_ld_x16(tmem + lane_base + (uint32_t)(t * D_COLS + c0), v);
+          uint32_t vh[16], vl[16];
+          tmem_ld_x16(tmem + lane_base + (uint32_t)(t * D_COLS + c0), vh);
+          tmem_ld_x16(tmem + lane_base + (uint32_t)(t * D_COLS + NPAD + c0), vl);
           tmem_wait_ld();
 #pragma unroll
           for (int c = 0; c < 16; ++c) {
             const int k = c0 + c;
-            if (k < K && i < I) part[((int64_t)split * K + k) * I + i] = (nkb > 0) ? __uint_as_float(v[c]) : 0.f;
+            if (k < K && i < I)
+              part[((int64_t)split * K + k) * I + i] =
+                  (nkb > 0) ? __uint_as_float(vh[c]) + __uint_as_float(vl[c]) : 0.f;
           }
         }
       }
@@ -318,9 +321,19 @@ tc_sketch_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
     *abort_flag = 1;
     set_error(st, RHOSVD_ETIMEOUT);
   }
-  // teardown: every role is past its last wait (all waits are bounded); let
-  // in-flight MMAs drain before TMEM is released
+  // teardown: every role is past its last wait (all waits are bounded); on the
+  // abort path let copies and MMAs in flight drain before the CTA releases
+  // tensor memory and exits
   __syncthreads();
+  if (sm.abort_flag && warp == 8 && lane == 0) {
+    for (int s = 0; s < X_STAGES && s < issued; ++s) {
+      const int kb_last = s + X_STAGES * ((issued - 1 - s) / X_STAGES);
+      const uint64_t t0 = globaltimer_ns();
+      while (!mbar_try_wait(&sm.full_x[s], (uint32_t)(kb_last / X_STAGES) & 1u) &&
+             globaltimer_ns() - t0 < kWaitLimitNs) {
+      }
+    }
+  }
   if (warp == 9) {
     if (sm.abort_flag && lane == 0) {
       const uint64_t t0 = globaltimer_ns();
@@ -371,12 +384,9 @@ cudaError_t launch_m(const CUtensorMap& tmX, const CUtensorMap& tmW, int I, int6
                 : launch_g<M1, NC, false>(tmX, tmW, I, L, J, K, pl, part, gen, st, stream);
 }
 
-// Chunks per stage for a view: 4 (64 j x 128 rows) for short modes, else 1.
-int chunks_for(const View& x) {
-  if (x.I > 128) return 1;
-  if (x.L == 1) return 4;
-  return (x.L % (BJ * 4) == 0) ? 4 : 1;             // a 64-j stage must not cross r
-}
+// Chunks per stage for a view: 4 (64 j x 128 rows, one tile) for short modes,
+// else 2 (32 j x 256 rows, two tiles).
+int chunks_for(const View& x) { return x.I > 128 ? 2 : 4; }
 
 }  // namespace
 
@@ -392,7 +402,7 @@ bool tc_sketch_supported(const View& x, const WView& w, int K) {
 
 static TcSketchPlan plan_nc(int64_t I, int64_t J, int nc) {
   TcSketchPlan pl;
-  const int rows = 512 / nc, sbj = BJ * nc;
+  const int rows = 512 / nc, sbj = BJ * nc;          // 256 rows for nc = 2, 128 for nc = 4
   pl.mgroups = (int)((I + rows - 1) / rows);
   const int64_t nblk = (J + sbj - 1) / sbj;            // stage-sized blocks of j, dealt round-robin
   pl.splits = (int)std::min<int64_t>(std::max<int64_t>(1, device_sms() / pl.mgroups), nblk);
@@ -403,7 +413,7 @@ static TcSketchPlan plan_nc(int64_t I, int64_t J, int nc) {
 TcSketchPlan plan_tc_sketch(int64_t I, int K, int64_t J) {
   (void)K;
   // the larger of the two possible split counts sizes the partial sums
-  const TcSketchPlan a = plan_nc(I, J, 1), b = plan_nc(I, J, 4);
+  const TcSketchPlan a = plan_nc(I, J, 2), b = plan_nc(I, J, 4);
   return (a.splits * a.mgroups >= b.splits * b.mgroups) ? a : b;
 }
 
@@ -421,20 +431,20 @@ static cudaError_t tc_sketch_impl(const View& x, const WView& w, int K, float* Y
     if (!make_tmap_f32(&tmW, w.p, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B)) return cudaErrorNotSupported;
   }
   cudaError_t e;
-  const uint32_t boxw = nc == 1 ? 256u : 128u;
+  const uint32_t boxw = nc == 2 ? 256u : 128u;          // rows per CTA (one TMA box)
   if (x.L == 1) {
     const uint64_t dims[2] = {(uint64_t)I, (uint64_t)J};
     const uint64_t strides[1] = {(uint64_t)I};
     const uint32_t box[2] = {boxw, (uint32_t)(BJ * nc)};
     if (!make_tmap_f32(&tmX, x.p, 2, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_NONE)) return cudaErrorNotSupported;
-    e = nc == 1 ? launch_m<true, 1>(tmX, tmW, (int)I, 1, J, K, pl, part, gen, st, stream)
+    e = nc == 2 ? launch_m<true, 2>(tmX, tmW, (int)I, 1, J, K, pl, part, gen, st, stream)
                 : launch_m<true, 4>(tmX, tmW, (int)I, 1, J, K, pl, part, gen, st, stream);
   } else {
     const uint64_t dims[3] = {(uint64_t)x.L, (uint64_t)I, (uint64_t)x.Rt};
     const uint64_t strides[2] = {(uint64_t)x.s_i, x.Rt > 1 ? (uint64_t)x.s_r : (uint64_t)x.s_i * (uint64_t)I};
     const uint32_t box[3] = {BJ, boxw, 1};
     if (!make_tmap_f32(&tmX, x.p, 3, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_64B)) return cudaErrorNotSupported;
-    e = nc == 1 ? launch_m<false, 1>(tmX, tmW, (int)I, x.L, J, K, pl, part, gen, st, stream)
+    e = nc == 2 ? launch_m<false, 2>(tmX, tmW, (int)I, x.L, J, K, pl, part, gen, st, stream)
                 : launch_m<false, 4>(tmX, tmW, (int)I, x.L, J, K, pl, part, gen, st, stream);
   }
   if (e != cudaSuccess) return e;
@@ -458,7 +468,7 @@ cudaError_t launch_tc_sketch(const View& x, const WView& w, int K, float* Y, int
 bool tc_sketch_seeded_supported(const View& x, int K) {
   const int64_t J = x.L * x.Rt;
   if (!tc_sketch_supported(x, WView{nullptr, x.L, J}, K)) return false;
-  return chunks_for(x) == 1 || x.s_i >= (int64_t(1) << 20);
+  return chunks_for(x) == 2 || x.s_i >= (int64_t(1) << 20);
 }
 
 cudaError_t launch_tc_sketch_seeded(const View& x, int K, uint64_t seed, uint32_t stream_id, float* Y, int64_t ldy,
