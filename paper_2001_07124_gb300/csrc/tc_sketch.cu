@@ -457,18 +457,18 @@ cudaError_t launch_tc_sketch(const View& x, const WView& w, int K, float* Y, int
 }
 
 // Where the test matrix is generated in-kernel: the transform warps evaluate the
-// generator for every stage, which costs about one generator call per thread
-// and stage with 512-row stages but four with 128-row stages (64 j per stage),
-// where it becomes the slowest step of the pipeline (measured on 128^4: 450 us
-// per mode against 125 + 240 us for drawing Omega first and sketching from
-// memory).  Short modes therefore generate in-kernel only when the stream of X
-// is itself slow: rows of X_(n) 4 MB or more apart (the last mode of a large
-// tensor), where the TMA copies, not the generator, set the pace (460 us
-// against 125 + 560 us).
+// generator for every stage, and with two row groups per j block (or 64-j
+// stages for short modes) each W tile is generated more than once per SM's
+// worth of X.  Measured on GB300 with the stacked-operand kernel: 512^3 mode 1,
+// 174 us generated in-kernel against 28 + 105 us for drawing Omega first and
+// sketching from memory; 128^4 mode 1, 335 against 126 + 194 us.  Omega is
+// therefore drawn first, except where the stream of X is itself slow: rows of
+// X_(n) 4 MB or more apart (the last mode of a large tensor), where the TMA
+// copies, not the generator, set the pace.
 bool tc_sketch_seeded_supported(const View& x, int K) {
   const int64_t J = x.L * x.Rt;
   if (!tc_sketch_supported(x, WView{nullptr, x.L, J}, K)) return false;
-  return chunks_for(x) == 2 || x.s_i >= (int64_t(1) << 20);
+  return x.s_i >= (int64_t(1) << 20);
 }
 
 cudaError_t launch_tc_sketch_seeded(const View& x, int K, uint64_t seed, uint32_t stream_id, float* Y, int64_t ldy,

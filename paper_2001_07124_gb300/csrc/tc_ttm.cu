@@ -26,10 +26,10 @@
 //   * warps 0-7 (two transform warpgroups, alternating stages): split X into
 //     TF32 hi/lo and store it in tensor memory as the A operand (thread = row j
 //     = TMEM lane), split M into hi/lo B tiles in the canonical K-major layout;
-//   * warp 13 (one thread): per stage, four K steps of the three MMAs
-//     A_hi*B_hi + A_hi*B_lo + A_lo*B_hi into an FP32 TMEM accumulator; every
-//     SEG stages of a tile form a segment with its own accumulator buffer (four
-//     buffers in turn), committed when the segment's last stage is issued;
+//   * warp 13 (one thread): per stage, four K steps of two MMAs (the stacked
+//     3xTF32 form below) into an FP32 TMEM accumulator; every SEG stages of a
+//     tile form a segment with its own accumulator buffer (buffers in turn),
+//     committed when the segment's last stage is issued;
 //   * warps 8-11 (epilogue): read each finished segment (tcgen05.ld), add it
 //     into FP32 registers, hand the buffer back, and write the rows of Out
 //     once the tile's last segment is in.
@@ -57,10 +57,9 @@ constexpr int NUM_EPI = 128;              // warps 8-11
 constexpr int PRODUCER_WARP = 12, MMA_WARP = 13;
 constexpr int NUM_THREADS = NUM_XFORM + NUM_EPI + 64;   // + the producer and MMA warps
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int D_COLS = 64;                // per accumulator buffer
-constexpr int NBUF = 4;                   // accumulator buffers, cycled per segment
-constexpr int A_COL0 = NBUF * D_COLS;     // A stages after the accumulators
 constexpr int A_STAGE_COLS = 2 * BI;      // 32 hi + 32 lo columns
+constexpr int A_COL0 = 0;                 // A stages first, then the accumulator buffers
+constexpr int D_COL0 = A_STAGES * A_STAGE_COLS;
 // The tensor core rounds its FP32 accumulation toward zero, so a long
 // accumulation in tensor memory drifts toward zero by about half an ulp per
 // MMA (measured -1e-5 relative over a 512^3 sketch).  Each output tile is
@@ -68,6 +67,19 @@ constexpr int A_STAGE_COLS = 2 * BI;      // 32 hi + 32 lo columns
 // (SEG * 4 K steps, 3 MMAs each); the epilogue adds the segments in FP32
 // registers with round-to-nearest, in segment order (deterministic).
 constexpr int SEG = 2;
+
+// Products in 3xTF32: X_hi M_hi + X_hi M_lo + X_lo M_hi.  The B operand of a
+// stage is the stacked [M_hi; M_lo] (N = 2 NPAD rows), so each K step takes two
+// MMAs, D[:, 0:2NPAD) += X_hi [M_hi M_lo] and D[:, 0:NPAD) += X_lo M_hi, and
+// the product is D[:, 0:NPAD) + D[:, NPAD:2NPAD).  An accumulator buffer holds
+// both halves; as many buffers as tensor memory allows (at most four) cycle
+// over the segments.
+template <int NPAD>
+struct TtmAcc {
+  static constexpr int D_COLS = 2 * NPAD;
+  static constexpr int FIT = (512 - D_COL0) / D_COLS;
+  static constexpr int NBUF = FIT < 4 ? FIT : 4;
+};
 
 // The M and B tiles hold NPAD rows (K padded to 16), and the X ring is as deep
 // as 227 KB allows.  The pace is set by the MMA stream (12 skinny MMAs per
@@ -87,7 +99,7 @@ struct __align__(1024) TtmSmem {
   float ostage[4][32 * 17];                // per epilogue warp: 32 rows x 16 columns (+1 pad)
   uint64_t full_x[X_STAGES], empty_x[X_STAGES];
   uint64_t full_a[A_STAGES], empty_a[A_STAGES];
-  uint64_t d_full[NBUF], d_empty[NBUF];
+  uint64_t d_full[TtmAcc<NPAD>::NBUF], d_empty[TtmAcc<NPAD>::NBUF];
   uint64_t drain;                          // arrives when every MMA this CTA issued has completed
   uint32_t tmem_base;
   int abort_flag;
@@ -106,6 +118,7 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   if (skip != nullptr && skip->orth_fail) return;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   constexpr int X_STAGES = TtmGeo<NPAD>::X_STAGES, M_TILE = TtmGeo<NPAD>::M_TILE;
+  constexpr int NBUF = TtmAcc<NPAD>::NBUF, D_COLS = TtmAcc<NPAD>::D_COLS;
   TtmSmem<NPAD>& sm = *reinterpret_cast<TtmSmem<NPAD>*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -119,7 +132,7 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
   const uint32_t xbytes = (uint32_t)((M1 ? TILE_J : bl * tr) * BI * 4);
   const int nst = (I + BI - 1) / BI;                  // stages per tile
   const int nseg = (nst + SEG - 1) / SEG;             // accumulation segments per tile
-  constexpr uint32_t idesc = idesc_tf32(128, NPAD);
+  constexpr uint32_t idesc2 = idesc_tf32(128, 2 * NPAD), idesc1 = idesc_tf32(128, NPAD);
 
   if (tid == 0) {
     for (int s = 0; s < X_STAGES; ++s) {
@@ -190,16 +203,14 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         const int a = g % A_STAGES;
         if (!mbar_wait(&sm.full_a[a], (uint32_t)(g / A_STAGES) & 1u, abort_flag)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(buf * D_COLS);
+        const uint32_t d = tmem + (uint32_t)(D_COL0 + buf * D_COLS);
         const uint32_t ahi = tmem + (uint32_t)(A_COL0 + a * A_STAGE_COLS);
-        const uint32_t bhi = smem_u32(sm.b[a][0]), blo = smem_u32(sm.b[a][1]);
+        const uint32_t bhl = smem_u32(sm.b[a][0]);   // the lo tile follows: rows NPAD.. of the stacked operand
 #pragma unroll
         for (int ks = 0; ks < BI / 8; ++ks) {
-          const uint64_t dbh = smem_desc_kmajor_nosw(bhi + ks * 256, 128, 1024);
-          const uint64_t dbl = smem_desc_kmajor_nosw(blo + ks * 256, 128, 1024);
-          mma_tf32_ts(d, ahi + ks * 8, dbh, idesc, (!seg_first || ks > 0) ? 1u : 0u);
-          mma_tf32_ts(d, ahi + ks * 8, dbl, idesc, 1u);
-          mma_tf32_ts(d, ahi + BI + ks * 8, dbh, idesc, 1u);
+          const uint64_t db = smem_desc_kmajor_nosw(bhl + ks * 256, 128, 1024);
+          mma_tf32_ts(d, ahi + ks * 8, db, idesc2, (!seg_first || ks > 0) ? 1u : 0u);
+          mma_tf32_ts(d, ahi + BI + ks * 8, db, idesc1, 1u);
         }
         mma_commit(&sm.empty_a[a]);
         if (seg_last) mma_commit(&sm.d_full[buf]);
@@ -282,11 +293,13 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
         tc_fence_after();
 #pragma unroll
         for (int c0 = 0; c0 < NPAD / 16; ++c0) {
-          uint32_t v[16];
-          tmem_ld_x16(tmem + lane_base + (uint32_t)(buf * D_COLS + 16 * c0), v);
+          uint32_t vh[16], vl[16];
+          const uint32_t dcol = tmem + lane_base + (uint32_t)(D_COL0 + buf * D_COLS + 16 * c0);
+          tmem_ld_x16(dcol, vh);
+          tmem_ld_x16(dcol + NPAD, vl);
           tmem_wait_ld();
 #pragma unroll
-          for (int c = 0; c < 16; ++c) acc[16 * c0 + c] += __uint_as_float(v[c]);
+          for (int c = 0; c < 16; ++c) acc[16 * c0 + c] += __uint_as_float(vh[c]) + __uint_as_float(vl[c]);
         }
         tc_fence_before();
         mbar_arrive(&sm.d_empty[buf]);

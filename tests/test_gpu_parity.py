@@ -163,11 +163,13 @@ def test_tc_sketch_strided_parity(dims, mode, K):
 
 @pytest.mark.parametrize("dims,mode,K", [((512, 64, 64), 0, 42), ((128, 36, 111), 0, 7), ((32, 512, 40), 1, 42),
                                          ((16, 8, 40, 12), 2, 20), ((100, 48, 50), 0, 33),
-                                         # short last mode with rows 4 MB apart: 64-j stages generate in-kernel
-                                         ((1024, 1024, 6), 2, 26)])
+                                         # last modes with rows 4 MB apart generate Omega in-kernel
+                                         ((1024, 1024, 6), 2, 26), ((4, 262144, 136), 2, 42)])
 def test_seeded_sketch_generates_omega_in_kernel(dims, mode, K):
-    """With no explicit Omega the tensor-core sketch draws the test matrix inside
-    the kernel; it equals, bit for bit, the sketch with the materialised matrix."""
+    """With no explicit Omega the sketch uses the seeded test matrix: generated
+    inside the tensor-core kernel where the rows of X_(n) lie 4 MB or more apart,
+    drawn into memory first elsewhere.  Either way it equals, bit for bit, the
+    sketch with the materialised matrix."""
     X = dev(random_tensor(dims, 27))
     J = int(np.prod(dims)) // dims[mode]
     om = R().rhosvd_omega(91, mode, J, K).t().contiguous().reshape(-1)
