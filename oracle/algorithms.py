@@ -116,6 +116,36 @@ def hooi(x: np.ndarray, ranks: Sequence[int], sweeps: int = 20):
     return g, us
 
 
+def rp_hooi_sweep(x: np.ndarray, us: Sequence[np.ndarray], ranks: Sequence[int],
+                  omegas: Sequence[np.ndarray]):
+    """One sweep of Algorithm 7 (RP-HOOI), in its order: for each n in turn,
+    S = X x_{p != n} Q^(p)T with the latest factors, and Q^(n) from a random
+    projection of S_(n).  The factor step is Algorithm 1 with q = 0: the sketch
+    S_(n) Omega^(n) with K_n = min(R_n + p, I_n, J_n) columns, its orthonormal
+    basis, and the truncation to R_n through the SVD of the projected matrix
+    (the oversampling reading taken for Alg. 6 as well).  omegas[n] is
+    J_n x K_n with J_n = prod_{p != n} R_p.  The core is the last S times
+    Q^(N)T, i.e. X x_1 Q^(1)T ... x_N Q^(N)T with the new factors.
+    Used as the refinement sweep after a single-pass or reduced-precision run."""
+    x = np.asarray(x, dtype=np.float64)
+    us = [np.asarray(u, dtype=np.float64) for u in us]
+    s = x
+    for n in range(x.ndim):
+        mats = [None if k == n else us[k].T for k in range(x.ndim)]
+        s = multi_ttm(x, mats)
+        us[n] = brsvd(unfold(s, n), ranks[n], 0, omegas[n])[0]
+    return ttm(s, us[-1].T, x.ndim - 1), us
+
+
+def rp_hooi_omega_shapes(dims: Sequence[int], ranks: Sequence[int], p: int):
+    """Sizes (J_n, K_n) of the test matrices of one RP-HOOI sweep: J_n = prod_{k != n} R_k."""
+    shapes = []
+    for n in range(len(dims)):
+        j_n = int(np.prod([int(ranks[k]) for k in range(len(dims)) if k != n], dtype=np.int64))
+        shapes.append((j_n, sketch_width(int(ranks[n]), p, int(dims[n]), j_n)))
+    return shapes
+
+
 def rhosvd(x: np.ndarray, ranks: Sequence[int], q: int, omegas: Sequence[np.ndarray]):
     """Algorithm 6 (RP-HOSVD) with each factor from Algorithm 1 on the original X:
     Q^(n) from X_(n) Omega^(n) (J_n = prod_{k != n} I_k rows), then

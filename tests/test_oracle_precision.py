@@ -28,13 +28,8 @@ import pytest
 from oracle import algorithms as A
 from oracle import metrics as M
 from oracle import tensor as T
+from oracle.precision import bf16_round, e4m3_round
 from workloads import WORKLOADS, gaussian_matrix
-
-
-def bf16_round(a):
-    """Round to the nearest BF16 value (ties to even), returned in FP64."""
-    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32)
-    return ((u + (((u >> 16) & 1) + 0x7FFF)) & 0xFFFF0000).view(np.float32).astype(np.float64)
 
 
 def test_bf16_round_is_correct():
@@ -327,16 +322,6 @@ def test_round_toward_zero_accumulation_reproduces_the_excess():
     print(f"E {e / e0 - 1:+.3%} over exact, core scale - 1 {scale:+.2e}")
     assert 0.01 < e / e0 - 1 < 0.04
     assert -3e-5 < scale < -5e-6
-
-
-def e4m3_round(a):
-    """Round to FP8 e4m3 (bias 7, 3 mantissa bits, largest 448, subnormal spacing
-    2^-9), ties to even, saturating at 448."""
-    a = np.asarray(a, dtype=np.float64)
-    m = np.minimum(np.abs(a), 448.0)
-    e = np.maximum(np.floor(np.log2(np.maximum(m, 2.0 ** -9))), -6.0)
-    step = 2.0 ** (e - 3)
-    return np.sign(a) * np.minimum(np.round(m / step) * step, 448.0)
 
 
 def test_e4m3_round_is_correct():
