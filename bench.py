@@ -83,14 +83,16 @@ def _l2_note(w) -> str:
     return f"input {mib:.1f} MiB fits in L2 (not flushed)"
 
 
-def metric_name(w) -> str:
+def metric_name(w, dtype="f32", refine=0) -> str:
     """Metric label of a workload, e.g. decomps/s (R-STHOSVD 512^3 FP32, rank 32, p=10, q=1)."""
     d = w.dims
     shape = f"{d[0]}^{len(d)}" if len(set(d)) == 1 else "x".join(str(v) for v in d)
     r = w.ranks
     rank = str(r[0]) if len(set(r)) == 1 else "(" + ",".join(str(v) for v in r) + ")"
     par = f"K={w.K[0]}, S={w.S[0]}" if w.algo == "rpet" and w.K else f"p={w.p}, q={w.q}"
-    return f"decomps/s ({_ALGO_NAMES[w.algo]} {shape} FP32, rank {rank}, {par})"
+    extra = "" if dtype == "f32" else f", {dtype.upper()} sketch passes"
+    extra += f", {refine} RP-HOOI sweep" + ("s" if refine > 1 else "") if refine else ""
+    return f"decomps/s ({_ALGO_NAMES[w.algo]} {shape} FP32, rank {rank}, {par}{extra})"
 UNIT = "decomps/s"
 
 
@@ -200,21 +202,29 @@ def accuracy_report(x32, g_gpu, u_gpu, g_or, u_or, tol=1e-5, max_sine=1e-4) -> d
             "E_transpose_core": M.rel_error(x32, g_t, u_gpu)}
 
 
-def oracle_decompose(w, x32):
-    """Time one oracle decomposition (FP64 NumPy) with the generator's own test matrices."""
+def oracle_decompose(w, x32, dtype="f32", refine=0):
+    """Time one oracle decomposition (FP64 NumPy) with the generator's own test
+    matrices (rounded to the format of a reduced-precision run, as the device
+    rounds its own) and the same number of RP-HOOI sweeps."""
     from oracle import algorithms as A
     from oracle import philox
+    from oracle.precision import round_to
     shapes = A.omega_shapes(w.algo, w.dims, w.ranks, w.p, K=w.K, S=w.S)
+    N = len(w.dims)
+    rnd = (lambda a: round_to(a, dtype)) if (dtype != "f32" and w.algo == "rpet") else (lambda a: a)
     t0 = time.perf_counter()
     if w.algo == "rpet":
         fs, ts = shapes
-        N = len(w.dims)
-        om = [philox.omega(w.omega_seed, n, r, c).astype(np.float64) for n, (r, c) in enumerate(fs)]
-        ot = [philox.omega(w.omega_seed, N + n, r, c).astype(np.float64) for n, (r, c) in enumerate(ts)]
+        om = [rnd(philox.omega(w.omega_seed, n, r, c).astype(np.float64)) for n, (r, c) in enumerate(fs)]
+        ot = [rnd(philox.omega(w.omega_seed, N + n, r, c).astype(np.float64)) for n, (r, c) in enumerate(ts)]
         g, u, _ = A.rpet(x32, w.ranks, om, ot)
     else:
         om = [philox.omega(w.omega_seed, n, r, c).astype(np.float64) for n, (r, c) in enumerate(shapes)]
         g, u = getattr(A, w.algo)(x32, w.ranks, w.q, om)
+    for t in range(refine):
+        ref = [philox.omega(w.omega_seed, 2 * N + t * N + n, j, k).astype(np.float64)
+               for n, (j, k) in enumerate(A.rp_hooi_omega_shapes(w.dims, w.ranks, w.p))]
+        g, u = A.rp_hooi_sweep(x32, u, w.ranks, ref)
     return time.perf_counter() - t0, g, u
 
 
@@ -424,6 +434,9 @@ def main():
     ap.add_argument("--serve", type=int, default=0, metavar="N", help="serving run with N requests")
     ap.add_argument("--serve-rate", type=float, default=200.0, metavar="R", help="Poisson arrival rate (req/s)")
     ap.add_argument("--batch", type=int, default=0, metavar="N", help="batched run with N small tensors")
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "e4m3"],
+                    help="arithmetic of the sketch passes (reduced-precision copy of X)")
+    ap.add_argument("--refine", type=int, default=0, help="RP-HOOI sweeps after the decomposition")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -463,8 +476,9 @@ def main():
     del x
     X = x_host.cuda()
     dims, ranks = w.dims, w.ranks
-    kw = dict(algo=w.algo, p=w.p, q=w.q, seed=w.omega_seed, K=w.K, S=w.S)
-    ws = R.Workspace(R.rhosvd_workspace_size(dims, ranks, w.algo, w.p, w.q, K=w.K, S=w.S))
+    kw = dict(algo=w.algo, p=w.p, q=w.q, seed=w.omega_seed, K=w.K, S=w.S, dtype=args.dtype, refine=args.refine)
+    ws = R.Workspace(R.rhosvd_workspace_size(dims, ranks, w.algo, w.p, w.q, K=w.K, S=w.S, dtype=args.dtype,
+                                             refine=args.refine))
     G = R.empty_colmajor(ranks)
     Us = [R.empty_colmajor((dims[n], ranks[n])) for n in range(len(dims))]
     out = (G, Us)
@@ -601,19 +615,32 @@ def main():
     cpu = None
     accuracy = None
     if rank == 0 and x32 is not None:
-        t_or, g_or, u_or = oracle_decompose(w, x32)
+        t_or, g_or, u_or = oracle_decompose(w, x32, args.dtype, args.refine)
         g_gpu = R.fortran_view(G, ranks).cpu().numpy().astype(np.float64)
         u_gpu = [R.matrix(u, dims[n], ranks[n]).cpu().numpy().astype(np.float64) for n, u in enumerate(Us)]
-        accuracy = accuracy_report(x32, g_gpu, u_gpu, g_or, u_or)
+        if args.dtype == "f32" and args.refine == 0:
+            accuracy = accuracy_report(x32, g_gpu, u_gpu, g_or, u_or)
+        elif args.dtype == "f32":
+            # after a randomized refinement sweep the subspaces are fixed by the data only to
+            # about the spread between test-matrix draws, so the gate is the reconstruction
+            accuracy = accuracy_report(x32, g_gpu, u_gpu, g_or, u_or, max_sine=1.0)
+            accuracy["tolerance"] = "FP32 path after refinement: |dE| <= 1e-5 (sines reported, not gated)"
+        else:
+            # reduced-precision tolerance: |dE| <= 2% of E_oracle and <= 1e-3 (subspaces not gated)
+            accuracy = accuracy_report(x32, g_gpu, u_gpu, g_or, u_or, tol=1.0, max_sine=1.0)
+            d = abs(accuracy["E_gpu"] - accuracy["E_oracle"])
+            accuracy["pass"] = bool(d <= 0.02 * accuracy["E_oracle"] and d <= 1e-3)
+            accuracy["tolerance"] = "reduced precision: |dE| <= 2% E_oracle and <= 1e-3"
         cpu = {"value": 1.0 / t_or, "unit": UNIT, "cores": _CORES, "kind": "oracle",
                "sample": f"one full decomposition of the {w.name} workload in FP64 NumPy (seeded Philox test matrices)"}
 
-    launches = R.rhosvd_launch_count(dims, ranks, w.algo, w.p, w.q, K=w.K, S=w.S)
+    launches = R.rhosvd_launch_count(dims, ranks, w.algo, w.p, w.q, K=w.K, S=w.S, dtype=args.dtype,
+                                     refine=args.refine)
     if rank == 0:
         line = {
-            "metric": metric_name(w), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "metric": metric_name(w, args.dtype, args.refine), "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
             "data": "synthetic (seeded low-rank tensor, device-drawn Philox test matrices)",
             "config": {"workload": w.name, "dims": list(dims), "ranks": list(ranks), "algo": w.algo, "p": w.p,
                        "q": w.q, "parallelism": f"replicas{world}", "l2_flush": _l2_note(w),

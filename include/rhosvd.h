@@ -65,6 +65,22 @@ typedef enum rhosvd_algo {
   RHOSVD_ALGO_RPET = 2        /* R-PET, Alg. 9 (single pass over X) */
 } rhosvd_algo;
 
+/* Arithmetic of the sketch passes (the paper leaves it open).  RHOSVD_F32:
+ * FP32 data, products in 3xTF32 with FP32 accumulation.  RHOSVD_BF16 and
+ * RHOSVD_E4M3: the call first makes a reduced-precision copy of X (BF16, or
+ * FP8 e4m3 with one power-of-two scale per frontal slice of the last mode,
+ * chosen so that the slice's largest magnitude maps to at most 448), and the
+ * passes listed under rhosvd_opts.dtype read that copy with BF16 (.kind::f16)
+ * or e4m3 (.kind::f8f6f4) tensor-core MMAs and FP32 accumulation. */
+typedef enum rhosvd_dtype {
+  RHOSVD_F32 = 0,
+  RHOSVD_BF16 = 1,
+  RHOSVD_E4M3 = 2
+} rhosvd_dtype;
+
+/* bits of rhosvd_opts.flags */
+#define RHOSVD_OPT_KRONECKER 1    /* R-PET with Kronecker-structured factor sketches (two reads of X) */
+
 /* device status flags (bit set in the `flags` output of rhosvd_device_status) */
 #define RHOSVD_FLAG_FALLBACK 1    /* a Householder fallback ran in some orthonormalisation */
 
@@ -77,10 +93,33 @@ typedef struct rhosvd_opts {
   int32_t algo;                       /* rhosvd_algo */
   int32_t p;                          /* oversampling p >= 0 (Remark 1) */
   int32_t q;                          /* power iterations q >= 0 (Remark 1) */
-  int32_t flags;                      /* reserved, 0 */
+  int32_t flags;                      /* RHOSVD_OPT_* bits, else 0.  RHOSVD_OPT_KRONECKER
+                                         (R-PET only): the factor sketch of mode n is
+                                         Y_n = (X x_{p != n} Phi_p^T)_(n), i.e. X_(n) times the
+                                         Kronecker product of Gaussian matrices Phi_p (I_p x k)
+                                         (the memory-efficient test matrices of Sec. 5.1), with
+                                         k the smallest width such that k^(N-1) >= max K_n;
+                                         every K_n becomes k^(N-1).  Phi_p is drawn on stream_id
+                                         10N + p, or taken from Omega[p] (I_p x k, ld I_p).  All
+                                         sketches then come from two reads of X: one product
+                                         over the last mode with [Omega~_N^T Phi_N] and one over
+                                         the first with Phi_1. */
   uint64_t seed;                      /* seed of the Gaussian test matrices */
   int32_t K[RHOSVD_MAX_MODES];        /* R-PET factor sketch widths, 0 => R_n + p */
   int32_t S[RHOSVD_MAX_MODES];        /* R-PET core sketch widths, 0 => 2 K_n + 1 */
+  int32_t dtype;                      /* rhosvd_dtype of the sketch passes: for R-PET the
+                                         single pass (every factor sketch and the first
+                                         core-sketch product), for RP-HOSVD and R-STHOSVD
+                                         the power-iteration products of mode 1; test
+                                         matrices drawn from the seed are rounded to the
+                                         format.  Passes whose layout the reduced-precision
+                                         kernels do not take run in FP32. */
+  int32_t refine_iters;               /* sweeps of RP-HOOI (Alg. 7) on the FP32 X after the
+                                         decomposition, 0..8: for each mode in turn,
+                                         S = X x_{p != n} U_p^T and U_n from Alg. 1 (q = 0,
+                                         oversampling p) on S_(n); test matrices of sweep t,
+                                         mode n from the seed on stream_id 2N + tN + n; the
+                                         core is X x_1 U_1^T ... x_N U_N^T. */
 } rhosvd_opts;
 
 /* ---------------------------------------------------------------- sizing */

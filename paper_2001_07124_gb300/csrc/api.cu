@@ -179,6 +179,79 @@ void op_sketch_seeded(Ctx& c, const View& x, int K, uint64_t seed, uint32_t stre
   op_sketch(c, x, WView{Om, x.L, J}, K, Y, ldy);
 }
 
+// ------------------------------------------------------------------ reduced-precision copy of X
+
+// X_q (BF16 or e4m3) with one scale per frontal slice of the last mode (e4m3).
+struct LpCopy {
+  int eb = 0;                   // bytes per element: 2 BF16, 1 e4m3; 0 = no copy
+  const void* xq = nullptr;
+  const float* scale = nullptr; // e4m3 only
+  int64_t slice_len = 0;        // elements of one frontal slice
+  int64_t nslices = 0;          // I_N
+};
+
+int eb_of(int dtype) { return dtype == RHOSVD_BF16 ? 2 : dtype == RHOSVD_E4M3 ? 1 : 0; }
+
+// Quantise X into a copy carved from the workspace (left taken until the end of the call).
+LpCopy lp_make(Ctx& c, const float* X, const Geom& g, int dtype) {
+  LpCopy lp;
+  lp.eb = eb_of(dtype);
+  if (lp.eb == 0 || g.N < 2) {
+    lp.eb = 0;
+    return lp;
+  }
+  const int64_t n = g.numel();
+  lp.nslices = g.d[g.N - 1];
+  lp.slice_len = n / lp.nslices;
+  unsigned char* xq = c.take<unsigned char>((size_t)n * lp.eb);
+  float* sc = lp.eb == 1 ? c.take<float>((size_t)lp.nslices) : nullptr;
+  unsigned int* amax = lp.eb == 1 ? c.take<unsigned int>((size_t)lp.nslices) : nullptr;
+  lp.xq = xq;
+  lp.scale = sc;
+  c.launches += lp.eb == 1 ? 3 : 1;
+  if (!c.dry) c.check(launch_quantize(X, n, lp.slice_len, lp.eb, xq, sc, amax, c.s));
+  return lp;
+}
+
+// Elements of the mode-n unfolding's columns per frontal slice of the last mode.
+int64_t lp_col_slice(const LpCopy& lp, const Geom& g, int n) { return g.J(n) / lp.nslices; }
+
+// Y = X_q,(n) W on the tensor cores if the layout allows; false leaves the pass to FP32.
+bool lp_sketch(Ctx& c, const LpCopy& lp, const Geom& g, int n, const float* W, int K, float* Y) {
+  if (lp.eb == 0) return false;
+  const View xv = mode_view(nullptr, g, n);
+  const bool last = n == g.N - 1;
+  const int mode = lp.scale == nullptr ? 0 : (last ? 2 : 1);
+  const int64_t sl = last ? 0 : lp_col_slice(lp, g, n);
+  if (!tc_sketch_lp_supported(xv, lp.eb, K, mode, sl)) return false;
+  Scope sc(c);
+  float* part = c.take<float>(sketch_lp_scratch_floats(xv.I, K, g.J(n), lp.eb));
+  c.launches += 2;
+  if (!c.dry)
+    c.check(launch_tc_sketch_lp(xv, lp.xq, lp.eb, W, K, Y, g.d[n], lp.scale, mode, sl, part, c.st, c.s));
+  return true;
+}
+
+// Out(j, k) = (X_q,(1)^T M)(j, k) on the tensor cores; false leaves it to FP32.
+bool lp_ttm1(Ctx& c, const LpCopy& lp, const Geom& g, const float* M, int64_t ldm, int K, float* out,
+             int64_t o_k, int64_t o_r) {
+  if (lp.eb == 0 || !tc_ttm_lp_supported(g.d[0], g.J(0), lp.eb, K, ldm)) return false;
+  c.launches += 1;
+  if (!c.dry)
+    c.check(launch_tc_ttm_lp(lp.xq, lp.eb, g.d[0], g.J(0), M, ldm, K, out, o_k, o_r, lp.scale,
+                             lp_col_slice(lp, g, 0), c.st, c.s));
+  return true;
+}
+
+// The seeded test matrix of (seed, stream_id), rounded to the copy's format.
+void lp_omega(Ctx& c, const LpCopy& lp, uint64_t seed, uint32_t stream_id, int64_t rows, int cols, float* out) {
+  c.launches += 2;
+  if (!c.dry) {
+    c.check(launch_omega(seed, stream_id, rows, cols, out, rows, c.s));
+    c.check(launch_round_to_format(out, rows * (int64_t)cols, lp.eb, c.s));
+  }
+}
+
 // ------------------------------------------------------------------ Alg. 1 on one mode
 
 struct ModeResult {
@@ -191,20 +264,27 @@ struct ModeResult {
 // sketch, orth, q power iterations, projection B, truncation of B B^T.
 // Buffers Yb (I x K), Zb (J x K), Om (J x K, unless explicit) and Ub (K x R, ld ldu_of(K))
 // belong to the caller.
+// The test matrix is seeded on stream_id stream_base + n.  With lp (mode 1 of
+// the original X only) the power-iteration products read the reduced-precision
+// copy where its kernels take the layout.
 void alg1_mode(Ctx& c, const float* x, const Geom& g, int n, int K, int R, int q, uint64_t seed,
-               const float* omega_explicit, float* Yb, float* Zb, float* Om, float* Ub) {
+               const float* omega_explicit, float* Yb, float* Zb, float* Om, float* Ub, uint32_t stream_base = 0,
+               const LpCopy* lp = nullptr) {
   const View xv = mode_view(x, g, n);
   const int64_t I = g.d[n], L = g.L(n), J = g.J(n);
   if (omega_explicit != nullptr)
     op_sketch(c, xv, WView{omega_explicit, L, J}, K, Yb, I);   // Y = X_(n) Omega
   else
-    op_sketch_seeded(c, xv, K, seed, (uint32_t)n, Yb, I, Om);
+    op_sketch_seeded(c, xv, K, seed, stream_base + (uint32_t)n, Yb, I, Om);
   op_orth(c, Yb, I, K, I, q > 0 ? 1 : 2);               // Q = orth(Y)
   const OView zo{Zb, J, L};                              // Z(j,k) at j + k*J
+  const bool use_lp = lp != nullptr && lp->eb != 0 && n == 0;
   for (int it = 0; it < q; ++it) {
-    op_ttm(c, xv, Yb, 1, I, K, zo);                      // Z = X_(n)^T Q
+    if (!(use_lp && lp_ttm1(c, *lp, g, Yb, I, K, Zb, J, 1)))
+      op_ttm(c, xv, Yb, 1, I, K, zo);                    // Z = X_(n)^T Q
     op_orth(c, Zb, J, K, J, 1);                          // Z = orth(Z)
-    op_sketch(c, xv, WView{Zb, L, J}, K, Yb, I);         // Y = X_(n) Z
+    if (!(use_lp && lp_sketch(c, *lp, g, n, Zb, K, Yb)))
+      op_sketch(c, xv, WView{Zb, L, J}, K, Yb, I);       // Y = X_(n) Z
     op_orth(c, Yb, I, K, I, it + 1 < q ? 1 : 2);         // Q = orth(Y)
   }
   op_ttm(c, xv, Yb, 1, I, K, zo);                        // B^T = X_(n)^T Q
@@ -237,6 +317,10 @@ struct Plan {
   int K[RHOSVD_MAX_MODES];
   int S[RHOSVD_MAX_MODES];
   int64_t J[RHOSVD_MAX_MODES];
+  int kron = 0;             // R-PET with Kronecker-structured factor sketches: width k of each Phi_p
+  int dtype = RHOSVD_F32;   // arithmetic of the sketch passes
+  int refine = 0;           // RP-HOOI sweeps after the decomposition
+  int p = 0;                // oversampling (also of the refinement's sketches)
 };
 
 rhosvd_status validate_shape(const rhosvd_shape* sh, Geom& g) {
@@ -256,6 +340,11 @@ rhosvd_status make_plan(const Geom& g, const int32_t* ranks, const rhosvd_opts* 
   if (ranks == nullptr || o == nullptr) return RHOSVD_EINVAL;
   if (o->algo < RHOSVD_ALGO_RHOSVD || o->algo > RHOSVD_ALGO_RPET) return RHOSVD_EINVAL;
   if (o->p < 0 || o->q < 0 || o->q > 64) return RHOSVD_EINVAL;
+  if (o->dtype < RHOSVD_F32 || o->dtype > RHOSVD_E4M3 || o->refine_iters < 0 || o->refine_iters > 8)
+    return RHOSVD_EINVAL;
+  pl.dtype = o->dtype;
+  pl.refine = o->refine_iters;
+  pl.p = o->p;
   int64_t cur[RHOSVD_MAX_MODES];
   for (int n = 0; n < g.N; ++n) cur[n] = g.d[n];
   for (int n = 0; n < g.N; ++n) {
@@ -277,6 +366,29 @@ rhosvd_status make_plan(const Geom& g, const int32_t* ranks, const rhosvd_opts* 
       pl.S[n] = (int)S;
     }
     if (o->algo == RHOSVD_ALGO_RSTHOSVD) cur[n] = R;
+  }
+  if (o->flags & ~RHOSVD_OPT_KRONECKER) return RHOSVD_EINVAL;
+  if (o->flags & RHOSVD_OPT_KRONECKER) {
+    // every factor sketch has k^(N-1) columns, k the smallest width that reaches
+    // the largest requested K_n; S_n defaults to 2 K_n + 1 of that width
+    if (o->algo != RHOSVD_ALGO_RPET || g.N < 2) return RHOSVD_EINVAL;
+    int kmax = 1;
+    for (int n = 0; n < g.N; ++n) kmax = std::max(kmax, pl.K[n]);
+    int64_t k = 1, kp = 1;
+    for (;;) {
+      kp = 1;
+      for (int e = 0; e < g.N - 1; ++e) kp *= k;
+      if (kp >= kmax) break;
+      ++k;
+    }
+    for (int n = 0; n < g.N; ++n) {
+      if (kp > g.d[n] || kp > pl.J[n] || kp > RHOSVD_MAX_K || k > g.d[n]) return RHOSVD_EINVAL;
+      pl.K[n] = (int)kp;
+      const int64_t S = o->S[n] > 0 ? o->S[n] : 2 * kp + 1;
+      if (S < kp || S > (int64_t(1) << 20)) return RHOSVD_EINVAL;
+      pl.S[n] = (int)S;
+    }
+    pl.kron = (int)k;
   }
   return RHOSVD_OK;
 }
@@ -303,6 +415,8 @@ void run_rsthosvd(Ctx& c, const float* X, const Geom& g0, const int32_t* ranks, 
   for (int n = 0; n < g0.N; ++n) need_om |= (Omega == nullptr || Omega[n] == nullptr);
   float* Om = need_om ? c.take<float>(max_jk) : nullptr;
   float* Sb[2] = {c.take<float>(max_s), c.take<float>(max_s)};
+  // the reduced-precision copy serves the power products of mode 1 (the original X)
+  const LpCopy lp = (q > 0 && pl.dtype != RHOSVD_F32) ? lp_make(c, X, g0, pl.dtype) : LpCopy{};
   Geom g = g0;
   const float* cur = X;
   int ping = 0;
@@ -317,7 +431,7 @@ void run_rsthosvd(Ctx& c, const float* X, const Geom& g0, const int32_t* ranks, 
       continue;
     }
     const float* om = (Omega != nullptr) ? Omega[n] : nullptr;
-    alg1_mode(c, cur, g, n, K, R, q, seed, om, Yb, Zb, Om, Ub);
+    alg1_mode(c, cur, g, n, K, R, q, seed, om, Yb, Zb, Om, Ub, 0, n == 0 ? &lp : nullptr);
     lift_factor(c, Yb, I, K, Ub, R, U[n]);
     float* dst = last ? G : Sb[ping];
     refold_core(c, Zb, g, n, K, Ub, R, dst);
@@ -351,6 +465,7 @@ void run_rhosvd(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, con
   for (int n = 0; n < g.N; ++n) need_om |= (Omega == nullptr || Omega[n] == nullptr);
   float* Om = need_om ? c.take<float>(max_jk) : nullptr;
   float* Tb[2] = {c.take<float>(max_t), c.take<float>(max_t)};
+  const LpCopy lp = (q > 0 && pl.dtype != RHOSVD_F32) ? lp_make(c, X, g, pl.dtype) : LpCopy{};
   // factors of modes N-1..1 first, mode 0 last so its projection B_1 (still in
   // Zb) gives the first core step X x_1 U_1^T = Ubar^T B_1 without a pass over X
   const float* chain = X;
@@ -365,7 +480,7 @@ void run_rhosvd(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, con
       continue;
     }
     const float* om = (Omega != nullptr) ? Omega[n] : nullptr;
-    alg1_mode(c, X, g, n, K, R, q, seed, om, Yb, Zb, Om, Ub);
+    alg1_mode(c, X, g, n, K, R, q, seed, om, Yb, Zb, Om, Ub, 0, n == 0 ? &lp : nullptr);
     lift_factor(c, Yb, I, K, Ub, R, U[n]);
     if (n == 0) {
       float* dst = (g.N == 1) ? G : Tb[ping];
@@ -394,7 +509,7 @@ void run_rhosvd(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, con
 
 // Core sketch chain H = X x_1 Omega~_1 ... x_N Omega~_N (the core sketch of Alg. 9).
 void core_sketch_chain(Ctx& c, const float* X, const Geom& g, const int* S, uint64_t seed,
-                       const float* const* Om_t, float* const* om_t_buf, float* H) {
+                       const float* const* Om_t, float* const* om_t_buf, float* H, const LpCopy* lp = nullptr) {
   size_t max_t = 1, max_m = 1;
   {
     Geom t = g;
@@ -418,11 +533,144 @@ void core_sketch_chain(Ctx& c, const float* X, const Geom& g, const int* S, uint
     // tensor-core kernel streams with TMA
     c.launches += 1;
     if (!c.dry) c.check(launch_transpose(om, S[n], g.d[n], S[n], Mt, c.s));
-    ttm_mode(c, cur, t, n, Mt, 1, g.d[n], S[n], dst);
+    // the first product reads X: from the reduced-precision copy when there is one
+    const bool done = n == 0 && lp != nullptr && lp_ttm1(c, *lp, g, Mt, g.d[0], S[0], dst, 1, S[0]);
+    if (!done) ttm_mode(c, cur, t, n, Mt, 1, g.d[n], S[n], dst);
     t.d[n] = S[n];
     cur = dst;
     ping ^= 1;
   }
+}
+
+// R-PET's sketches with Kronecker-structured factor test matrices (the
+// memory-efficient form of Sec. 5.1): Y_n = (X x_{p != n} Phi_p^T)_(n) =
+// X_(n) (Phi_N x ... x Phi_1, without Phi_n), Phi_p Gaussian I_p x k, and the
+// core sketch H = X x_1 Omega~_1 ... x_N Omega~_N, from two reads of X:
+//   * C = X x_N [Omega~_N^T Phi_N]: its first S_N slices along the last mode
+//     are X x_N Omega~_N (the core sketch's first product), the last k are
+//     X x_N Phi_N^T, which every Y_n with n < N reduces further;
+//   * E = X x_1 Phi_1^T, which Y_N reduces further.
+// The products after the first act on tensors k / I_p (or S_N / I_N) of X's size.
+void rpet_kron_sketches(Ctx& c, const float* X, const Geom& g, const Plan& pl, uint64_t seed,
+                        const float* const* Omega, const float* const* Omega_t, float* const* Omt,
+                        float* const* Ys, float* H) {
+  const int N = g.N, k = pl.kron, last = N - 1;
+  const int SN = pl.S[last];
+  Scope sc(c);
+  // Phi_p (I_p x k), explicit or drawn on stream_id 10N + p
+  const float* Phi[RHOSVD_MAX_MODES];
+  for (int p = 0; p < N; ++p) {
+    if (Omega != nullptr && Omega[p] != nullptr) {
+      Phi[p] = Omega[p];
+    } else {
+      float* f = c.take<float>((size_t)g.d[p] * k);
+      op_omega(c, seed, (uint32_t)(10 * N + p), g.d[p], k, f);
+      Phi[p] = f;
+    }
+  }
+  // the core sketch's test matrices Omega~_n (S_n x I_n), drawn unless explicit
+  for (int n = 0; n < N; ++n)
+    if (Omt[n] != nullptr) op_omega(c, seed, (uint32_t)(N + n), pl.S[n], (int)g.d[n], Omt[n]);
+  auto omt = [&](int n) { return (Omega_t != nullptr && Omega_t[n] != nullptr) ? Omega_t[n] : Omt[n]; };
+  // chain buffers: the largest intermediate of any of the reductions below
+  size_t max_t = 1, max_m = 1;
+  {
+    Geom t = g;
+    t.d[last] = SN;
+    for (int p = 0; p < last; ++p) {
+      t.d[p] = pl.S[p];
+      max_t = std::max<size_t>(max_t, (size_t)t.numel());
+    }
+    for (int n = 0; n < N; ++n) max_m = std::max<size_t>(max_m, (size_t)g.d[n] * std::max(pl.S[n], k));
+    // a factor chain only shrinks its start (k <= I_p), so its intermediates are
+    // bounded by X x_N Phi_N^T or X x_1 Phi_1^T
+    max_t = std::max<size_t>(max_t, (size_t)g.L(last) * k);
+    max_t = std::max<size_t>(max_t, (size_t)g.J(0) * k);
+  }
+  const int64_t LN = g.L(last);
+  float* Mc = c.take<float>((size_t)g.d[last] * (SN + k));
+  float* C = c.take<float>((size_t)LN * (SN + k));
+  float* E = c.take<float>((size_t)g.J(0) * k);
+  float* Tb[2] = {c.take<float>(max_t), c.take<float>(max_t)};
+  float* Mt = c.take<float>(max_m);
+  size_t max_w = 1;
+  for (int n = 0; n < N; ++n) max_w = std::max<size_t>(max_w, (size_t)g.d[n] * pl.K[n]);
+  float* Wn = c.take<float>(max_w);
+  // read 1: C = X x_N [Omega~_N^T Phi_N]
+  c.launches += 1;
+  if (!c.dry) {
+    c.check(launch_transpose(omt(last), SN, g.d[last], SN, Mc, c.s));
+    c.check(cudaMemcpyAsync(Mc + (size_t)g.d[last] * SN, Phi[last], sizeof(float) * g.d[last] * k,
+                            cudaMemcpyDeviceToDevice, c.s));
+  }
+  ttm_mode(c, X, g, last, Mc, 1, g.d[last], SN + k, C);
+  // chain src (geometry t) x_p M_p for the listed modes, the last product into dst
+  auto chain = [&](const float* src, Geom t, const int* modes, int nm, bool core, float* dst) -> Geom {
+    const float* cur = src;
+    int ping = 0;
+    for (int q = 0; q < nm; ++q) {
+      const int p = modes[q];
+      const int width = core ? pl.S[p] : k;
+      const float* M = Phi[p];
+      if (core) {                                  // the TTM takes Omega~_p^T (I_p x S_p)
+        c.launches += 1;
+        if (!c.dry) c.check(launch_transpose(omt(p), pl.S[p], g.d[p], pl.S[p], Mt, c.s));
+        M = Mt;
+      }
+      float* out = (q == nm - 1) ? dst : Tb[ping];
+      ttm_mode(c, cur, t, p, M, 1, g.d[p], width, out);
+      t.d[p] = width;
+      cur = out;
+      ping ^= 1;
+    }
+    return t;
+  };
+  // core sketch H = (X x_N Omega~_N) x_1 Omega~_1 ... x_{N-1} Omega~_{N-1}
+  {
+    Geom t = g;
+    t.d[last] = SN;
+    int modes[RHOSVD_MAX_MODES], nm = 0;
+    for (int p = 0; p < last; ++p) modes[nm++] = p;
+    if (nm == 0) {
+      if (!c.dry) c.check(cudaMemcpyAsync(H, C, sizeof(float) * LN * SN, cudaMemcpyDeviceToDevice, c.s));
+    } else {
+      chain(C, t, modes, nm, true, H);
+    }
+  }
+  // factor sketch of mode n, as the unfolding of the reduced tensor
+  auto emit = [&](const float* red, const Geom& t, int n) {
+    c.launches += 1;
+    if (!c.dry) c.check(launch_unfold(red, t.L(n), t.d[n], t.Rt(n), Ys[n], c.s));
+  };
+  const float* CF = C + (size_t)LN * SN;         // X x_N Phi_N^T
+  for (int n = 0; n < last; ++n) {
+    Geom t = g;
+    t.d[last] = k;
+    int modes[RHOSVD_MAX_MODES], nm = 0;
+    for (int p = 0; p < last; ++p)
+      if (p != n) modes[nm++] = p;
+    if (nm == 0) {
+      emit(CF, t, n);
+    } else {
+      const Geom r = chain(CF, t, modes, nm, false, Wn);
+      emit(Wn, r, n);
+    }
+  }
+  // read 2: E = X x_1 Phi_1^T, then Y_N
+  ttm_mode(c, X, g, 0, Phi[0], 1, g.d[0], k, E);
+  {
+    Geom t = g;
+    t.d[0] = k;
+    int modes[RHOSVD_MAX_MODES], nm = 0;
+    for (int p = 1; p < last; ++p) modes[nm++] = p;
+    if (nm == 0) {
+      emit(E, t, last);
+    } else {
+      const Geom r = chain(E, t, modes, nm, false, Wn);
+      emit(Wn, r, last);
+    }
+  }
+  for (int n = 0; n < N; ++n) op_orth(c, Ys[n], g.d[n], pl.K[n], g.d[n]);
 }
 
 void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const Plan& pl, uint64_t seed,
@@ -446,7 +694,7 @@ void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const
   }
   bool need_om = false;
   for (int n = 0; n < N; ++n) need_om |= (Omega == nullptr || Omega[n] == nullptr);
-  float* Om = need_om ? c.take<float>(max_jk) : nullptr;
+  float* Om = (need_om && pl.kron == 0) ? c.take<float>(max_jk) : nullptr;
   Geom hs = g, cs = g;
   for (int n = 0; n < N; ++n) {
     hs.d[n] = pl.S[n];
@@ -466,20 +714,36 @@ void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const
   float* Lf = c.take<float>(max_kk);
 
   // R-PET (Alg. 9, Sec. 5.1): factor sketches and their bases, the core
-  // sketch, recovery of the core by pseudo-inverses, truncation.
-  // Factor sketches Y_n = X_(n) Omega_n and their orthonormal bases Q_n
-  for (int n = 0; n < N; ++n) {
-    const float* W = (Omega != nullptr) ? Omega[n] : nullptr;
-    if (W != nullptr)
-      op_sketch(c, mode_view(X, g, n), WView{W, g.L(n), g.J(n)}, pl.K[n], Ys[n], g.d[n]);
-    else
-      op_sketch_seeded(c, mode_view(X, g, n), pl.K[n], seed, (uint32_t)n, Ys[n], g.d[n], Om);
-    op_orth(c, Ys[n], g.d[n], pl.K[n], g.d[n]);
+  // sketch, recovery of the core by pseudo-inverses, truncation.  With a
+  // reduced dtype the single pass reads the reduced-precision copy of X and the
+  // seeded test matrices are rounded to its format.
+  if (pl.kron > 0) {
+    rpet_kron_sketches(c, X, g, pl, seed, Omega, Omega_t, Omt, Ys, H);
+  } else {
+    const LpCopy lp = lp_make(c, X, g, pl.dtype);
+    // Factor sketches Y_n = X_(n) Omega_n and their orthonormal bases Q_n
+    for (int n = 0; n < N; ++n) {
+      const float* W = (Omega != nullptr) ? Omega[n] : nullptr;
+      if (lp.eb != 0 && W == nullptr) {
+        lp_omega(c, lp, seed, (uint32_t)n, g.J(n), pl.K[n], Om);
+        W = Om;
+      }
+      if (lp.eb != 0 && lp_sketch(c, lp, g, n, W, pl.K[n], Ys[n])) {
+      } else if (W != nullptr) {
+        op_sketch(c, mode_view(X, g, n), WView{W, g.L(n), g.J(n)}, pl.K[n], Ys[n], g.d[n]);
+      } else {
+        op_sketch_seeded(c, mode_view(X, g, n), pl.K[n], seed, (uint32_t)n, Ys[n], g.d[n], Om);
+      }
+      op_orth(c, Ys[n], g.d[n], pl.K[n], g.d[n]);
+    }
+    // core sketch H
+    for (int n = 0; n < N; ++n)
+      if (Omt[n] != nullptr) {
+        if (lp.eb != 0) lp_omega(c, lp, seed, (uint32_t)(N + n), pl.S[n], (int)g.d[n], Omt[n]);
+        else op_omega(c, seed, (uint32_t)(N + n), pl.S[n], (int)g.d[n], Omt[n]);
+      }
+    core_sketch_chain(c, X, g, pl.S, seed, Omega_t, Omt, H, &lp);
   }
-  // core sketch H
-  for (int n = 0; n < N; ++n)
-    if (Omt[n] != nullptr) op_omega(c, seed, (uint32_t)(N + n), pl.S[n], (int)g.d[n], Omt[n]);
-  core_sketch_chain(c, X, g, pl.S, seed, Omega_t, Omt, H);
   // recovered core C = H x_n (Omega~_n Q_n)^+ with the pseudo-inverse from the normal
   // equations (Omega~_n Q_n is a well-conditioned Gaussian-times-orthonormal
   // matrix): P^T = A (A^T A)^-1 = (A R^-1) R^-T, R^T R = A^T A
@@ -539,6 +803,95 @@ void run_rpet(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const
     tc.d[n] = ranks[n];
     chain = dst;
     which ^= 1;
+  }
+}
+
+// Refinement: sweeps of RP-HOOI (Alg. 7) on the FP32 X, starting from the
+// factors U[n] (I_n x R_n) of the decomposition.  For each mode n in turn
+// S = X x_{p != n} U_p^T with the latest factors, and U_n is re-formed by
+// Alg. 1 with q = 0 on S_(n) (sketch width min(R_n + p, I_n, J_n), truncation
+// to R_n); the core is X x_1 U_1^T ... x_N U_N^T with the new factors.  Two
+// full reads of X per sweep: S_1 is formed starting from the last mode, and
+// T = X x_1 U_1^T (after U_1 is updated) serves every later mode, extended by
+// one factor per mode as the sweep goes on.  Test matrices of sweep t, mode n
+// are seeded on stream_id 2N + tN + n.
+void run_refine(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, const Plan& pl, uint64_t seed,
+                float* const* U, float* G) {
+  const int N = g.N;
+  if (pl.refine <= 0 || N < 2) return;
+  // sizes: the chains' intermediates, the per-mode S_n, Alg. 1's buffers
+  size_t max_t = 1, max_jk = 1, max_ik = 1, max_kk = 1;
+  int Kr[RHOSVD_MAX_MODES];
+  for (int n = 0; n < N; ++n) {
+    int64_t J = 1;
+    for (int k = 0; k < N; ++k)
+      if (k != n) J *= ranks[k];
+    Kr[n] = (int)std::min<int64_t>(ranks[n] + pl.p, std::min<int64_t>(g.d[n], J));
+    Kr[n] = std::max(Kr[n], (int)ranks[n]);
+    max_jk = std::max<size_t>(max_jk, (size_t)J * Kr[n]);
+    max_ik = std::max<size_t>(max_ik, (size_t)g.d[n] * Kr[n]);
+    max_kk = std::max<size_t>(max_kk, (size_t)ldu_of(Kr[n]) * ranks[n]);
+  }
+  {
+    Geom t = g;                                       // X x_{N-1} ... (chain of S_1)
+    for (int p = N - 1; p >= 1; --p) {
+      t.d[p] = ranks[p];
+      max_t = std::max<size_t>(max_t, (size_t)t.numel());
+    }
+    t = g;                                            // T = X x_1 U_1^T and its extensions
+    t.d[0] = ranks[0];
+    max_t = std::max<size_t>(max_t, (size_t)t.numel());
+  }
+  Scope sc(c);
+  float* Tb[2] = {c.take<float>(max_t), c.take<float>(max_t)};   // T and its extension (ping-pong)
+  float* Cb[2] = {c.take<float>(max_t), c.take<float>(max_t)};   // the chain forming S_n
+  float* Yb = c.take<float>(max_ik);
+  float* Zb = c.take<float>(max_jk);
+  float* Om = c.take<float>(max_jk);
+  float* Ub = c.take<float>(max_kk);
+  // chain: src (geometry t) x_p U_p^T for p = N-1 down to lo, p != skip; returns the result
+  auto chain = [&](const float* src, Geom& t, int lo, int skip) -> const float* {
+    const float* cur = src;
+    int ping = 0;
+    for (int p = N - 1; p >= lo; --p) {
+      if (p == skip) continue;
+      float* dst = Cb[ping];
+      ttm_mode(c, cur, t, p, U[p], 1, g.d[p], ranks[p], dst);
+      t.d[p] = ranks[p];
+      cur = dst;
+      ping ^= 1;
+    }
+    return cur;
+  };
+  for (int sweep = 0; sweep < pl.refine; ++sweep) {
+    const uint32_t sb = (uint32_t)(2 * N + sweep * N);
+    // mode 1: S_1 = X x_{p > 1} U_p^T
+    Geom t = g;
+    const float* s1 = chain(X, t, 1, -1);
+    alg1_mode(c, s1, t, 0, Kr[0], ranks[0], 0, seed, nullptr, Yb, Zb, Om, Ub, sb);
+    lift_factor(c, Yb, g.d[0], Kr[0], Ub, ranks[0], U[0]);
+    // T = X x_1 U_1^T, then for n >= 2: S_n = T x_{p > n} U_p^T, T <- T x_n U_n^T
+    Geom tg = g;
+    int tp = 0;
+    const float* T = X;
+    {
+      float* dst = (N == 1) ? G : Tb[tp];
+      ttm_mode(c, X, tg, 0, U[0], 1, g.d[0], ranks[0], dst);
+      tg.d[0] = ranks[0];
+      T = dst;
+      tp ^= 1;
+    }
+    for (int n = 1; n < N; ++n) {
+      Geom ts = tg;
+      const float* sn = chain(T, ts, n + 1, -1);
+      alg1_mode(c, sn, ts, n, Kr[n], ranks[n], 0, seed, nullptr, Yb, Zb, Om, Ub, sb);
+      lift_factor(c, Yb, g.d[n], Kr[n], Ub, ranks[n], U[n]);
+      float* dst = (n == N - 1) ? G : Tb[tp];
+      ttm_mode(c, T, tg, n, U[n], 1, g.d[n], ranks[n], dst);
+      tg.d[n] = ranks[n];
+      T = dst;
+      tp ^= 1;
+    }
   }
 }
 
@@ -631,6 +984,7 @@ static size_t decompose_ws(const Geom& g, const int32_t* ranks, const rhosvd_opt
   if (o->algo == RHOSVD_ALGO_RSTHOSVD) run_rsthosvd(c, nullptr, g, ranks, pl, o->q, o->seed, Omega, U, nullptr);
   else if (o->algo == RHOSVD_ALGO_RHOSVD) run_rhosvd(c, nullptr, g, ranks, pl, o->q, o->seed, Omega, U, nullptr);
   else run_rpet(c, nullptr, g, ranks, pl, o->seed, Omega, Omega_t, U, nullptr);
+  run_refine(c, nullptr, g, ranks, pl, o->seed, U, nullptr);
   return c.high;
 }
 
@@ -644,6 +998,7 @@ int64_t rhosvd_launch_count(const rhosvd_shape* shape, const int32_t* ranks, con
   if (opts->algo == RHOSVD_ALGO_RSTHOSVD) run_rsthosvd(c, nullptr, g, ranks, pl, opts->q, opts->seed, nullptr, U, nullptr);
   else if (opts->algo == RHOSVD_ALGO_RHOSVD) run_rhosvd(c, nullptr, g, ranks, pl, opts->q, opts->seed, nullptr, U, nullptr);
   else run_rpet(c, nullptr, g, ranks, pl, opts->seed, nullptr, nullptr, U, nullptr);
+  run_refine(c, nullptr, g, ranks, pl, opts->seed, U, nullptr);
   return c.launches;
 }
 
@@ -843,6 +1198,7 @@ rhosvd_status rhosvd_decompose(const float* X, const rhosvd_shape* shape, const 
   if (opts->algo == RHOSVD_ALGO_RSTHOSVD) run_rsthosvd(c, X, g, ranks, pl, opts->q, opts->seed, Omega, U, G);
   else if (opts->algo == RHOSVD_ALGO_RHOSVD) run_rhosvd(c, X, g, ranks, pl, opts->q, opts->seed, Omega, U, G);
   else run_rpet(c, X, g, ranks, pl, opts->seed, Omega, Omega_tilde, U, G);
+  run_refine(c, X, g, ranks, pl, opts->seed, U, G);
   return finish(c);
 }
 

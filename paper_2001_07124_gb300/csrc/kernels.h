@@ -96,6 +96,30 @@ cudaError_t launch_tc_ttm(const View& x, const float* Mp, int64_t m_k, int K, co
 cudaError_t launch_ttm_auto(const View& x, const float* Mp, int64_t m_i, int64_t m_k, int K, const OView& out,
                             const DevStatus* skip, DevStatus* st, cudaStream_t stream);
 
+// ---- tc_lp.cu: reduced-precision copy of X (eb = bytes per element: 2 BF16, 1 e4m3)
+// X_q = format(X / s_slice) for frontal slices of slice_len elements; e4m3 also
+// writes the power-of-two scales (n / slice_len floats, amax: as many uints of
+// scratch); BF16 is unscaled (scale untouched).
+cudaError_t launch_quantize(const float* X, int64_t n, int64_t slice_len, int eb, void* Xq, float* scale,
+                            unsigned int* amax, cudaStream_t st);
+// a <- nearest value of the format, in place (test matrices of a reduced-precision run)
+cudaError_t launch_round_to_format(float* a, int64_t n, int eb, cudaStream_t st);
+// Y = X_q,(n) W with the view x in elements (x.p unused; the data is xq) and W
+// a plain J x K FP32 matrix; scale_mode 0 none, 1 per column slice (slice =
+// j / slice_len), 2 per row (scale[i]).  part: sketch_lp_scratch_floats floats.
+bool tc_sketch_lp_supported(const View& x, int eb, int K, int scale_mode, int64_t slice_len);
+size_t sketch_lp_scratch_floats(int64_t I, int K, int64_t J, int eb);
+cudaError_t launch_tc_sketch_lp(const View& x, const void* xq, int eb, const float* W, int K, float* Y,
+                                int64_t ldy, const float* scale, int scale_mode, int64_t slice_len, float* part,
+                                DevStatus* st, cudaStream_t stream);
+// Out(j, k) = s(j / slice_len) sum_i X_q(i, j) M(i, k) for the mode-1 unfolding
+// (X_q I x J, i contiguous), M column-major with ldm; Out(j, k) at
+// out[j * o_r + k * o_k]; scale may be NULL.
+bool tc_ttm_lp_supported(int64_t I, int64_t J, int eb, int K, int64_t ldm);
+cudaError_t launch_tc_ttm_lp(const void* xq, int eb, int64_t I, int64_t J, const float* M, int64_t ldm, int K,
+                             float* out, int64_t o_k, int64_t o_r, const float* scale, int64_t slice_len,
+                             DevStatus* st, cudaStream_t stream);
+
 // ---- gram.cu
 // G (K x K, FP64) = A^T A for A m x K (ld).  exact: double-float products
 // (FP64-accurate for ill-conditioned A); otherwise FP32 within 64-row tiles and
@@ -144,5 +168,7 @@ cudaError_t launch_small_eig(const double* G, int K, int R, float* Ub, int ldu, 
 cudaError_t launch_transpose(const float* in, int64_t rows, int64_t cols, int64_t ld, float* out,
                              cudaStream_t st);
 cudaError_t launch_fill_identity(float* U, int64_t I, int R, cudaStream_t st);
+// out (I x L*Rt, column-major) = mode unfolding of in viewed as [L, I, Rt]
+cudaError_t launch_unfold(const float* in, int64_t L, int64_t I, int64_t Rt, float* out, cudaStream_t st);
 
 }  // namespace rhosvd

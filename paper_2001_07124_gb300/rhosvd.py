@@ -25,9 +25,11 @@ from . import _build
 MAX_MODES = 8
 MAX_K = 128
 ALGOS = {"rhosvd": 0, "rsthosvd": 1, "rpet": 2}
+DTYPES = {"f32": 0, "bf16": 1, "e4m3": 2}
 STATUS = {0: "RHOSVD_OK", 1: "RHOSVD_EINVAL", 2: "RHOSVD_ENOMEM", 3: "RHOSVD_ECUDA", 4: "RHOSVD_ENONFINITE",
           5: "RHOSVD_EBREAKDOWN", 6: "RHOSVD_ETIMEOUT", 7: "RHOSVD_EUNSUPPORTED"}
 FLAG_FALLBACK = 1
+OPT_KRONECKER = 1
 
 
 class RhosvdError(RuntimeError):
@@ -44,7 +46,8 @@ class Shape(ctypes.Structure):
 class Opts(ctypes.Structure):
     _fields_ = [("algo", ctypes.c_int32), ("p", ctypes.c_int32), ("q", ctypes.c_int32),
                 ("flags", ctypes.c_int32), ("seed", ctypes.c_uint64),
-                ("K", ctypes.c_int32 * MAX_MODES), ("S", ctypes.c_int32 * MAX_MODES)]
+                ("K", ctypes.c_int32 * MAX_MODES), ("S", ctypes.c_int32 * MAX_MODES),
+                ("dtype", ctypes.c_int32), ("refine_iters", ctypes.c_int32)]
 
 
 _LIB = None
@@ -120,10 +123,13 @@ def make_shape(dims: Sequence[int]) -> Shape:
 
 
 def make_opts(algo: str = "rsthosvd", p: int = 10, q: int = 1, seed: int = 0,
-              K: Sequence[int] | None = None, S: Sequence[int] | None = None) -> Opts:
+              K: Sequence[int] | None = None, S: Sequence[int] | None = None,
+              dtype: str = "f32", refine: int = 0, kron: bool = False) -> Opts:
     o = Opts()
+    o.dtype = DTYPES[dtype]
+    o.refine_iters = int(refine)
     o.algo = ALGOS[algo]
-    o.p, o.q, o.flags, o.seed = int(p), int(q), 0, int(seed) & 0xFFFFFFFFFFFFFFFF
+    o.p, o.q, o.flags, o.seed = int(p), int(q), OPT_KRONECKER if kron else 0, int(seed) & 0xFFFFFFFFFFFFFFFF
     for n in range(MAX_MODES):
         o.K[n] = int(K[n]) if K is not None and n < len(K) else 0
         o.S[n] = int(S[n]) if S is not None and n < len(S) else 0
@@ -228,23 +234,25 @@ class Workspace:
 
 # ------------------------------------------------------------------ entry points
 
-def rhosvd_plan(dims, ranks, algo="rsthosvd", p=10, q=1, K=None, S=None):
+def rhosvd_plan(dims, ranks, algo="rsthosvd", p=10, q=1, K=None, S=None, dtype="f32", refine=0, kron=False):
     """(K_n, S_n, J_n) lists a decomposition uses."""
     N = len(dims)
     Ko, So, Jo = (ctypes.c_int32 * N)(), (ctypes.c_int32 * N)(), (ctypes.c_int64 * N)()
     _check(lib().rhosvd_plan(ctypes.byref(make_shape(dims)), _i32(ranks),
-                             ctypes.byref(make_opts(algo, p, q, 0, K, S)), Ko, So, Jo), "rhosvd_plan")
+                             ctypes.byref(make_opts(algo, p, q, 0, K, S, dtype, refine, kron)), Ko, So, Jo), "rhosvd_plan")
     return list(Ko), list(So), list(Jo)
 
 
-def rhosvd_workspace_size(dims, ranks, algo="rsthosvd", p=10, q=1, K=None, S=None) -> int:
+def rhosvd_workspace_size(dims, ranks, algo="rsthosvd", p=10, q=1, K=None, S=None, dtype="f32", refine=0,
+                          kron=False) -> int:
     return int(lib().rhosvd_workspace_size(ctypes.byref(make_shape(dims)), _i32(ranks),
-                                           ctypes.byref(make_opts(algo, p, q, 0, K, S))))
+                                           ctypes.byref(make_opts(algo, p, q, 0, K, S, dtype, refine, kron))))
 
 
-def rhosvd_launch_count(dims, ranks, algo="rsthosvd", p=10, q=1, K=None, S=None) -> int:
+def rhosvd_launch_count(dims, ranks, algo="rsthosvd", p=10, q=1, K=None, S=None, dtype="f32", refine=0,
+                        kron=False) -> int:
     return int(lib().rhosvd_launch_count(ctypes.byref(make_shape(dims)), _i32(ranks),
-                                         ctypes.byref(make_opts(algo, p, q, 0, K, S))))
+                                         ctypes.byref(make_opts(algo, p, q, 0, K, S, dtype, refine, kron))))
 
 
 def rhosvd_primitive_workspace_size(dims, Kmax) -> int:
@@ -393,16 +401,20 @@ def rhosvd_core(X, dims, Qs, ws=None, stream=None):
 
 
 def rhosvd_decompose(X, dims, ranks, algo="rsthosvd", p=10, q=1, seed=0, Omega=None, Omega_tilde=None,
-                     K=None, S=None, ws=None, out=None, stream=None, check=True):
+                     K=None, S=None, ws=None, out=None, stream=None, check=True, dtype="f32", refine=0,
+                     kron=False):
     """Randomized Tucker decomposition; returns (G as an (R_1..R_N) view, [U_n as (I_n, R_n) views]).
 
     Omega / Omega_tilde: optional lists of explicit test matrices as column-major
     buffers (rows x cols) with the sizes rhosvd_plan reports.  ``out``: optional
     (G_buf, [U_bufs]) preallocated buffers.  ``check``: synchronise and raise on
-    a device-detected error."""
+    a device-detected error.  ``dtype``: "f32", "bf16" or "e4m3", the
+    arithmetic of the sketch passes; ``refine``: RP-HOOI sweeps afterwards;
+    ``kron``: R-PET with Kronecker-structured factor sketches (Omega[p] then
+    supplies Phi_p, I_p x k)."""
     X = colmajor(X, dims)
     N = len(dims)
-    shape, opts = make_shape(dims), make_opts(algo, p, q, seed, K, S)
+    shape, opts = make_shape(dims), make_opts(algo, p, q, seed, K, S, dtype, refine, kron)
     r = _i32(ranks)
     if out is None:
         G = empty_colmajor(ranks)
@@ -445,7 +457,8 @@ class DecomposeGraph:
         if out is None:
             out = (empty_colmajor(ranks), [empty_colmajor((dims[n], ranks[n])) for n in range(N)])
         shape, opts = make_shape(dims), make_opts(kw.get("algo", "rsthosvd"), kw.get("p", 10), kw.get("q", 1),
-                                                 kw.get("seed", 0), kw.get("K"), kw.get("S"))
+                                                 kw.get("seed", 0), kw.get("K"), kw.get("S"),
+                                                 kw.get("dtype", "f32"), kw.get("refine", 0), kw.get("kron", False))
         need = int(lib().rhosvd_workspace_size(ctypes.byref(shape), _i32(ranks), ctypes.byref(opts)))
         if need == 0:
             _check(1, "rhosvd_workspace_size")
@@ -487,7 +500,8 @@ class BatchGraph:
             N = len(dims)
             out = (empty_colmajor(ranks), [empty_colmajor((dims[n], ranks[n])) for n in range(N)])
             shape, opts = make_shape(dims), make_opts(kw.get("algo", "rsthosvd"), kw.get("p", 10),
-                                                     kw.get("q", 1), kw.get("seed", 0), kw.get("K"), kw.get("S"))
+                                                     kw.get("q", 1), kw.get("seed", 0), kw.get("K"), kw.get("S"),
+                                                     kw.get("dtype", "f32"), kw.get("refine", 0), kw.get("kron", False))
             need = int(lib().rhosvd_workspace_size(ctypes.byref(shape), _i32(ranks), ctypes.byref(opts)))
             if need == 0:
                 _check(1, "rhosvd_workspace_size")
