@@ -83,14 +83,15 @@ def _l2_note(w) -> str:
     return f"input {mib:.1f} MiB fits in L2 (not flushed)"
 
 
-def metric_name(w, dtype="f32", refine=0) -> str:
+def metric_name(w, dtype="f32", refine=0, kron=False) -> str:
     """Metric label of a workload, e.g. decomps/s (R-STHOSVD 512^3 FP32, rank 32, p=10, q=1)."""
     d = w.dims
     shape = f"{d[0]}^{len(d)}" if len(set(d)) == 1 else "x".join(str(v) for v in d)
     r = w.ranks
     rank = str(r[0]) if len(set(r)) == 1 else "(" + ",".join(str(v) for v in r) + ")"
     par = f"K={w.K[0]}, S={w.S[0]}" if w.algo == "rpet" and w.K else f"p={w.p}, q={w.q}"
-    extra = "" if dtype == "f32" else f", {dtype.upper()} sketch passes"
+    extra = ", Kronecker factor sketches" if kron else ""
+    extra += "" if dtype == "f32" else f", {dtype.upper()} sketch passes"
     extra += f", {refine} RP-HOOI sweep" + ("s" if refine > 1 else "") if refine else ""
     return f"decomps/s ({_ALGO_NAMES[w.algo]} {shape} FP32, rank {rank}, {par}{extra})"
 UNIT = "decomps/s"
@@ -202,7 +203,7 @@ def accuracy_report(x32, g_gpu, u_gpu, g_or, u_or, tol=1e-5, max_sine=1e-4) -> d
             "E_transpose_core": M.rel_error(x32, g_t, u_gpu)}
 
 
-def oracle_decompose(w, x32, dtype="f32", refine=0):
+def oracle_decompose(w, x32, dtype="f32", refine=0, kron=False):
     """Time one oracle decomposition (FP64 NumPy) with the generator's own test
     matrices (rounded to the format of a reduced-precision run, as the device
     rounds its own) and the same number of RP-HOOI sweeps."""
@@ -213,7 +214,18 @@ def oracle_decompose(w, x32, dtype="f32", refine=0):
     N = len(w.dims)
     rnd = (lambda a: round_to(a, dtype)) if (dtype != "f32" and w.algo == "rpet") else (lambda a: a)
     t0 = time.perf_counter()
-    if w.algo == "rpet":
+    if w.algo == "rpet" and kron:
+        # Kronecker-structured factor sketches: Phi_p on stream_id 10N + p, k from the plan's K_n = k^(N-1)
+        fs, ts = shapes
+        from paper_2001_07124_gb300 import rhosvd as R
+        Kp, Sp, _ = R.rhosvd_plan(w.dims, w.ranks, "rpet", w.p, w.q, K=w.K, S=w.S, kron=True)
+        k = int(round(Kp[0] ** (1.0 / (N - 1))))
+        phis = [philox.omega(w.omega_seed, 10 * N + p, w.dims[p], k).astype(np.float64) for p in range(N)]
+        om = [A.kronecker_test_matrix(phis, n) for n in range(N)]
+        ot = [philox.omega(w.omega_seed, N + n, Sp[n], w.dims[n]).astype(np.float64) for n in range(N)]
+        t0 = time.perf_counter()
+        g, u, _ = A.rpet(x32, w.ranks, om, ot)
+    elif w.algo == "rpet":
         fs, ts = shapes
         om = [rnd(philox.omega(w.omega_seed, n, r, c).astype(np.float64)) for n, (r, c) in enumerate(fs)]
         ot = [rnd(philox.omega(w.omega_seed, N + n, r, c).astype(np.float64)) for n, (r, c) in enumerate(ts)]
@@ -265,8 +277,12 @@ def run_serving(args):
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
     sizes = np.clip(np.rint(np.exp(rng.uniform(np.log(64), np.log(768), size=n)) / 64) * 64, 64, 768).astype(int)
     ranks = np.minimum(rng.integers(8, 65, size=n), sizes)
-    # one low-rank-plus-noise tensor per size, drawn on the device and kept in pinned host memory
+    # half of the requests are fixed-accuracy ones (eps 1e-2 on a core with a 0.9^(i+j+k)
+    # decay and 1e-4 noise; ranks found on the device), half fixed-rank
+    fixed_acc = (np.arange(n) % 2) == 1
+    # one low-rank-plus-noise tensor per size and kind, drawn on the device and kept in pinned host memory
     pool = {}
+    pool_acc = {}
     g = torch.Generator(device="cuda")
     for I in sorted(set(sizes.tolist())):
         g.manual_seed(1005 + I)
@@ -277,12 +293,27 @@ def run_serving(args):
         noise = torch.randn(x.shape, device="cuda", generator=g)
         x = x + 1e-3 * x.norm() / noise.norm() * noise
         pool[I] = x.contiguous().reshape(-1).cpu().pin_memory()
-        del x, noise, core, U
+        del x, noise
+        ii = torch.arange(r, device="cuda", dtype=torch.float32)
+        decay = 0.9 ** (ii[:, None, None] + ii[None, :, None] + ii[None, None, :])
+        xa = torch.einsum("abc,ia,jb,kc->kji", core * decay, U[0], U[1], U[2])
+        noise = torch.randn(xa.shape, device="cuda", generator=g)
+        xa = xa + 1e-4 * xa.norm() / noise.norm() * noise
+        pool_acc[I] = xa.contiguous().reshape(-1).cpu().pin_memory()
+        del xa, noise, core, U
     torch.cuda.empty_cache()
 
     def requests():
-        return [serving.Request(i, (int(sizes[i]),) * 3, (int(ranks[i]),) * 3, float(arrivals[i]),
-                                x_host=pool[int(sizes[i])], p=10, q=1, seed=i) for i in range(n)]
+        out = []
+        for i in range(n):
+            I = int(sizes[i])
+            if fixed_acc[i]:
+                out.append(serving.Request(i, (I,) * 3, (int(ranks[i]),) * 3, float(arrivals[i]), x_host=pool_acc[I],
+                                           seed=i, tol=1e-2, block=16, k_max=(min(I, 96),) * 3))
+            else:
+                out.append(serving.Request(i, (I,) * 3, (int(ranks[i]),) * 3, float(arrivals[i]), x_host=pool[I],
+                                           p=10, q=1, seed=i))
+        return out
 
     # warm-up: the whole stream once, untimed, so that kernel attributes, the
     # device and pinned-host caching allocators and the per-size workspaces are
@@ -290,11 +321,18 @@ def run_serving(args):
     serving.serve(requests(), slots=4, budget_bytes=150 * 10 ** 9)
     line = {"mode": "serve", "requests": n, "arrival_rate_per_s": rate,
             "sizes": "cubic, log-uniform in [64, 768], multiples of 64", "ranks": "uniform 8..64",
-            "algo": "rsthosvd p=10 q=1 (fixed rank)", "budget_gb": 150,
-            "note": "fixed-accuracy (adaptive range finder) requests not implemented"}
+            "algo": "half R-STHOSVD p=10 q=1 (fixed rank), half fixed-accuracy R-STHOSVD eps=1e-2 "
+                    "(blocked range finder, block 16, k_max 96)", "budget_gb": 150}
     for slots in (4, 1):
         res = serving.serve(requests(), slots=slots, budget_bytes=150 * 10 ** 9)
         line[f"slots{slots}"] = serving.latency_summary(res)
+        acc = [r for r in res if fixed_acc[r.rid]]
+        if acc:
+            line[f"slots{slots}"]["fixed_accuracy"] = serving.latency_summary(acc)
+            line[f"slots{slots}"]["fixed_accuracy"]["mean_rank"] = float(np.mean([r.ranks[0] for r in acc]))
+        rk = [r for r in res if not fixed_acc[r.rid]]
+        if rk:
+            line[f"slots{slots}"]["fixed_rank"] = serving.latency_summary(rk)
     print(json.dumps(line), flush=True)
 
 
@@ -437,6 +475,7 @@ def main():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "e4m3"],
                     help="arithmetic of the sketch passes (reduced-precision copy of X)")
     ap.add_argument("--refine", type=int, default=0, help="RP-HOOI sweeps after the decomposition")
+    ap.add_argument("--kron", action="store_true", help="R-PET with Kronecker-structured factor sketches")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -476,9 +515,10 @@ def main():
     del x
     X = x_host.cuda()
     dims, ranks = w.dims, w.ranks
-    kw = dict(algo=w.algo, p=w.p, q=w.q, seed=w.omega_seed, K=w.K, S=w.S, dtype=args.dtype, refine=args.refine)
+    kw = dict(algo=w.algo, p=w.p, q=w.q, seed=w.omega_seed, K=w.K, S=w.S, dtype=args.dtype, refine=args.refine,
+              kron=args.kron)
     ws = R.Workspace(R.rhosvd_workspace_size(dims, ranks, w.algo, w.p, w.q, K=w.K, S=w.S, dtype=args.dtype,
-                                             refine=args.refine))
+                                             refine=args.refine, kron=args.kron))
     G = R.empty_colmajor(ranks)
     Us = [R.empty_colmajor((dims[n], ranks[n])) for n in range(len(dims))]
     out = (G, Us)
@@ -615,7 +655,7 @@ def main():
     cpu = None
     accuracy = None
     if rank == 0 and x32 is not None:
-        t_or, g_or, u_or = oracle_decompose(w, x32, args.dtype, args.refine)
+        t_or, g_or, u_or = oracle_decompose(w, x32, args.dtype, args.refine, args.kron)
         g_gpu = R.fortran_view(G, ranks).cpu().numpy().astype(np.float64)
         u_gpu = [R.matrix(u, dims[n], ranks[n]).cpu().numpy().astype(np.float64) for n, u in enumerate(Us)]
         if args.dtype == "f32" and args.refine == 0:
@@ -635,10 +675,10 @@ def main():
                "sample": f"one full decomposition of the {w.name} workload in FP64 NumPy (seeded Philox test matrices)"}
 
     launches = R.rhosvd_launch_count(dims, ranks, w.algo, w.p, w.q, K=w.K, S=w.S, dtype=args.dtype,
-                                     refine=args.refine)
+                                     refine=args.refine, kron=args.kron)
     if rank == 0:
         line = {
-            "metric": metric_name(w, args.dtype, args.refine), "value": value, "unit": UNIT, "n_gpus": world,
+            "metric": metric_name(w, args.dtype, args.refine, args.kron), "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": args.dtype,
             "data": "synthetic (seeded low-rank tensor, device-drawn Philox test matrices)",

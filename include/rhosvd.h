@@ -233,6 +233,32 @@ rhosvd_status rhosvd_decompose(const float* X, const rhosvd_shape* shape, const 
                                const float* const* Omega_tilde, float* const* U, float* G,
                                void* ws, size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------- fixed accuracy */
+
+/* Workspace bytes rhosvd_decompose_tol needs (0 on invalid input). */
+size_t rhosvd_workspace_size_tol(const rhosvd_shape* shape, int32_t block, const int32_t* k_max);
+
+/* Fixed-accuracy R-STHOSVD: Alg. 8 with a fixed-precision range finder in
+ * place of Alg. 1 (the rank-revealing randomized algorithms Sec. 5 cites for
+ * adaptive use), returning ranks chosen so that ||X - [[G; U]]||_F <= eps ||X||_F.
+ * Reading of the tolerance split (Eqs. DT1 / SubPro disagree): every mode gets
+ * tol = eps ||X||_F / sqrt(N).  Per mode, on the unfolding A of the current
+ * core: blocked randomized QB with an error indicator -- blocks of `block`
+ * Gaussian columns (block i of mode n drawn from (seed, stream_id 4096 +
+ * 256 n + i)), Y = A Omega_i - Q (B Omega_i), Q_i = orth(Y) re-orthogonalised
+ * against Q, B_i = Q_i^T A, E = ||A||^2 - sum ||B_i||^2, until E <= tol^2 or
+ * k_max[n] columns; then R_n = the smallest rank r (>= 1) whose truncated SVD
+ * of B keeps E + sum_{i > r} sigma_i^2 <= tol^2, U_n = Q Ubar_r, and the core
+ * shrinks to Ubar_r^T B.  U[n] must hold I_n x k_max[n] floats (ld I_n) and G
+ * prod k_max[n]; on return ranks[n] (host) holds R_n, U[n] its first R_n
+ * columns and G the R_1 x ... x R_N core.  1 <= k_max[n] <= min(I_n, 128),
+ * 0 < eps < 1, 1 <= block <= 128.  The ranks depend on the data: the call reads
+ * the indicator on the host after every block (it synchronises `stream` that
+ * often and returns when the work is done); it cannot be captured in a graph. */
+rhosvd_status rhosvd_decompose_tol(const float* X, const rhosvd_shape* shape, double eps, int32_t block,
+                                   const int32_t* k_max, uint64_t seed, int32_t* ranks, float* const* U,
+                                   float* G, void* ws, size_t ws_bytes, void* stream);
+
 /* Read the device status word kept at the start of `ws` with a copy ordered
  * on `stream`, wait for that stream (and no other), and return the first error
  * recorded there by earlier calls (RHOSVD_OK if none); `flags` (nullable)

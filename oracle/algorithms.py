@@ -285,6 +285,18 @@ def rpet(x: np.ndarray, ranks: Sequence[int], omegas: Sequence[np.ndarray],
     return g, us, {"Y": ys, "Q": qs, "H": h, "C": c}
 
 
+def kronecker_test_matrix(phis: Sequence[np.ndarray], n: int) -> np.ndarray:
+    """The structured test matrix of the memory-efficient sketch of Sec. 5.1:
+    Omega_n = Phi_N kron ... kron Phi_1 with Phi_n left out, in the reversed order
+    of the unfolding (Eq. "TuckerUnfold"), so that X_(n) Omega_n equals the
+    n-unfolding of X x_{p != n} Phi_p^T.  phis[p] is I_p x k_p."""
+    m = np.ones((1, 1))
+    for p in reversed(range(len(phis))):
+        if p != n:
+            m = np.kron(m, np.asarray(phis[p], dtype=np.float64))
+    return m
+
+
 def omega_shapes(algo: str, dims: Sequence[int], ranks: Sequence[int], p: int,
                  K: Sequence[int] | None = None, S: Sequence[int] | None = None):
     """Sizes (rows, cols) of the Gaussian test matrices each algorithm consumes.

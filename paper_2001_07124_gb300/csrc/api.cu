@@ -895,6 +895,131 @@ void run_refine(Ctx& c, const float* X, const Geom& g, const int32_t* ranks, con
   }
 }
 
+// ------------------------------------------------------------------ fixed accuracy
+
+// Reads n doubles from the device (stream-ordered) and waits for the stream.
+bool host_read(Ctx& c, const double* d, double* h, int n) {
+  if (cudaMemcpyAsync(h, d, sizeof(double) * n, cudaMemcpyDeviceToHost, c.s) != cudaSuccess) return false;
+  return cudaStreamSynchronize(c.s) == cudaSuccess;
+}
+
+// Fixed-accuracy R-STHOSVD: Alg. 8 with the blocked randomized QB with an
+// error indicator in place of Alg. 1 (the fixed-precision range finders Sec. 5
+// cites).  Per mode the tolerance is eps ||X||_F / sqrt(N), so that the
+// sequential truncation keeps the total error within eps ||X||_F.  For the
+// unfolding A = S_(n) of the current core the basis Q grows by blocks of b
+// columns: Y = A Omega_i - Q (B Omega_i), Q_i = orth(Y) re-orthogonalised once
+// against Q, B_i = Q_i^T A, and the indicator E = ||A||_F^2 - sum ||B_i||_F^2
+// (equal to ||A - Q B||_F^2) is read on the host after each block; the loop
+// stops at E <= tol^2 or kmax_n columns.  Then B = Ubar Sigma Vbar^T through
+// the eigenvectors of B B^T, R_n = the smallest r with E + sum_{i>r} sigma_i^2
+// <= tol^2 (at least 1), U_n = Q Ubar_R and S_(n) <- Ubar_R^T B.  Block i of
+// mode n is drawn on stream_id 4096 + 256 n + i.  A dry run (sizing) takes every
+// block and keeps kmax_n columns.
+rhosvd_status run_fixed_accuracy(Ctx& c, const float* X, const Geom& g0, double eps, int block,
+                                 const int32_t* kmax, uint64_t seed, int32_t* ranks_out, float* const* U,
+                                 float* G) {
+  const int N = g0.N;
+  size_t max_s = 1, max_q = 1, max_bt = 1, max_om = 1, max_kk = 1;
+  {
+    Geom g = g0;
+    for (int n = 0; n < N; ++n) {
+      const int64_t J = g.J(n);
+      max_q = std::max<size_t>(max_q, (size_t)g.d[n] * kmax[n]);
+      max_bt = std::max<size_t>(max_bt, (size_t)J * kmax[n]);
+      max_om = std::max<size_t>(max_om, (size_t)J * block);
+      max_kk = std::max<size_t>(max_kk, (size_t)ldu_of(kmax[n]) * kmax[n]);
+      g.d[n] = kmax[n];
+      max_s = std::max<size_t>(max_s, (size_t)g.numel());
+    }
+  }
+  float* Qb = c.take<float>(max_q);
+  float* Bt = c.take<float>(max_bt);
+  float* Om = c.take<float>(max_om);
+  float* Cm = c.take<float>((size_t)RHOSVD_MAX_K * block);
+  float* Tmp = c.take<float>(max_q);
+  float* Ub = c.take<float>(max_kk);
+  float* sv = c.take<float>(RHOSVD_MAX_K);
+  double* Gd = c.take<double>((size_t)RHOSVD_MAX_K * RHOSVD_MAX_K);
+  float* Sb[2] = {c.take<float>(max_s), c.take<float>(max_s)};
+  Geom g = g0;
+  const float* cur = X;
+  int ping = 0;
+  double tol2 = 0.0;
+  for (int n = 0; n < N; ++n) {
+    const int64_t I = g.d[n], L = g.L(n), J = g.J(n);
+    const View av = mode_view(cur, g, n);
+    // ||A||_F^2 of the current core (a one-column Gram)
+    op_gram_matrix(c, cur, g.numel(), 1, g.numel(), Gd);
+    double e = 0.0;
+    if (!c.dry && !host_read(c, Gd, &e, 1)) return RHOSVD_ECUDA;
+    if (n == 0) tol2 = eps * eps * e / N;
+    int kq = 0;
+    for (int i = 0; kq < kmax[n]; ++i) {
+      if (!c.dry && e <= tol2) break;
+      const int b = std::min(block, kmax[n] - kq);
+      float* Y = Qb + (size_t)kq * I;
+      op_omega(c, seed, (uint32_t)(4096 + 256 * n + i), J, b, Om);
+      op_sketch(c, av, WView{Om, L, J}, b, Y, I);                            // A Omega_i
+      if (kq > 0) {
+        // Y -= Q (B Omega_i), B Omega_i = Bt^T Omega_i (kq x b)
+        View btv{Bt, J, kq, 1, J, J * kq};
+        op_sketch(c, btv, WView{Om, J, J}, b, Cm, kq);
+        op_ttm(c, matrix_view(Qb, I, kq, I), Cm, 1, kq, b, OView{Tmp, I, 0});
+        c.launches += 1;
+        if (!c.dry) c.check(launch_axpy(Y, Tmp, -1.f, I * (int64_t)b, c.s));
+      }
+      op_orth(c, Y, I, b, I);
+      if (kq > 0) {                                                           // once more against Q
+        View qv{Qb, I, kq, 1, I, I * kq};
+        op_sketch(c, qv, WView{Y, I, I}, b, Cm, kq);                          // Q^T Q_i
+        op_ttm(c, matrix_view(Qb, I, kq, I), Cm, 1, kq, b, OView{Tmp, I, 0});
+        c.launches += 1;
+        if (!c.dry) c.check(launch_axpy(Y, Tmp, -1.f, I * (int64_t)b, c.s));
+        op_orth(c, Y, I, b, I);
+      }
+      op_ttm(c, av, Y, 1, I, b, OView{Bt + (size_t)kq * J, J, L});           // B_i^T = A^T Q_i
+      op_gram_matrix(c, Bt + (size_t)kq * J, J * (int64_t)b, 1, J * (int64_t)b, Gd);
+      double bb = 0.0;
+      if (!c.dry && !host_read(c, Gd, &bb, 1)) return RHOSVD_ECUDA;
+      e -= bb;
+      kq += b;
+    }
+    if (kq == 0) kq = 1;                       // rank 0 is not representable: keep one direction
+    // truncation: eigenvectors of B B^T (all kq, descending) and the rank
+    op_gram_matrix(c, Bt, J, kq, J, Gd);
+    c.launches += 1;
+    if (!c.dry) c.check(launch_small_eig(Gd, kq, kq, Ub, ldu_of(kq), sv, c.st, c.s));
+    int r = kq;
+    if (!c.dry) {
+      float hs[RHOSVD_MAX_K];
+      if (cudaMemcpyAsync(hs, sv, sizeof(float) * kq, cudaMemcpyDeviceToHost, c.s) != cudaSuccess ||
+          cudaStreamSynchronize(c.s) != cudaSuccess)
+        return RHOSVD_ECUDA;
+      // smallest r with E + sum_{i >= r} sigma_i^2 <= tol^2 (0-based), tail[r] the suffix sums
+      double tail[RHOSVD_MAX_K + 1];
+      tail[kq] = 0.0;
+      for (int t = kq - 1; t >= 0; --t) tail[t] = tail[t + 1] + (double)hs[t] * hs[t];
+      const double res = std::max(e, 0.0);
+      r = kq;
+      for (int t = 0; t <= kq; ++t)
+        if (res + tail[t] <= tol2) {
+          r = t;
+          break;
+        }
+      r = std::max(r, 1);
+    }
+    lift_factor(c, Qb, I, kq, Ub, r, U[n]);
+    float* dst = (n == N - 1) ? G : Sb[ping];
+    refold_core(c, Bt, g, n, kq, Ub, r, dst);
+    g.d[n] = r;
+    ranks_out[n] = r;
+    cur = dst;
+    ping ^= 1;
+  }
+  return RHOSVD_OK;
+}
+
 rhosvd_status finish(const Ctx& c) { return c.err == cudaSuccess ? RHOSVD_OK : RHOSVD_ECUDA; }
 
 rhosvd_status begin(Ctx& c, void* ws, size_t ws_bytes, void* stream) {
@@ -1199,6 +1324,46 @@ rhosvd_status rhosvd_decompose(const float* X, const rhosvd_shape* shape, const 
   else if (opts->algo == RHOSVD_ALGO_RHOSVD) run_rhosvd(c, X, g, ranks, pl, opts->q, opts->seed, Omega, U, G);
   else run_rpet(c, X, g, ranks, pl, opts->seed, Omega, Omega_tilde, U, G);
   run_refine(c, X, g, ranks, pl, opts->seed, U, G);
+  return finish(c);
+}
+
+static rhosvd_status validate_tol(const rhosvd_shape* shape, double eps, int32_t block, const int32_t* k_max,
+                                  Geom& g) {
+  rhosvd_status s = validate_shape(shape, g);
+  if (s != RHOSVD_OK) return s;
+  if (!(eps > 0.0 && eps < 1.0) || block < 1 || block > RHOSVD_MAX_K || k_max == nullptr) return RHOSVD_EINVAL;
+  Geom t = g;
+  for (int n = 0; n < g.N; ++n) {
+    if (k_max[n] < 1 || k_max[n] > RHOSVD_MAX_K || k_max[n] > g.d[n] || k_max[n] > t.J(n)) return RHOSVD_EINVAL;
+    t.d[n] = k_max[n];
+  }
+  return RHOSVD_OK;
+}
+
+size_t rhosvd_workspace_size_tol(const rhosvd_shape* shape, int32_t block, const int32_t* k_max) {
+  Geom g;
+  if (validate_tol(shape, 0.5, block, k_max, g) != RHOSVD_OK) return 0;
+  Ctx c = dry_ctx();
+  int32_t r[RHOSVD_MAX_MODES];
+  float* U[RHOSVD_MAX_MODES] = {nullptr};
+  run_fixed_accuracy(c, nullptr, g, 0.5, block, k_max, 0, r, U, nullptr);
+  return c.high;
+}
+
+rhosvd_status rhosvd_decompose_tol(const float* X, const rhosvd_shape* shape, double eps, int32_t block,
+                                   const int32_t* k_max, uint64_t seed, int32_t* ranks, float* const* U, float* G,
+                                   void* ws, size_t ws_bytes, void* stream) {
+  Geom g;
+  rhosvd_status s = validate_tol(shape, eps, block, k_max, g);
+  if (s != RHOSVD_OK) return s;
+  if (X == nullptr || ranks == nullptr || U == nullptr || G == nullptr) return RHOSVD_EINVAL;
+  for (int n = 0; n < g.N; ++n)
+    if (U[n] == nullptr) return RHOSVD_EINVAL;
+  if (ws_bytes < rhosvd_workspace_size_tol(shape, block, k_max)) return RHOSVD_ENOMEM;
+  Ctx c;
+  if ((s = begin(c, ws, ws_bytes, stream)) != RHOSVD_OK) return s;
+  s = run_fixed_accuracy(c, X, g, eps, block, k_max, seed, ranks, U, G);
+  if (s != RHOSVD_OK) return s;
   return finish(c);
 }
 

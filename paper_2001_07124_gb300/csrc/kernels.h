@@ -168,6 +168,8 @@ cudaError_t launch_small_eig(const double* G, int K, int R, float* Ub, int ldu, 
 cudaError_t launch_transpose(const float* in, int64_t rows, int64_t cols, int64_t ld, float* out,
                              cudaStream_t st);
 cudaError_t launch_fill_identity(float* U, int64_t I, int R, cudaStream_t st);
+// y += a x (n elements)
+cudaError_t launch_axpy(float* y, const float* x, float a, int64_t n, cudaStream_t st);
 // out (I x L*Rt, column-major) = mode unfolding of in viewed as [L, I, Rt]
 cudaError_t launch_unfold(const float* in, int64_t L, int64_t I, int64_t Rt, float* out, cudaStream_t st);
 

@@ -32,6 +32,21 @@ __global__ void transpose_kernel(const float* __restrict__ in, int64_t rows, int
   out[c + r * cols] = in[r + c * ld];
 }
 
+// out (I x L*Rt, column-major) = the unfolding of in viewed as [L, I, Rt]:
+// out[i + I (l + L r)] = in[l + L (i + I r)]
+__global__ void unfold_kernel(const float* __restrict__ in, int64_t L, int64_t I, int64_t Rt,
+                              float* __restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // index into in (coalesced reads)
+  if (e >= L * I * Rt) return;
+  const int64_t l = e % L, t = e / L, i = t % I, r = t / I;
+  out[i + I * (l + L * r)] = in[e];
+}
+
+__global__ void axpy_kernel(float* __restrict__ y, const float* __restrict__ x, float a, int64_t n) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) y[e] = fmaf(a, x[e], y[e]);
+}
+
 __global__ void fill_identity_kernel(float* U, int64_t I, int R) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= I * R) return;
@@ -54,6 +69,19 @@ cudaError_t launch_transpose(const float* in, int64_t rows, int64_t cols, int64_
   const int64_t n = rows * cols;
   if (n == 0) return cudaSuccess;
   transpose_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, rows, cols, ld, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unfold(const float* in, int64_t L, int64_t I, int64_t Rt, float* out, cudaStream_t st) {
+  const int64_t n = L * I * Rt;
+  if (n == 0) return cudaSuccess;
+  unfold_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(in, L, I, Rt, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(float* y, const float* x, float a, int64_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  axpy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y, x, a, n);
   return cudaGetLastError();
 }
 

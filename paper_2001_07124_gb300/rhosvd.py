@@ -91,6 +91,9 @@ def lib() -> ctypes.CDLL:
         "rhosvd_decompose": (st, [_P, ctypes.POINTER(Shape), _I32P, ctypes.POINTER(Opts), _PP, _PP, _PP, _P,
                                   _P, ctypes.c_size_t, _P]),
         "rhosvd_device_status": (st, [_P, ctypes.c_size_t, _P, _I32P]),
+        "rhosvd_workspace_size_tol": (ctypes.c_size_t, [ctypes.POINTER(Shape), ctypes.c_int32, _I32P]),
+        "rhosvd_decompose_tol": (st, [_P, ctypes.POINTER(Shape), ctypes.c_double, ctypes.c_int32, _I32P,
+                                      ctypes.c_uint64, _I32P, _PP, _P, _P, ctypes.c_size_t, _P]),
         "rhosvd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
@@ -550,6 +553,40 @@ class BatchGraph:
             code, _ = rhosvd_device_status(ws)
             worst = worst or code
         return worst
+
+
+def rhosvd_workspace_size_tol(dims, block, k_max) -> int:
+    return int(lib().rhosvd_workspace_size_tol(ctypes.byref(make_shape(dims)), int(block), _i32(k_max)))
+
+
+def rhosvd_decompose_tol(X, dims, eps, block=8, k_max=None, seed=0, ws=None, out=None, stream=None, check=True):
+    """Fixed-accuracy R-STHOSVD: returns (G as an (R_1..R_N) view, [U_n as (I_n, R_n) views], ranks).
+    Synchronises the stream after every block of the range finder."""
+    X = colmajor(X, dims)
+    N = len(dims)
+    k_max = [min(int(d), MAX_K) for d in dims] if k_max is None else [int(k) for k in k_max]
+    if out is None:
+        G = empty_colmajor(k_max)
+        Us = [empty_colmajor((dims[n], k_max[n])) for n in range(N)]
+    else:
+        G, Us = out
+    need = rhosvd_workspace_size_tol(dims, block, k_max)
+    if need == 0:
+        _check(1, "rhosvd_workspace_size_tol")
+    own_ws = ws is None
+    ws = _ws_for(ws, need)
+    ranks = (ctypes.c_int32 * N)()
+    _check(lib().rhosvd_decompose_tol(_dptr(X), ctypes.byref(make_shape(dims)), float(eps), int(block),
+                                      _i32(k_max), int(seed) & 0xFFFFFFFFFFFFFFFF, ranks, _ptrs(Us), _dptr(G),
+                                      ws.ptr, ws.nbytes, _stream(stream)), "rhosvd_decompose_tol")
+    r = [int(v) for v in ranks]
+    if own_ws:
+        _hold(stream, ws.buf)
+    if check:
+        dev, _ = rhosvd_device_status(ws, stream)
+        _check(dev, "rhosvd_decompose_tol (device)")
+    ng = int(np.prod(r))
+    return fortran_view(G[:ng], r), [matrix(Us[n][:dims[n] * r[n]], dims[n], r[n]) for n in range(N)], r
 
 
 def rhosvd_device_status(ws, stream=None):

@@ -145,3 +145,24 @@ def test_rp_hooi_refines_a_single_pass_result():
     # the core of the sweep is the projection of X onto its factors
     from oracle import tensor as T
     assert np.allclose(g1, T.multi_ttm(x, u1, transpose=True), atol=1e-12 * np.linalg.norm(x))
+
+
+def test_kronecker_test_matrix_is_the_mode_product_sketch():
+    """X_(n) (Phi_N kron ... kron Phi_1, without Phi_n) equals the n-unfolding of
+    X x_{p != n} Phi_p^T, computed by mode products; the forward Kronecker order
+    does not (a transposed ordering is caught)."""
+    from oracle import tensor as T
+    rng = np.random.default_rng(9)
+    dims, k = (5, 4, 3, 6), 2
+    x = rng.standard_normal(dims)
+    phis = [rng.standard_normal((d, k)) for d in dims]
+    for n in range(4):
+        om = A.kronecker_test_matrix(phis, n)
+        assert om.shape == (int(np.prod(dims)) // dims[n], k ** 3)
+        via_ttm = T.unfold(T.multi_ttm(x, [None if p == n else phis[p].T for p in range(4)]), n)
+        assert np.allclose(T.unfold(x, n) @ om, via_ttm, atol=1e-12)
+        fwd = np.ones((1, 1))
+        for p in range(4):
+            if p != n:
+                fwd = np.kron(fwd, phis[p])
+        assert not np.allclose(T.unfold(x, n) @ fwd, via_ttm, atol=1e-6)
