@@ -246,8 +246,13 @@ size_t rhosvd_workspace_size_tol(const rhosvd_shape* shape, int32_t block, const
  * core: blocked randomized QB with an error indicator -- blocks of `block`
  * Gaussian columns (block i of mode n drawn from (seed, stream_id 4096 +
  * 256 n + i)), Y = A Omega_i - Q (B Omega_i), Q_i = orth(Y) re-orthogonalised
- * against Q, B_i = Q_i^T A, E = ||A||^2 - sum ||B_i||^2, until E <= tol^2 or
- * k_max[n] columns; then R_n = the smallest rank r (>= 1) whose truncated SVD
+ * against Q, B_i = Q_i^T A (FP32 FMA arithmetic, rounded to nearest: the
+ * tensor cores' truncating accumulation would leave B ~5e-7 low and E with an
+ * error ~1e-6 ||A||^2), E = ||A||^2 - ||P_Q A||^2 (= ||A - Q B||^2), with the
+ * projected energy tr((Q^T Q)^-1 B B^T) taken to first order in Q^T Q - I (the
+ * FP32 Q is orthonormal to ~1e-6, which the plain sum ||B_i||^2 would carry
+ * into E as an error ~1e-6 ||A||^2), until E <= tol^2 (after at least one
+ * block) or k_max[n] columns; then R_n = the smallest rank r (>= 1) whose truncated SVD
  * of B keeps E + sum_{i > r} sigma_i^2 <= tol^2, U_n = Q Ubar_r, and the core
  * shrinks to Ubar_r^T B.  U[n] must hold I_n x k_max[n] floats (ld I_n) and G
  * prod k_max[n]; on return ranks[n] (host) holds R_n, U[n] its first R_n

@@ -247,6 +247,13 @@ def rsthosvd_fixed_accuracy(x: np.ndarray, eps: float, block: int, k_max: Sequen
             ubar, sig, _ = np.linalg.svd(bm, full_matrices=False)
             r = truncation_rank(sig, max(e, 0.0), tol)
         u = qm @ ubar[:, :r] if r > 0 else np.zeros((a.shape[0], 0))
+        if r > 0:
+            # sign convention: each factor column's largest-magnitude entry positive
+            # (factors are defined up to column signs; the later modes sketch the core
+            # in this mode's coordinates, so the convention fixes their test matrices)
+            flip = np.where(u[np.argmax(np.abs(u), axis=0), np.arange(r)] < 0, -1.0, 1.0)
+            u = u * flip
+            ubar = ubar[:, :r] * flip
         sn = ubar[:, :r].T @ bm if r > 0 else np.zeros((0, a.shape[1]))
         dims = list(s.shape)
         dims[n] = r

@@ -243,13 +243,10 @@ bool lp_ttm1(Ctx& c, const LpCopy& lp, const Geom& g, const float* M, int64_t ld
   return true;
 }
 
-// The seeded test matrix of (seed, stream_id), rounded to the copy's format.
+// The seeded test matrix of (seed, stream_id), rounded to the copy's format as it is drawn.
 void lp_omega(Ctx& c, const LpCopy& lp, uint64_t seed, uint32_t stream_id, int64_t rows, int cols, float* out) {
-  c.launches += 2;
-  if (!c.dry) {
-    c.check(launch_omega(seed, stream_id, rows, cols, out, rows, c.s));
-    c.check(launch_round_to_format(out, rows * (int64_t)cols, lp.eb, c.s));
-  }
+  c.launches += 1;
+  if (!c.dry) c.check(launch_omega_rounded(seed, stream_id, rows, cols, out, rows, lp.eb, c.s));
 }
 
 // ------------------------------------------------------------------ Alg. 1 on one mode
@@ -282,7 +279,7 @@ void alg1_mode(Ctx& c, const float* x, const Geom& g, int n, int K, int R, int q
   for (int it = 0; it < q; ++it) {
     if (!(use_lp && lp_ttm1(c, *lp, g, Yb, I, K, Zb, J, 1)))
       op_ttm(c, xv, Yb, 1, I, K, zo);                    // Z = X_(n)^T Q
-    op_orth(c, Zb, J, K, J, 1);                          // Z = orth(Z)
+    op_orth(c, Zb, J, K, J, 1);                          // Z = orth(X_(n)^T Q)
     if (!(use_lp && lp_sketch(c, *lp, g, n, Zb, K, Yb)))
       op_sketch(c, xv, WView{Zb, L, J}, K, Yb, I);       // Y = X_(n) Z
     op_orth(c, Yb, I, K, I, it + 1 < q ? 1 : 2);         // Q = orth(Y)
@@ -545,17 +542,24 @@ void core_sketch_chain(Ctx& c, const float* X, const Geom& g, const int* S, uint
 // R-PET's sketches with Kronecker-structured factor test matrices (the
 // memory-efficient form of Sec. 5.1): Y_n = (X x_{p != n} Phi_p^T)_(n) =
 // X_(n) (Phi_N x ... x Phi_1, without Phi_n), Phi_p Gaussian I_p x k, and the
-// core sketch H = X x_1 Omega~_1 ... x_N Omega~_N, from two reads of X:
-//   * C = X x_N [Omega~_N^T Phi_N]: its first S_N slices along the last mode
-//     are X x_N Omega~_N (the core sketch's first product), the last k are
-//     X x_N Phi_N^T, which every Y_n with n < N reduces further;
-//   * E = X x_1 Phi_1^T, which Y_N reduces further.
-// The products after the first act on tensors k / I_p (or S_N / I_N) of X's size.
+// core sketch H = X x_1 Omega~_1 ... x_N Omega~_N, from two reads of X, both
+// in layouts the TMA streams at full rate:
+//   * C = X x_1 [Omega~_1^T Phi_1], written column-major in (j, s): its first
+//     S_1 columns are the tensor X x_1 Omega~_1 with mode 1 moved last
+//     (I_2 x ... x I_N x S_1), the last k columns X x_1 Phi_1^T likewise; the
+//     core chain reduces the first part (H comes out with S_1 last and is
+//     transposed once), every Y_n with n > 1 reduces the second;
+//   * E = X x_2 Phi_2^T, which Y_1 reduces further.
+// Y_n with n > 1 comes out with its columns in a permuted order (Phi_1's
+// index slowest); a column permutation leaves range(Y_n), and so R-PET's
+// result, unchanged.  The products after the first act on tensors k / I_p
+// (or S_1 / I_1) of X's size.
 void rpet_kron_sketches(Ctx& c, const float* X, const Geom& g, const Plan& pl, uint64_t seed,
                         const float* const* Omega, const float* const* Omega_t, float* const* Omt,
                         float* const* Ys, float* H) {
-  const int N = g.N, k = pl.kron, last = N - 1;
-  const int SN = pl.S[last];
+  const int N = g.N, k = pl.kron;
+  const int S0 = pl.S[0];
+  const int64_t J0 = g.J(0);
   Scope sc(c);
   // Phi_p (I_p x k), explicit or drawn on stream_id 10N + p
   const float* Phi[RHOSVD_MAX_MODES];
@@ -568,106 +572,120 @@ void rpet_kron_sketches(Ctx& c, const float* X, const Geom& g, const Plan& pl, u
       Phi[p] = f;
     }
   }
-  // the core sketch's test matrices Omega~_n (S_n x I_n), drawn unless explicit
   for (int n = 0; n < N; ++n)
     if (Omt[n] != nullptr) op_omega(c, seed, (uint32_t)(N + n), pl.S[n], (int)g.d[n], Omt[n]);
   auto omt = [&](int n) { return (Omega_t != nullptr && Omega_t[n] != nullptr) ? Omega_t[n] : Omt[n]; };
-  // chain buffers: the largest intermediate of any of the reductions below
+  // T: X's modes 2..N at positions 0..N-2, then the first product's index
+  Geom tg;
+  tg.N = N;
+  for (int q = 0; q + 1 < N; ++q) tg.d[q] = g.d[q + 1];
   size_t max_t = 1, max_m = 1;
   {
-    Geom t = g;
-    t.d[last] = SN;
-    for (int p = 0; p < last; ++p) {
-      t.d[p] = pl.S[p];
+    Geom t = tg;
+    t.d[N - 1] = S0;
+    for (int q = 0; q + 1 < N; ++q) {
+      t.d[q] = pl.S[q + 1];
       max_t = std::max<size_t>(max_t, (size_t)t.numel());
     }
     for (int n = 0; n < N; ++n) max_m = std::max<size_t>(max_m, (size_t)g.d[n] * std::max(pl.S[n], k));
     // a factor chain only shrinks its start (k <= I_p), so its intermediates are
-    // bounded by X x_N Phi_N^T or X x_1 Phi_1^T
-    max_t = std::max<size_t>(max_t, (size_t)g.L(last) * k);
-    max_t = std::max<size_t>(max_t, (size_t)g.J(0) * k);
+    // bounded by X x_1 Phi_1^T or X x_2 Phi_2^T
+    max_t = std::max<size_t>(max_t, (size_t)J0 * k);
+    max_t = std::max<size_t>(max_t, (size_t)g.J(N > 1 ? 1 : 0) * k);
   }
-  const int64_t LN = g.L(last);
-  float* Mc = c.take<float>((size_t)g.d[last] * (SN + k));
-  float* C = c.take<float>((size_t)LN * (SN + k));
-  float* E = c.take<float>((size_t)g.J(0) * k);
+  float* Mc = c.take<float>((size_t)g.d[0] * (S0 + k));
+  float* C = c.take<float>((size_t)J0 * (S0 + k));
+  float* E = c.take<float>((size_t)g.J(1) * k);
+  float* Hp = c.take<float>((size_t)max_t);
   float* Tb[2] = {c.take<float>(max_t), c.take<float>(max_t)};
   float* Mt = c.take<float>(max_m);
   size_t max_w = 1;
   for (int n = 0; n < N; ++n) max_w = std::max<size_t>(max_w, (size_t)g.d[n] * pl.K[n]);
   float* Wn = c.take<float>(max_w);
-  // read 1: C = X x_N [Omega~_N^T Phi_N]
+  // read 1: C(j, s) = (X x_1 [Omega~_1^T Phi_1])(s, j), column-major in (j, s)
   c.launches += 1;
   if (!c.dry) {
-    c.check(launch_transpose(omt(last), SN, g.d[last], SN, Mc, c.s));
-    c.check(cudaMemcpyAsync(Mc + (size_t)g.d[last] * SN, Phi[last], sizeof(float) * g.d[last] * k,
+    c.check(launch_transpose(omt(0), S0, g.d[0], S0, Mc, c.s));
+    c.check(cudaMemcpyAsync(Mc + (size_t)g.d[0] * S0, Phi[0], sizeof(float) * g.d[0] * k,
                             cudaMemcpyDeviceToDevice, c.s));
   }
-  ttm_mode(c, X, g, last, Mc, 1, g.d[last], SN + k, C);
-  // chain src (geometry t) x_p M_p for the listed modes, the last product into dst
-  auto chain = [&](const float* src, Geom t, const int* modes, int nm, bool core, float* dst) -> Geom {
+  op_ttm(c, mode_view(X, g, 0), Mc, 1, g.d[0], S0 + k, OView{C, J0, 1});
+  // chain src (geometry t) over the listed (position, X mode) pairs; the last product into dst
+  auto chain = [&](const float* src, Geom t, const int* pos, const int* xm, int nm, bool core,
+                   float* dst) -> Geom {
     const float* cur = src;
     int ping = 0;
     for (int q = 0; q < nm; ++q) {
-      const int p = modes[q];
-      const int width = core ? pl.S[p] : k;
-      const float* M = Phi[p];
-      if (core) {                                  // the TTM takes Omega~_p^T (I_p x S_p)
+      const int p = pos[q], m = xm[q];
+      const int width = core ? pl.S[m] : k;
+      const float* M = Phi[m];
+      if (core) {                                  // the TTM takes Omega~_m^T (I_m x S_m)
         c.launches += 1;
-        if (!c.dry) c.check(launch_transpose(omt(p), pl.S[p], g.d[p], pl.S[p], Mt, c.s));
+        if (!c.dry) c.check(launch_transpose(omt(m), pl.S[m], g.d[m], pl.S[m], Mt, c.s));
         M = Mt;
       }
       float* out = (q == nm - 1) ? dst : Tb[ping];
-      ttm_mode(c, cur, t, p, M, 1, g.d[p], width, out);
+      ttm_mode(c, cur, t, p, M, 1, g.d[m], width, out);
       t.d[p] = width;
       cur = out;
       ping ^= 1;
     }
     return t;
   };
-  // core sketch H = (X x_N Omega~_N) x_1 Omega~_1 ... x_{N-1} Omega~_{N-1}
-  {
-    Geom t = g;
-    t.d[last] = SN;
-    int modes[RHOSVD_MAX_MODES], nm = 0;
-    for (int p = 0; p < last; ++p) modes[nm++] = p;
-    if (nm == 0) {
-      if (!c.dry) c.check(cudaMemcpyAsync(H, C, sizeof(float) * LN * SN, cudaMemcpyDeviceToDevice, c.s));
-    } else {
-      chain(C, t, modes, nm, true, H);
-    }
-  }
-  // factor sketch of mode n, as the unfolding of the reduced tensor
-  auto emit = [&](const float* red, const Geom& t, int n) {
+  auto emit = [&](const float* red, const Geom& t, int p, int n) {   // Y_n = unfolding at position p
     c.launches += 1;
-    if (!c.dry) c.check(launch_unfold(red, t.L(n), t.d[n], t.Rt(n), Ys[n], c.s));
+    if (!c.dry) c.check(launch_unfold(red, t.L(p), t.d[p], t.Rt(p), Ys[n], c.s));
   };
-  const float* CF = C + (size_t)LN * SN;         // X x_N Phi_N^T
-  for (int n = 0; n < last; ++n) {
-    Geom t = g;
-    t.d[last] = k;
-    int modes[RHOSVD_MAX_MODES], nm = 0;
-    for (int p = 0; p < last; ++p)
-      if (p != n) modes[nm++] = p;
+  int pos[RHOSVD_MAX_MODES], xm[RHOSVD_MAX_MODES], nm;
+  // core sketch: H' = (X x_1 Omega~_1) x_2 Omega~_2 ... (S_2 x ... x S_N x S_1), then H = H'^T
+  {
+    Geom t = tg;
+    t.d[N - 1] = S0;
+    nm = 0;
+    for (int q = 0; q + 1 < N; ++q) {
+      pos[nm] = q;
+      xm[nm++] = q + 1;
+    }
+    const int64_t rest = t.numel() / S0;
+    int64_t hrest = 1;
+    for (int q = 1; q < N; ++q) hrest *= pl.S[q];
+    if (nm > 0) chain(C, t, pos, xm, nm, true, Hp);
+    c.launches += 1;
+    if (!c.dry) c.check(launch_transpose(nm > 0 ? Hp : C, nm > 0 ? hrest : rest, S0, nm > 0 ? hrest : rest, H, c.s));
+  }
+  // factor sketches of modes 2..N from X x_1 Phi_1^T (mode n at position n - 1)
+  const float* CF = C + (size_t)J0 * S0;
+  for (int n = 1; n < N; ++n) {
+    Geom t = tg;
+    t.d[N - 1] = k;
+    nm = 0;
+    for (int q = 0; q + 1 < N; ++q)
+      if (q != n - 1) {
+        pos[nm] = q;
+        xm[nm++] = q + 1;
+      }
     if (nm == 0) {
-      emit(CF, t, n);
+      emit(CF, t, n - 1, n);
     } else {
-      const Geom r = chain(CF, t, modes, nm, false, Wn);
-      emit(Wn, r, n);
+      const Geom r = chain(CF, t, pos, xm, nm, false, Wn);
+      emit(Wn, r, n - 1, n);
     }
   }
-  // read 2: E = X x_1 Phi_1^T, then Y_N
-  ttm_mode(c, X, g, 0, Phi[0], 1, g.d[0], k, E);
+  // read 2: E = X x_2 Phi_2^T, then Y_1
+  ttm_mode(c, X, g, 1, Phi[1], 1, g.d[1], k, E);
   {
     Geom t = g;
-    t.d[0] = k;
-    int modes[RHOSVD_MAX_MODES], nm = 0;
-    for (int p = 1; p < last; ++p) modes[nm++] = p;
+    t.d[1] = k;
+    nm = 0;
+    for (int p = 2; p < N; ++p) {
+      pos[nm] = p;
+      xm[nm++] = p;
+    }
     if (nm == 0) {
-      emit(E, t, last);
+      emit(E, t, 0, 0);
     } else {
-      const Geom r = chain(E, t, modes, nm, false, Wn);
-      emit(Wn, r, last);
+      const Geom r = chain(E, t, pos, xm, nm, false, Wn);
+      emit(Wn, r, 0, 0);
     }
   }
   for (int n = 0; n < N; ++n) op_orth(c, Ys[n], g.d[n], pl.K[n], g.d[n]);
@@ -909,9 +927,11 @@ bool host_read(Ctx& c, const double* d, double* h, int n) {
 // sequential truncation keeps the total error within eps ||X||_F.  For the
 // unfolding A = S_(n) of the current core the basis Q grows by blocks of b
 // columns: Y = A Omega_i - Q (B Omega_i), Q_i = orth(Y) re-orthogonalised once
-// against Q, B_i = Q_i^T A, and the indicator E = ||A||_F^2 - sum ||B_i||_F^2
-// (equal to ||A - Q B||_F^2) is read on the host after each block; the loop
-// stops at E <= tol^2 or kmax_n columns.  Then B = Ubar Sigma Vbar^T through
+// against Q, B_i = Q_i^T A, and the indicator E = ||A||_F^2 - ||P_Q A||_F^2
+// (equal to ||A - Q B||_F^2; the projected energy tr((Q^T Q)^-1 B B^T) to first
+// order in Q^T Q - I, which for an exactly orthonormal Q is sum ||B_i||_F^2) is
+// read on the host after each block; the loop stops at E <= tol^2 (after at
+// least one block) or kmax_n columns.  Then B = Ubar Sigma Vbar^T through
 // the eigenvectors of B B^T, R_n = the smallest r with E + sum_{i>r} sigma_i^2
 // <= tol^2 (at least 1), U_n = Q Ubar_R and S_(n) <- Ubar_R^T B.  Block i of
 // mode n is drawn on stream_id 4096 + 256 n + i.  A dry run (sizing) takes every
@@ -940,7 +960,9 @@ rhosvd_status run_fixed_accuracy(Ctx& c, const float* X, const Geom& g0, double 
   float* Tmp = c.take<float>(max_q);
   float* Ub = c.take<float>(max_kk);
   float* sv = c.take<float>(RHOSVD_MAX_K);
-  double* Gd = c.take<double>((size_t)RHOSVD_MAX_K * RHOSVD_MAX_K);
+  double* Gd = c.take<double>((size_t)RHOSVD_MAX_K * RHOSVD_MAX_K);   // C = B B^T
+  double* Gq = c.take<double>((size_t)RHOSVD_MAX_K * RHOSVD_MAX_K);   // M = Q^T Q
+  double* pe = c.take<double>(1);
   float* Sb[2] = {c.take<float>(max_s), c.take<float>(max_s)};
   Geom g = g0;
   const float* cur = X;
@@ -951,12 +973,13 @@ rhosvd_status run_fixed_accuracy(Ctx& c, const float* X, const Geom& g0, double 
     const View av = mode_view(cur, g, n);
     // ||A||_F^2 of the current core (a one-column Gram)
     op_gram_matrix(c, cur, g.numel(), 1, g.numel(), Gd);
-    double e = 0.0;
-    if (!c.dry && !host_read(c, Gd, &e, 1)) return RHOSVD_ECUDA;
-    if (n == 0) tol2 = eps * eps * e / N;
+    double a2 = 0.0;
+    if (!c.dry && !host_read(c, Gd, &a2, 1)) return RHOSVD_ECUDA;
+    if (n == 0) tol2 = eps * eps * a2 / N;
+    double e = a2;
     int kq = 0;
     for (int i = 0; kq < kmax[n]; ++i) {
-      if (!c.dry && e <= tol2) break;
+      if (!c.dry && kq > 0 && e <= tol2) break;
       const int b = std::min(block, kmax[n] - kq);
       float* Y = Qb + (size_t)kq * I;
       op_omega(c, seed, (uint32_t)(4096 + 256 * n + i), J, b, Om);
@@ -978,16 +1001,24 @@ rhosvd_status run_fixed_accuracy(Ctx& c, const float* X, const Geom& g0, double 
         if (!c.dry) c.check(launch_axpy(Y, Tmp, -1.f, I * (int64_t)b, c.s));
         op_orth(c, Y, I, b, I);
       }
-      op_ttm(c, av, Y, 1, I, b, OView{Bt + (size_t)kq * J, J, L});           // B_i^T = A^T Q_i
-      op_gram_matrix(c, Bt + (size_t)kq * J, J * (int64_t)b, 1, J * (int64_t)b, Gd);
-      double bb = 0.0;
-      if (!c.dry && !host_read(c, Gd, &bb, 1)) return RHOSVD_ECUDA;
-      e -= bb;
+      // B_i^T = A^T Q_i by the FP32 FMA TTM (round to nearest): the tensor cores'
+      // truncating accumulation leaves B ~5e-7 low, which E would carry as
+      // ~1e-6 ||A||^2 and so could not resolve eps below ~2e-3
+      c.launches += 1;
+      if (!c.dry) c.check(launch_ttm(av, Y, 1, I, b, OView{Bt + (size_t)kq * J, J, L}, nullptr, c.s));
       kq += b;
+      // E = ||A||^2 - ||P_Q A||^2, the projected energy from M = Q^T Q and
+      // C = B B^T: Q is orthonormal only to FP32 storage (||Q^T Q - I|| ~ 1e-6),
+      // which in ||A||^2 - sum ||B_i||^2 would leave an error ~1e-6 ||A||^2
+      op_gram_matrix(c, Qb, I, kq, I, Gq);
+      op_gram_matrix(c, Bt, J, kq, J, Gd);
+      c.launches += 1;
+      if (!c.dry) c.check(launch_proj_energy(Gq, Gd, kq, pe, c.s));
+      double pa = 0.0;
+      if (!c.dry && !host_read(c, pe, &pa, 1)) return RHOSVD_ECUDA;
+      e = a2 - pa;
     }
-    if (kq == 0) kq = 1;                       // rank 0 is not representable: keep one direction
-    // truncation: eigenvectors of B B^T (all kq, descending) and the rank
-    op_gram_matrix(c, Bt, J, kq, J, Gd);
+    // truncation: eigenvectors of B B^T (Gd, all kq, descending) and the rank
     c.launches += 1;
     if (!c.dry) c.check(launch_small_eig(Gd, kq, kq, Ub, ldu_of(kq), sv, c.st, c.s));
     int r = kq;
@@ -1010,6 +1041,11 @@ rhosvd_status run_fixed_accuracy(Ctx& c, const float* X, const Geom& g0, double 
       r = std::max(r, 1);
     }
     lift_factor(c, Qb, I, kq, Ub, r, U[n]);
+    // sign convention (largest-magnitude entry of each factor column positive): the
+    // next modes sketch the core in this mode's coordinates, so the convention
+    // fixes which test matrix they effectively see
+    c.launches += 1;
+    if (!c.dry) c.check(launch_sign_canon(U[n], I, r, Ub, ldu_of(kq), kq, c.s));
     float* dst = (n == N - 1) ? G : Sb[ping];
     refold_core(c, Bt, g, n, kq, Ub, r, dst);
     g.d[n] = r;

@@ -168,7 +168,7 @@ small_eig_kernel(const double* __restrict__ G, int K, int R, float* __restrict__
     int rank = 0;
     for (int o = 0; o < K; ++o) rank += (norms[o] > nc) || (norms[o] == nc && o < c);
     order[rank] = c;
-    if (sv != nullptr) sv[rank] = nc * ldexpf(1.f, e2 / 2);
+    if (sv != nullptr) sv[rank] = nc;          // X holds the unscaled factor L (chol_grid undoes 2^-e2)
   }
   __syncthreads();
   const float smax = norms[order[0]];

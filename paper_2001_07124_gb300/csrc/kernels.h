@@ -104,6 +104,9 @@ cudaError_t launch_quantize(const float* X, int64_t n, int64_t slice_len, int eb
                             unsigned int* amax, cudaStream_t st);
 // a <- nearest value of the format, in place (test matrices of a reduced-precision run)
 cudaError_t launch_round_to_format(float* a, int64_t n, int eb, cudaStream_t st);
+// the seeded test matrix of launch_omega with every entry rounded to the format (eb bytes)
+cudaError_t launch_omega_rounded(uint64_t seed, uint32_t stream_id, int64_t rows, int cols, float* out,
+                                 int64_t ld, int eb, cudaStream_t st);
 // Y = X_q,(n) W with the view x in elements (x.p unused; the data is xq) and W
 // a plain J x K FP32 matrix; scale_mode 0 none, 1 per column slice (slice =
 // j / slice_len), 2 per row (scale[i]).  part: sketch_lp_scratch_floats floats.
@@ -139,7 +142,7 @@ cudaError_t launch_omega(uint64_t seed, uint32_t stream_id, int64_t rows, int co
 // ---- orth.cu
 // Cholesky factor L (K x K, FP32, column-major lower, zero above) of the FP64
 // Gram G = L L^T.  pass 0 writes orth_fail; pass 1 runs only if orth_fail is
-// clear.  Breakdown sets orth_fail and, if fail_code is non-zero, records
+// clear; pass 2 (shifted CholeskyQR: G + 100 u tr(G) I in FP32) writes orth_fail.  Breakdown sets orth_fail and, if fail_code is non-zero, records
 // fail_code as the device error.  Minv (nullable) receives R^-1 = L^-T (K x K,
 // column-major, leading dimension ldm) for the GEMM form of the apply.
 cudaError_t launch_chol(const double* G, int K, float* L, float* Minv, int ldm, int pass, int fail_code,
@@ -168,6 +171,12 @@ cudaError_t launch_small_eig(const double* G, int K, int R, float* Ub, int ldu, 
 cudaError_t launch_transpose(const float* in, int64_t rows, int64_t cols, int64_t ld, float* out,
                              cudaStream_t st);
 cudaError_t launch_fill_identity(float* U, int64_t I, int R, cudaStream_t st);
+// flip columns of U (I x R) and of Ub (K x R, ld ldu) so that each U column's
+// largest-magnitude entry is positive
+cudaError_t launch_sign_canon(float* U, int64_t I, int R, float* Ub, int ldu, int K, cudaStream_t st);
+// out[0] = tr(C) - sum_ij (M - I)_ij C_ij: the projected energy tr(M^-1 C) to
+// first order in M - I, for M = Q^T Q and C = (Q^T A)(Q^T A)^T (K x K, FP64)
+cudaError_t launch_proj_energy(const double* M, const double* C, int K, double* out, cudaStream_t st);
 // y += a x (n elements)
 cudaError_t launch_axpy(float* y, const float* x, float a, int64_t n, cudaStream_t st);
 // out (I x L*Rt, column-major) = mode unfolding of in viewed as [L, I, Rt]

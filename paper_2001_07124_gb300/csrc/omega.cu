@@ -47,6 +47,67 @@ __global__ void axpy_kernel(float* __restrict__ y, const float* __restrict__ x, 
   if (e < n) y[e] = fmaf(a, x[e], y[e]);
 }
 
+// Sign convention of a factor: column c of U (I x R, ld I) is flipped, together
+// with column c of Ub (K x R, ld ldu), so that its entry of largest magnitude
+// (the first such on ties) is positive.  One block per column.
+__global__ void sign_canon_kernel(float* __restrict__ U, int64_t I, float* __restrict__ Ub, int ldu, int K) {
+  const int c = blockIdx.x;
+  float* u = U + (int64_t)c * I;
+  __shared__ float sv[256];
+  __shared__ int64_t si[256];
+  float best = -1.f;
+  int64_t bi = 0;
+  for (int64_t i = threadIdx.x; i < I; i += blockDim.x) {
+    const float a = fabsf(u[i]);
+    if (a > best) {
+      best = a;
+      bi = i;
+    }
+  }
+  sv[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const float a = sv[threadIdx.x + o];
+      const int64_t ia = si[threadIdx.x + o];
+      if (a > sv[threadIdx.x] || (a == sv[threadIdx.x] && ia < si[threadIdx.x])) {
+        sv[threadIdx.x] = a;
+        si[threadIdx.x] = ia;
+      }
+    }
+    __syncthreads();
+  }
+  const bool flip = u[si[0]] < 0.f;
+  __syncthreads();
+  if (!flip) return;
+  for (int64_t i = threadIdx.x; i < I; i += blockDim.x) u[i] = -u[i];
+  for (int k = threadIdx.x; k < K; k += blockDim.x) Ub[k + (int64_t)c * ldu] = -Ub[k + (int64_t)c * ldu];
+}
+
+// Energy of the projection of A onto range(Q) from M = Q^T Q and C = B B^T,
+// B = Q^T A (both K x K, FP64): ||Q M^-1 Q^T A||_F^2 = tr(M^-1 C), and with
+// M = I + D (Q orthonormal to FP32 storage, ||D|| ~ 1e-6) M^-1 = I - D + O(D^2),
+// so out = tr(C) - sum_ij D_ij C_ij to within ||D||^2 tr(C).  One block, fixed
+// summation order.
+__global__ void proj_energy_kernel(const double* __restrict__ M, const double* __restrict__ C, int K,
+                                   double* __restrict__ out) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
+    const int i = e % K, j = e / K;
+    const double d = M[e] - (i == j ? 1.0 : 0.0);
+    acc += (i == j ? C[e] : 0.0) - d * C[e];
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
 __global__ void fill_identity_kernel(float* U, int64_t I, int R) {
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= I * R) return;
@@ -82,6 +143,18 @@ cudaError_t launch_unfold(const float* in, int64_t L, int64_t I, int64_t Rt, flo
 cudaError_t launch_axpy(float* y, const float* x, float a, int64_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   axpy_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y, x, a, n);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sign_canon(float* U, int64_t I, int R, float* Ub, int ldu, int K, cudaStream_t st) {
+  if (R == 0 || I == 0) return cudaSuccess;
+  sign_canon_kernel<<<(unsigned)R, 256, 0, st>>>(U, I, Ub, ldu, K);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_proj_energy(const double* M, const double* C, int K, double* out, cudaStream_t st) {
+  if (K < 1) return cudaErrorInvalidValue;
+  proj_energy_kernel<<<1, 256, 0, st>>>(M, C, K, out);
   return cudaGetLastError();
 }
 

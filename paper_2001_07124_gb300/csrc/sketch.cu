@@ -391,7 +391,10 @@ cudaError_t launch_ttm(const View& x, const float* Mp, int64_t m_i, int64_t m_k,
   const bool wide = (J + TT_MAX_BJ - 1) / TT_MAX_BJ >= 296;
   const int bj = wide ? 128 : 32;
   const unsigned gx = (unsigned)((J + bj - 1) / bj);
-  if (K <= 64) {
+  if (K <= 16) {
+    if (wide) ttm_kernel<8, 1><<<dim3(gx, 1), TT_THREADS, 0, st>>>(x, Mp, m_i, m_k, K, out, skip);
+    else ttm_kernel<2, 1><<<dim3(gx, 1), TT_THREADS, 0, st>>>(x, Mp, m_i, m_k, K, out, skip);
+  } else if (K <= 64) {
     if (wide) ttm_kernel<8, 4><<<dim3(gx, 1), TT_THREADS, 0, st>>>(x, Mp, m_i, m_k, K, out, skip);
     else ttm_kernel<2, 4><<<dim3(gx, 1), TT_THREADS, 0, st>>>(x, Mp, m_i, m_k, K, out, skip);
   } else {

@@ -154,11 +154,30 @@ __global__ void round_to_format_kernel(float* __restrict__ a, int64_t n) {
   if (e < n) a[e] = Fmt<EB>::value(Fmt<EB>::bits(a[e]));
 }
 
+// The seeded Gaussian test matrix (the omega kernel's values) rounded to the
+// format on store: one thread per (row j, group of four columns).
+template <int EB>
+__global__ void omega_rounded_kernel(uint64_t seed, uint32_t stream_id, int64_t rows, int cols,
+                                     float* __restrict__ out, int64_t ld) {
+  const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.y;
+  if (j >= rows) return;
+  float z[4];
+  omega_quad(seed, stream_id, (uint64_t)j, (uint32_t)g, z);
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int k = 4 * g + t;
+    if (k < cols) out[j + (int64_t)k * ld] = Fmt<EB>::value(Fmt<EB>::bits(z[t]));
+  }
+}
+
 // ---------------------------------------------------------------- sketch Y = X_q,(n) W
-// Stage: ROWS rows x 4 K-step chunks of 32 bytes per row of X_q (KJ = 32 / EB
+// Stage: ROWS rows x NKS K-step chunks of 32 bytes per row of X_q (KJ = 32 / EB
 // elements of j per chunk: 16 BF16 or 32 e4m3): 32 KB with ROWS = 256 (two
-// 128-row tiles) for modes with I > 128, 16 KB with ROWS = 128 (one tile) for
-// short modes.  Layouts in shared memory: mode 1 (L = 1) one 2-D box
+// 128-row tiles, 4 chunks) for modes with I > 128, and for short modes
+// ROWS = 128 (one tile) with 8 chunks (32 KB) in BF16, 4 chunks (16 KB) in
+// e4m3, whose per-slice scales need slices of whole stages (a 4-chunk stage,
+// 128 j, divides every slice length that is a multiple of 128).  Layouts in shared memory: mode 1 (L = 1) one 2-D box
 // {ROWS i, SBJ j}, smem [jj][ROWS]; strided views one 3-D box {KJ l, ROWS i, 1 r}
 // per chunk, smem [chunk][i][32 bytes].  The transform warps pack each row's
 // chunk into eight 32-bit words (element order = K order) and store them into
@@ -173,11 +192,17 @@ constexpr int LP_A_STAGES = 2;
 constexpr int LP_A_SLOT_COLS = 8;          // 128 lanes x 32 bytes: eight 32-bit columns
 constexpr int LP_D_COL0 = LP_A_STAGES * 8 * LP_A_SLOT_COLS;   // 8 slots per stage
 
+__host__ __device__ constexpr int lp_nks(int eb, int tiles) {
+  return (tiles == 1 && eb == 2) ? 8 : 4;
+}
+
 template <int EB, int NPAD, int TILES>
 struct LpGeo {
   static constexpr int KJ = 32 / EB;                      // j per K step (one MMA)
   static constexpr int ROWS = 128 * TILES;
-  static constexpr int NKS = 4;                           // K steps per stage
+  // K steps per stage: 4 with two tiles (32 KB); 8 with one tile in BF16 (32 KB,
+  // the two warpgroups filling four A slots each), 4 in e4m3 (whole-stage slices)
+  static constexpr int NKS = lp_nks(EB, TILES);
   static constexpr int STAGE_BYTES = ROWS * NKS * 32;
   static constexpr int SBJ = KJ * NKS;                    // j per stage
   static constexpr int D_COLS = 2 * NPAD;                 // hi and lo halves of a tile's accumulator
@@ -754,7 +779,7 @@ LpPlan plan_lp(int64_t I, int64_t J, int eb) {
   LpPlan p;
   p.tiles = I > 128 ? 2 : 1;
   p.mgroups = (int)((I + 128 * p.tiles - 1) / (128 * p.tiles));
-  p.sbj = 4 * (32 / eb);
+  p.sbj = lp_nks(eb, p.tiles) * (32 / eb);
   const int64_t nblk = (J + p.sbj - 1) / p.sbj;
   p.splits = (int)std::min<int64_t>(std::max<int64_t>(1, device_sms() / p.mgroups), nblk);
   return p;
@@ -793,10 +818,20 @@ cudaError_t launch_round_to_format(float* a, int64_t n, int eb, cudaStream_t st)
   return cudaGetLastError();
 }
 
+cudaError_t launch_omega_rounded(uint64_t seed, uint32_t stream_id, int64_t rows, int cols, float* out,
+                                 int64_t ld, int eb, cudaStream_t st) {
+  if (rows == 0 || cols == 0) return cudaSuccess;
+  const dim3 grid((unsigned)((rows + 255) / 256), (unsigned)((cols + 3) / 4));
+  if (eb == 2) omega_rounded_kernel<2><<<grid, 256, 0, st>>>(seed, stream_id, rows, cols, out, ld);
+  else if (eb == 1) omega_rounded_kernel<1><<<grid, 256, 0, st>>>(seed, stream_id, rows, cols, out, ld);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
 bool tc_sketch_lp_supported(const View& x, int eb, int K, int scale_mode, int64_t slice_len) {
   if (eb != 1 && eb != 2) return false;
   const int64_t J = x.L * x.Rt;
-  const int kj = 32 / eb, sbj = 4 * kj;
+  const int kj = 32 / eb, sbj = lp_nks(eb, x.I > 128 ? 2 : 1) * kj;
   if (K < 1 || K > 64 || x.I < 1 || x.I >= (int64_t(1) << 31) || J < 1 || J >= (int64_t(1) << 31) || J % 4 != 0)
     return false;
   if (scale_mode == 1 && (slice_len < 1 || slice_len % sbj != 0)) return false;

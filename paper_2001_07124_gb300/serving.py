@@ -31,13 +31,16 @@ import numpy as np
 class Request:
     rid: int
     dims: tuple
-    ranks: tuple
+    ranks: tuple                        # fixed rank (ignored by fixed-accuracy requests)
     arrival: float                      # seconds from the start of the run
     x_host: object = None               # flat column-major FP32 tensor (torch, pinned) for the GPU executor
     algo: str = "rsthosvd"
     p: int = 10
     q: int = 1
     seed: int = 0
+    tol: float = 0.0                    # > 0: fixed-accuracy request, ||X - X_hat|| <= tol ||X||, ranks found
+    block: int = 16                     # range-finder block of a fixed-accuracy request
+    k_max: Optional[tuple] = None       # largest rank per mode of a fixed-accuracy request (default min(I_n, 128))
 
 
 @dataclasses.dataclass
@@ -48,6 +51,7 @@ class Result:
     finished: float
     G: Optional[np.ndarray] = None
     Us: Optional[List[np.ndarray]] = None
+    ranks: Optional[tuple] = None
 
     @property
     def latency(self) -> float:
@@ -113,8 +117,10 @@ class Scheduler:
             still = []
             for req, slot, h, adm in active:           # retire finished requests
                 if self.ex.done(h):
-                    G, Us = self.ex.finish(h)
-                    results.append(Result(req.rid, req.arrival, adm, self.clock(), G, Us))
+                    out = self.ex.finish(h)
+                    G, Us = out[0], out[1]
+                    ranks = out[2] if len(out) > 2 else tuple(req.ranks)
+                    results.append(Result(req.rid, req.arrival, adm, self.clock(), G, Us, ranks))
                     free_slots.append(slot)
                 else:
                     still.append((req, slot, h, adm))
@@ -143,22 +149,38 @@ class GpuExecutor:
     Each slot owns one device arena, carved per request into the workspace,
     the tensor and the outputs, and one pinned host buffer for the outputs.
     Both are reused by the slot's next request and only grow (or are dropped
-    by ``release``), so a request in steady state allocates nothing."""
+    by ``release``), so a request in steady state allocates nothing.
+    Fixed-rank requests are enqueued on the slot's stream and observed through
+    an event.  A fixed-accuracy request (rhosvd_decompose_tol) reads its error
+    indicator on the host after every block, so it runs in a worker thread on
+    its slot's stream; the other slots keep going meanwhile."""
 
     def __init__(self, slots: int):
+        import concurrent.futures as cf
         import torch
         from . import rhosvd as R
         self.torch, self.R = torch, R
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.arena = [None] * slots                  # device uint8 buffers
         self.host = [None] * slots                   # pinned float32 output buffers
+        self.pool = cf.ThreadPoolExecutor(max_workers=slots)
+
+    @staticmethod
+    def _kmax(req: Request):
+        return tuple(req.k_max) if req.k_max is not None else tuple(min(int(d), 128) for d in req.dims)
 
     def _layout(self, req: Request):
         """Byte offsets (ws, X, G, U_1..U_N) of a request inside its slot's arena and the total."""
         R = self.R
-        ws = _align(R.rhosvd_workspace_size(req.dims, req.ranks, req.algo, req.p, req.q))
-        sizes = [4 * int(np.prod(req.dims)), 4 * int(np.prod(req.ranks))] + \
-                [4 * int(d) * int(r) for d, r in zip(req.dims, req.ranks)]
+        if req.tol > 0:
+            km = self._kmax(req)
+            ws = _align(R.rhosvd_workspace_size_tol(req.dims, req.block, km))
+            out_ranks = km
+        else:
+            ws = _align(R.rhosvd_workspace_size(req.dims, req.ranks, req.algo, req.p, req.q))
+            out_ranks = req.ranks
+        sizes = [4 * int(np.prod(req.dims)), 4 * int(np.prod(out_ranks))] + \
+                [4 * int(d) * int(r) for d, r in zip(req.dims, out_ranks)]
         offs, off = [0], ws
         for sz in sizes:
             offs.append(off)
@@ -189,6 +211,20 @@ class GpuExecutor:
         for sz in sizes[1:]:
             hv.append(self.host[slot][off:off + sz // 4])
             off += sz // 4
+        if req.tol > 0:
+            def work():
+                with torch.cuda.stream(s):
+                    X.copy_(req.x_host, non_blocking=True)
+                    _, _, ranks = R.rhosvd_decompose_tol(X, req.dims, req.tol, block=req.block,
+                                                         k_max=self._kmax(req), seed=req.seed, ws=ws,
+                                                         out=(G, Us), stream=s, check=False)
+                    ng = int(np.prod(ranks))
+                    hv[0][:ng].copy_(G[:ng], non_blocking=True)
+                    for n, (d, r) in enumerate(zip(req.dims, ranks)):
+                        hv[1 + n][:d * r].copy_(Us[n][:d * r], non_blocking=True)
+                    s.synchronize()
+                return tuple(ranks)
+            return ("tol", req, slot, ws, hv, self.pool.submit(work))
         with torch.cuda.stream(s):
             X.copy_(req.x_host, non_blocking=True)
             R.rhosvd_decompose(X, req.dims, req.ranks, algo=req.algo, p=req.p, q=req.q, seed=req.seed,
@@ -197,18 +233,25 @@ class GpuExecutor:
                 hbuf.copy_(dbuf, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(s)
-        return (req, slot, ws, hv, ev)
+        return ("rank", req, slot, ws, hv, ev)
 
     def done(self, h) -> bool:
-        return h[-1].query()
+        return h[-1].done() if h[0] == "tol" else h[-1].query()
 
     def finish(self, h):
-        req, slot, ws, hv, ev = h
-        ev.synchronize()
+        kind, req, slot, ws, hv, waitable = h
+        if kind == "tol":
+            ranks = waitable.result()
+        else:
+            waitable.synchronize()
+            ranks = tuple(req.ranks)
         code, _ = self.R.rhosvd_device_status(ws, self.streams[slot])
         if code != 0:
             raise RuntimeError(f"request {req.rid}: device status {code}")
-        return hv[0].numpy().copy(), [u.numpy().copy() for u in hv[1:]]
+        ng = int(np.prod(ranks))
+        G = hv[0][:ng].numpy().copy()
+        Us = [hv[1 + n][:d * r].numpy().copy() for n, (d, r) in enumerate(zip(req.dims, ranks))]
+        return G, Us, ranks
 
 
 def serve(requests: Sequence[Request], slots: int = 4, budget_bytes: int = 150 * 10 ** 9) -> List[Result]:

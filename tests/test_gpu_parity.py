@@ -512,6 +512,29 @@ def test_batch_graph_matches_eager():
             np.testing.assert_array_equal(host(a), host(c))
 
 
+def test_batch_graph_config4_shapes_match_oracle():
+    """A batch shaped like the 4096-tensor configuration (each mode uniform in
+    [16, 96], ranks uniform in [4, 16] capped at the mode size, p = 5, q = 1, low
+    rank plus 1e-3 noise), run as one batched CUDA graph: every item agrees with
+    the FP64 oracle's R-STHOSVD with the same seeded test matrices, within the
+    FP32-path tolerances."""
+    rng = np.random.default_rng(1004)
+    items, xs = [], []
+    for b in range(24):
+        dims = tuple(int(v) for v in rng.integers(16, 97, size=3))
+        ranks = tuple(int(min(r, d)) for r, d in zip(rng.integers(4, 17, size=3), dims))
+        x = lowrank_tensor(dims, ranks, 2000 + b, noise=1e-3)
+        xs.append(f32(x))
+        items.append((dev(x), dims, ranks))
+    batch = R().BatchGraph(items, branches=8, algo="rsthosvd", p=5, q=1, seed=9)
+    batch.replay()
+    torch.cuda.synchronize()
+    assert batch.device_status() == 0
+    for (g_b, u_b), (X, dims, ranks), x32 in zip(batch.results(), items, xs):
+        g_or, u_or = _oracle_seeded("rsthosvd", x32, dims, ranks, 5, 1, 9)
+        _compare(x32, host(g_b), [host(u) for u in u_b], g_or, u_or)
+
+
 def test_rpet_graph_replay_matches_eager():
     """The captured form of R-PET (test matrices drawn into memory for some modes,
     generated in-kernel for others) gives bitwise the eager result."""
