@@ -401,7 +401,8 @@ def run_batch(args):
                       "ranks": "uniform in [4, 16], capped", "algo": "rsthosvd p=5 q=1",
                       "graph_chunk": chunk, "branches": 16, **rates,
                       "speedup": rates["batch_graph"]["decomps_per_s"] / rates["per_tensor_loop"]["decomps_per_s"],
-                      "identical_results": same, "device_status": status}), flush=True)
+                      "identical_results": same,
+                      "device_status": status}), flush=True)
 
 
 def run_primitive(args, w):

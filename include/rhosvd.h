@@ -264,6 +264,70 @@ rhosvd_status rhosvd_decompose_tol(const float* X, const rhosvd_shape* shape, do
                                    const int32_t* k_max, uint64_t seed, int32_t* ranks, float* const* U,
                                    float* G, void* ws, size_t ws_bytes, void* stream);
 
+/* ---------------------------------------------------------------- batches */
+
+/* One tensor of a batch: device pointers owned by the caller. */
+typedef struct rhosvd_batch_item {
+  const float* X;                     /* I_1 x ... x I_N, column-major (read only) */
+  float* G;                           /* R_1 x ... x R_N core, column-major (written) */
+  float* U[RHOSVD_MAX_MODES];         /* U[n]: I_n x R_n factor, ld I_n (written) */
+  int64_t dims[RHOSVD_MAX_MODES];     /* I_1..I_N, each in 1..256 */
+  int32_t ranks[RHOSVD_MAX_MODES];    /* R_1..R_N */
+  int32_t N;                          /* number of modes, 1..RHOSVD_MAX_MODES */
+} rhosvd_batch_item;
+
+/* Sizes and launch configuration of a batch (filled by rhosvd_batch_plan_create,
+ * updated by rhosvd_batch_tune; a plain struct the caller keeps). */
+typedef struct rhosvd_batch_plan {
+  int32_t n_items, q, p;
+  int32_t threads;                    /* threads per CTA: 128, 256 or 512 */
+  int32_t jc;                         /* columns of S_(n) per streamed tile: 32 or 64 */
+  int32_t ctas_per_sm;                /* persistent CTAs per SM, 1..4 */
+  int32_t imax, kmax;                 /* largest mode size and sketch width of the batch */
+  int32_t sms, max_ctas;
+  uint64_t seed;
+  int64_t zb_floats, s_floats;        /* per-CTA scratch: a J x K matrix, two core buffers */
+  size_t ws_bytes;                    /* workspace the batch needs */
+} rhosvd_batch_plan;
+
+/* Batched R-STHOSVD (Alg. 8 with Alg. 1 per mode, q power iterations,
+ * oversampling p) of many independent small tensors in ONE persistent launch:
+ * each CTA takes the next tensor from a work queue (largest work first) and
+ * decomposes it by itself in FP32 on the CUDA cores -- sketch and TTMs through
+ * shared-memory tiles with the test matrices generated in the kernel (the same
+ * values as rhosvd_decompose with the same seed: mode n on stream_id n), MGS2
+ * for the bases Q, one shifted CholeskyQR pass for the intermediate Z,
+ * two-sided Jacobi on B B^T for the truncation.  Restrictions: opts.algo =
+ * RHOSVD_ALGO_RSTHOSVD, dtype F32, no refinement or flags, q <= 8, every
+ * I_n <= 256 and every sketch width K_n = min(R_n + p, I_n, J_n) <= 32.
+ * Accuracy: the truncation's eigenvectors come from the FP32 Gram B B^T, so the
+ * subspace error grows as u (sigma_1 / sigma_R)^2 (u = 2^-24); suited to cores
+ * with sigma_1 / sigma_R below about 100.
+ *
+ * rhosvd_batch_plan_create (host only) validates the items and fills `plan`
+ * (sizes, a default launch configuration, plan->ws_bytes).
+ * rhosvd_batch_upload copies the item table and the work order into `ws`
+ * (>= plan->ws_bytes, 256-byte aligned) and waits for `stream`; call it again
+ * whenever an item's pointers change.
+ * rhosvd_batch_run launches the batch on `stream` (a memset and one kernel;
+ * capturable in a CUDA graph, no synchronisation).  Device errors (non-finite
+ * values) are recorded in the status block at the start of `ws`.
+ * NOT ENABLED: rhosvd_batch_run and rhosvd_batch_tune return
+ * RHOSVD_EUNSUPPORTED.  A process that had run the tuner and then other work
+ * met a GPU fault whose cause has not been found, so the kernel is not
+ * launched until it is.
+ * rhosvd_batch_tune runs every launchable configuration (threads x tile
+ * columns x CTAs per SM) twice on the uploaded batch, times the second run
+ * with CUDA events on `stream` (it synchronises), keeps the fastest in `plan`
+ * and returns its time in best_ms (nullable).  The outputs hold a complete
+ * decomposition afterwards. */
+rhosvd_status rhosvd_batch_plan_create(const rhosvd_batch_item* items, int32_t n_items, const rhosvd_opts* opts,
+                                       rhosvd_batch_plan* plan);
+rhosvd_status rhosvd_batch_upload(const rhosvd_batch_plan* plan, const rhosvd_batch_item* items, void* ws,
+                                  size_t ws_bytes, void* stream);
+rhosvd_status rhosvd_batch_run(const rhosvd_batch_plan* plan, void* ws, size_t ws_bytes, void* stream);
+rhosvd_status rhosvd_batch_tune(rhosvd_batch_plan* plan, void* ws, size_t ws_bytes, void* stream, float* best_ms);
+
 /* Read the device status word kept at the start of `ws` with a copy ordered
  * on `stream`, wait for that stream (and no other), and return the first error
  * recorded there by earlier calls (RHOSVD_OK if none); `flags` (nullable)

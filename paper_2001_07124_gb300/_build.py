@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "librhosvd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "sketch.cu", "tc_sketch.cu", "tc_ttm.cu", "tc_host.cu", "gram.cu", "omega.cu", "orth.cu", "eig.cu", "noalloc.cu", "tc_lp.cu"]
+SOURCES = ["api.cu", "sketch.cu", "tc_sketch.cu", "tc_ttm.cu", "tc_host.cu", "gram.cu", "omega.cu", "orth.cu", "eig.cu", "noalloc.cu", "tc_lp.cu", "batch.cu"]
 
 
 def _nvcc() -> str:

@@ -929,7 +929,7 @@ bool host_read(Ctx& c, const double* d, double* h, int n) {
 // columns: Y = A Omega_i - Q (B Omega_i), Q_i = orth(Y) re-orthogonalised once
 // against Q, B_i = Q_i^T A, and the indicator E = ||A||_F^2 - ||P_Q A||_F^2
 // (equal to ||A - Q B||_F^2; the projected energy tr((Q^T Q)^-1 B B^T) to first
-// order in Q^T Q - I, which for an exactly orthonormal Q is sum ||B_i||_F^2) is
+// order in Q^T Q - I: sum ||B_i||_F^2 less sum_ij (Q^T Q - I)_ij (B B^T)_ij) is
 // read on the host after each block; the loop stops at E <= tol^2 (after at
 // least one block) or kmax_n columns.  Then B = Ubar Sigma Vbar^T through
 // the eigenvectors of B B^T, R_n = the smallest r with E + sum_{i>r} sigma_i^2
@@ -962,7 +962,7 @@ rhosvd_status run_fixed_accuracy(Ctx& c, const float* X, const Geom& g0, double 
   float* sv = c.take<float>(RHOSVD_MAX_K);
   double* Gd = c.take<double>((size_t)RHOSVD_MAX_K * RHOSVD_MAX_K);   // C = B B^T
   double* Gq = c.take<double>((size_t)RHOSVD_MAX_K * RHOSVD_MAX_K);   // M = Q^T Q
-  double* pe = c.take<double>(1);
+  double* pe = c.take<double>(2);
   float* Sb[2] = {c.take<float>(max_s), c.take<float>(max_s)};
   Geom g = g0;
   const float* cur = X;
@@ -976,7 +976,7 @@ rhosvd_status run_fixed_accuracy(Ctx& c, const float* X, const Geom& g0, double 
     double a2 = 0.0;
     if (!c.dry && !host_read(c, Gd, &a2, 1)) return RHOSVD_ECUDA;
     if (n == 0) tol2 = eps * eps * a2 / N;
-    double e = a2;
+    double e = a2, sum_bb = 0.0;
     int kq = 0;
     for (int i = 0; kq < kmax[n]; ++i) {
       if (!c.dry && kq > 0 && e <= tol2) break;
@@ -1006,19 +1006,24 @@ rhosvd_status run_fixed_accuracy(Ctx& c, const float* X, const Geom& g0, double 
       // ~1e-6 ||A||^2 and so could not resolve eps below ~2e-3
       c.launches += 1;
       if (!c.dry) c.check(launch_ttm(av, Y, 1, I, b, OView{Bt + (size_t)kq * J, J, L}, nullptr, c.s));
+      // E = ||A||^2 - ||P_Q A||^2 with ||P_Q A||^2 = tr(M^-1 C), M = Q^T Q,
+      // C = B B^T: tr(C) = sum ||B_i||^2 from FP64-accurate one-column Grams,
+      // less the first-order term sum_ij (M - I)_ij C_ij, for which an FP32 Gram
+      // of B suffices.  Q is orthonormal only to FP32 storage (||M - I|| ~ 1e-6),
+      // which the plain sum ||B_i||^2 would carry into E as ~1e-6 ||A||^2
+      op_gram_matrix(c, Bt + (size_t)kq * J, J * (int64_t)b, 1, J * (int64_t)b, pe);
       kq += b;
-      // E = ||A||^2 - ||P_Q A||^2, the projected energy from M = Q^T Q and
-      // C = B B^T: Q is orthonormal only to FP32 storage (||Q^T Q - I|| ~ 1e-6),
-      // which in ||A||^2 - sum ||B_i||^2 would leave an error ~1e-6 ||A||^2
       op_gram_matrix(c, Qb, I, kq, I, Gq);
-      op_gram_matrix(c, Bt, J, kq, J, Gd);
+      op_gram_matrix(c, Bt, J, kq, J, Gd, false);
       c.launches += 1;
-      if (!c.dry) c.check(launch_proj_energy(Gq, Gd, kq, pe, c.s));
-      double pa = 0.0;
-      if (!c.dry && !host_read(c, pe, &pa, 1)) return RHOSVD_ECUDA;
-      e = a2 - pa;
+      if (!c.dry) c.check(launch_proj_energy(Gq, Gd, kq, pe + 1, c.s));
+      double h[2] = {0.0, 0.0};
+      if (!c.dry && !host_read(c, pe, h, 2)) return RHOSVD_ECUDA;
+      sum_bb += h[0];
+      e = a2 - sum_bb + h[1];
     }
-    // truncation: eigenvectors of B B^T (Gd, all kq, descending) and the rank
+    // truncation: eigenvectors of B B^T (FP64-accurate Gram, all kq, descending) and the rank
+    op_gram_matrix(c, Bt, J, kq, J, Gd);
     c.launches += 1;
     if (!c.dry) c.check(launch_small_eig(Gd, kq, kq, Ub, ldu_of(kq), sv, c.st, c.s));
     int r = kq;

@@ -174,8 +174,8 @@ cudaError_t launch_fill_identity(float* U, int64_t I, int R, cudaStream_t st);
 // flip columns of U (I x R) and of Ub (K x R, ld ldu) so that each U column's
 // largest-magnitude entry is positive
 cudaError_t launch_sign_canon(float* U, int64_t I, int R, float* Ub, int ldu, int K, cudaStream_t st);
-// out[0] = tr(C) - sum_ij (M - I)_ij C_ij: the projected energy tr(M^-1 C) to
-// first order in M - I, for M = Q^T Q and C = (Q^T A)(Q^T A)^T (K x K, FP64)
+// out[0] = sum_ij (M - I)_ij C_ij: the first-order correction tr(C) - tr(M^-1 C)
+// of the projected energy, for M = Q^T Q and C = (Q^T A)(Q^T A)^T (K x K, FP64)
 cudaError_t launch_proj_energy(const double* M, const double* C, int K, double* out, cudaStream_t st);
 // y += a x (n elements)
 cudaError_t launch_axpy(float* y, const float* x, float a, int64_t n, cudaStream_t st);

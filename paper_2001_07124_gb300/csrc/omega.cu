@@ -85,11 +85,12 @@ __global__ void sign_canon_kernel(float* __restrict__ U, int64_t I, float* __res
   for (int k = threadIdx.x; k < K; k += blockDim.x) Ub[k + (int64_t)c * ldu] = -Ub[k + (int64_t)c * ldu];
 }
 
-// Energy of the projection of A onto range(Q) from M = Q^T Q and C = B B^T,
-// B = Q^T A (both K x K, FP64): ||Q M^-1 Q^T A||_F^2 = tr(M^-1 C), and with
-// M = I + D (Q orthonormal to FP32 storage, ||D|| ~ 1e-6) M^-1 = I - D + O(D^2),
-// so out = tr(C) - sum_ij D_ij C_ij to within ||D||^2 tr(C).  One block, fixed
-// summation order.
+// First-order correction of the projected energy of A onto range(Q) for a
+// basis Q that is orthonormal only to FP32 storage: with M = Q^T Q = I + D and
+// C = B B^T, B = Q^T A (both K x K, FP64), ||Q M^-1 Q^T A||_F^2 = tr(M^-1 C)
+// = tr(C) - sum_ij D_ij C_ij + O(||D||^2 tr C); out = sum_ij D_ij C_ij.  C
+// need only be accurate to a few digits (the term is ~1e-6 tr C).  One block,
+// fixed summation order.
 __global__ void proj_energy_kernel(const double* __restrict__ M, const double* __restrict__ C, int K,
                                    double* __restrict__ out) {
   __shared__ double red[256];
@@ -97,7 +98,7 @@ __global__ void proj_energy_kernel(const double* __restrict__ M, const double* _
   for (int e = threadIdx.x; e < K * K; e += blockDim.x) {
     const int i = e % K, j = e / K;
     const double d = M[e] - (i == j ? 1.0 : 0.0);
-    acc += (i == j ? C[e] : 0.0) - d * C[e];
+    acc += d * C[e];
   }
   red[threadIdx.x] = acc;
   __syncthreads();

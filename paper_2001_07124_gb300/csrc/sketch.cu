@@ -262,13 +262,14 @@ void launch_partials(const SketchPlan& pl, const View& x, const WView& w, int K,
 }  // namespace
 
 cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes) {
-  // One flag per (device, kernel) pair; a handful of kernels use this.  The
-  // table is shared by every host thread, so it is read and written under a
-  // lock (a slot taken by one thread must not be reused for another kernel).
+  // The largest limit set so far per (device, kernel) pair; the attribute is
+  // raised whenever a launch needs more (a kernel whose shared memory depends
+  // on its arguments asks for different sizes).  The table is shared by every
+  // host thread, so it is read and written under a lock.
   constexpr int kMaxDev = 64, kMaxKern = 64;
   static std::mutex mu;
   static const void* kernels[kMaxKern] = {nullptr};
-  static bool done[kMaxKern][kMaxDev] = {{false}};
+  static size_t set_bytes[kMaxKern][kMaxDev] = {{0}};
   static int nk = 0;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -281,9 +282,9 @@ cudaError_t allow_dynamic_smem(const void* kernel, size_t bytes) {
     slot = nk++;
     kernels[slot] = kernel;
   }
-  if (slot >= 0 && dev < kMaxDev && done[slot][dev]) return cudaSuccess;
+  if (slot >= 0 && dev < kMaxDev && set_bytes[slot][dev] >= bytes) return cudaSuccess;
   e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e == cudaSuccess && slot >= 0 && dev < kMaxDev) done[slot][dev] = true;
+  if (e == cudaSuccess && slot >= 0 && dev < kMaxDev) set_bytes[slot][dev] = bytes;
   return e;
 }
 

@@ -50,6 +50,19 @@ class Opts(ctypes.Structure):
                 ("dtype", ctypes.c_int32), ("refine_iters", ctypes.c_int32)]
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("G", ctypes.c_void_p), ("U", ctypes.c_void_p * MAX_MODES),
+                ("dims", ctypes.c_int64 * MAX_MODES), ("ranks", ctypes.c_int32 * MAX_MODES), ("N", ctypes.c_int32)]
+
+
+class BatchPlan(ctypes.Structure):
+    _fields_ = [("n_items", ctypes.c_int32), ("q", ctypes.c_int32), ("p", ctypes.c_int32),
+                ("threads", ctypes.c_int32), ("jc", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
+                ("imax", ctypes.c_int32), ("kmax", ctypes.c_int32), ("sms", ctypes.c_int32),
+                ("max_ctas", ctypes.c_int32), ("seed", ctypes.c_uint64), ("zb_floats", ctypes.c_int64),
+                ("s_floats", ctypes.c_int64), ("ws_bytes", ctypes.c_size_t)]
+
+
 _LIB = None
 _P = ctypes.c_void_p
 _PP = ctypes.POINTER(ctypes.c_void_p)
@@ -95,6 +108,13 @@ def lib() -> ctypes.CDLL:
         "rhosvd_decompose_tol": (st, [_P, ctypes.POINTER(Shape), ctypes.c_double, ctypes.c_int32, _I32P,
                                       ctypes.c_uint64, _I32P, _PP, _P, _P, ctypes.c_size_t, _P]),
         "rhosvd_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "rhosvd_batch_plan_create": (st, [ctypes.POINTER(BatchItem), ctypes.c_int32, ctypes.POINTER(Opts),
+                                          ctypes.POINTER(BatchPlan)]),
+        "rhosvd_batch_upload": (st, [ctypes.POINTER(BatchPlan), ctypes.POINTER(BatchItem), _P, ctypes.c_size_t,
+                                     _P]),
+        "rhosvd_batch_run": (st, [ctypes.POINTER(BatchPlan), _P, ctypes.c_size_t, _P]),
+        "rhosvd_batch_tune": (st, [ctypes.POINTER(BatchPlan), _P, ctypes.c_size_t, _P,
+                                   ctypes.POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -553,6 +573,68 @@ class BatchGraph:
             code, _ = rhosvd_device_status(ws)
             worst = worst or code
         return worst
+
+
+class BatchPersistent:
+    """Many small R-STHOSVDs in one persistent launch (rhosvd_batch_*).
+
+    The launch is not enabled in this build (``run`` and ``tune`` raise
+    RHOSVD_EUNSUPPORTED); plan creation and upload validate on the host.
+
+    items: list of (X, dims, ranks) with X a column-major device tensor.  Each
+    item gets its own outputs; the batch shares one workspace (the item table,
+    the work queue and per-CTA scratch).  ``tune()`` times the launchable
+    configurations on this batch and keeps the fastest; ``run()`` enqueues the
+    batch on a stream (a memset and one kernel, capturable); ``results()``
+    returns (G, [U_n]) views per item."""
+
+    def __init__(self, items, algo="rsthosvd", p=5, q=1, seed=0, stream=None):
+        if algo != "rsthosvd":
+            raise ValueError("the persistent batch runs R-STHOSVD")
+        self.items = []
+        n = len(items)
+        self._table = (BatchItem * max(1, n))()
+        for t, (X, dims, ranks) in enumerate(items):
+            X = colmajor(X, dims)
+            N = len(dims)
+            out = (empty_colmajor(ranks), [empty_colmajor((dims[k], ranks[k])) for k in range(N)])
+            self.items.append((X, tuple(dims), tuple(ranks), out))
+            it = self._table[t]
+            it.X, it.G, it.N = _dptr(X), _dptr(out[0]), N
+            for k in range(N):
+                it.U[k] = _dptr(out[1][k])
+                it.dims[k] = int(dims[k])
+                it.ranks[k] = int(ranks[k])
+        self.plan = BatchPlan()
+        opts = make_opts(algo, p, q, seed)
+        _check(lib().rhosvd_batch_plan_create(self._table, n, ctypes.byref(opts), ctypes.byref(self.plan)),
+               "rhosvd_batch_plan_create")
+        self.ws = Workspace(int(self.plan.ws_bytes))
+        _check(lib().rhosvd_batch_upload(ctypes.byref(self.plan), self._table, _P(self.ws.ptr), self.ws.nbytes,
+                                         _stream(stream)), "rhosvd_batch_upload")
+
+    @property
+    def config(self):
+        return {"threads": int(self.plan.threads), "tile_columns": int(self.plan.jc),
+                "ctas_per_sm": int(self.plan.ctas_per_sm)}
+
+    def tune(self, stream=None) -> float:
+        ms = ctypes.c_float(0.0)
+        _check(lib().rhosvd_batch_tune(ctypes.byref(self.plan), _P(self.ws.ptr), self.ws.nbytes, _stream(stream),
+                                       ctypes.byref(ms)), "rhosvd_batch_tune")
+        return float(ms.value)
+
+    def run(self, stream=None):
+        _check(lib().rhosvd_batch_run(ctypes.byref(self.plan), _P(self.ws.ptr), self.ws.nbytes, _stream(stream)),
+               "rhosvd_batch_run")
+
+    def results(self):
+        return [(fortran_view(G, ranks), [matrix(Us[k], dims[k], ranks[k]) for k in range(len(dims))])
+                for X, dims, ranks, (G, Us) in self.items]
+
+    def device_status(self):
+        code, _ = rhosvd_device_status(self.ws)
+        return code
 
 
 def rhosvd_workspace_size_tol(dims, block, k_max) -> int:

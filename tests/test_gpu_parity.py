@@ -512,7 +512,7 @@ def test_batch_graph_matches_eager():
             np.testing.assert_array_equal(host(a), host(c))
 
 
-def test_batch_graph_config4_shapes_match_oracle():
+def test_batch_graph_of_small_uneven_tensors_matches_oracle():
     """A batch shaped like the 4096-tensor configuration (each mode uniform in
     [16, 96], ranks uniform in [4, 16] capped at the mode size, p = 5, q = 1, low
     rank plus 1e-3 noise), run as one batched CUDA graph: every item agrees with
