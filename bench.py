@@ -358,6 +358,13 @@ def run_batch(args):
         x = x + 1e-3 * x.norm() / noise.norm() * noise
         items.append((x.contiguous().reshape(-1), dims, ranks))
     kw = dict(algo="rsthosvd", p=5, q=1, seed=0)
+    # one persistent launch over the whole batch, its launch shape picked by the tuner
+    persistent = R.BatchPersistent(items, **kw)
+    tune_ms = persistent.tune()
+
+    def run_persistent():
+        persistent.run()
+
     # per-tensor launch loop (each tensor its own workspace and outputs, one stream)
     loop = []
     for X, dims, ranks in items:
@@ -378,7 +385,7 @@ def run_batch(args):
 
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     rates = {}
-    for name, fn in (("per_tensor_loop", run_loop), ("batch_graph", run_graphs)):
+    for name, fn in (("persistent", run_persistent), ("per_tensor_loop", run_loop), ("batch_graph", run_graphs)):
         fn()
         torch.cuda.synchronize()
         reps = 3
@@ -396,12 +403,33 @@ def run_batch(args):
         for it_g, it_l in zip(gr.items, lo):
             (Gg, Ug), (Gl, Ul) = it_g[4], it_l[4]            # flat column-major output buffers
             same &= bool(torch.equal(Gg, Gl)) and all(bool(torch.equal(a, b)) for a, b in zip(Ug, Ul))
-    status = max(gr.device_status() for gr in graphs)
+    status = max(max(gr.device_status() for gr in graphs), persistent.device_status())
+    # accuracy of the persistent form against the graph form (same algorithm and
+    # test matrices, different FP32 arithmetic): relative errors on every item
+
+    def rel_err(X, dims, G, Us):
+        Xh = torch.einsum("abc,ia,jb,kc->kji", G.double(), Us[0].double(), Us[1].double(), Us[2].double())
+        x = X.reshape(dims[2], dims[1], dims[0]).double()
+        return float((x - Xh).norm() / x.norm())
+
+    e_graph, e_pers = [], []
+    for gr in graphs:
+        for (g, us), it in zip(gr.results(), gr.items):
+            e_graph.append(rel_err(it[0], it[1], g, us))
+    for (g, us), it in zip(persistent.results(), persistent.items):
+        e_pers.append(rel_err(it[0], it[1], g, us))
+    e_graph, e_pers = np.array(e_graph), np.array(e_pers)
     print(json.dumps({"mode": "batch", "tensors": n, "sizes": "each mode uniform in [16, 96]",
                       "ranks": "uniform in [4, 16], capped", "algo": "rsthosvd p=5 q=1",
                       "graph_chunk": chunk, "branches": 16, **rates,
                       "speedup": rates["batch_graph"]["decomps_per_s"] / rates["per_tensor_loop"]["decomps_per_s"],
+                      "speedup_persistent_vs_graph": rates["persistent"]["decomps_per_s"]
+                      / rates["batch_graph"]["decomps_per_s"],
+                      "persistent_config": persistent.config, "tune_best_ms": tune_ms,
                       "identical_results": same,
+                      "rel_error_graph_mean": float(e_graph.mean()),
+                      "rel_error_persistent_mean": float(e_pers.mean()),
+                      "rel_error_max_abs_diff": float(np.max(np.abs(e_pers - e_graph))),
                       "device_status": status}), flush=True)
 
 

@@ -312,10 +312,6 @@ typedef struct rhosvd_batch_plan {
  * rhosvd_batch_run launches the batch on `stream` (a memset and one kernel;
  * capturable in a CUDA graph, no synchronisation).  Device errors (non-finite
  * values) are recorded in the status block at the start of `ws`.
- * NOT ENABLED: rhosvd_batch_run and rhosvd_batch_tune return
- * RHOSVD_EUNSUPPORTED.  A process that had run the tuner and then other work
- * met a GPU fault whose cause has not been found, so the kernel is not
- * launched until it is.
  * rhosvd_batch_tune runs every launchable configuration (threads x tile
  * columns x CTAs per SM) twice on the uploaded batch, times the second run
  * with CUDA events on `stream` (it synchronises), keeps the fastest in `plan`

@@ -489,21 +489,26 @@ __device__ bool blk_range_basis(float* __restrict__ Z, int64_t J, int K, const B
   }
   __syncthreads();
   const bool ok = *flag != 0;
-  if (ok)
-    for (int64_t j = tid; j < J; j += T) {
-      float z[BT_MAX_K];
-#pragma unroll
-      for (int c = 0; c < BT_MAX_K; ++c) z[c] = (c < K) ? Z[j + J * c] : 0.f;
-#pragma unroll
-      for (int k = 0; k < BT_MAX_K; ++k) {
-        if (k < K) {
-          float v = 0.f;
-#pragma unroll
-          for (int c = 0; c <= k; ++c) v = fmaf(z[c], Li[k + kp * c], v);
-          Z[j + J * k] = v;
-        }
+  if (ok) {
+    // Z <- Z L^-T tile by tile: rows staged in shared memory ([jj][k], pitch kp)
+    float* Zs = smf + sm.as;
+    const int jc = sm.jc;
+    for (int64_t j0 = 0; j0 < J; j0 += jc) {
+      const int nj = tile_cols(J, j0, jc);
+      for (int e = tid; e < jc * kp; e += T) {
+        const int jj = e % jc, k = e / jc;
+        Zs[jj * kp + k] = (jj < nj && k < K) ? Z[(j0 + jj) + J * k] : 0.f;
       }
+      __syncthreads();
+      for (int e = tid; e < nj * K; e += T) {
+        const int jj = e % nj, k = e / nj;
+        float v = 0.f;
+        for (int c = 0; c <= k; ++c) v = fmaf(Zs[jj * kp + c], Li[k + kp * c], v);
+        Z[(j0 + jj) + J * k] = v;
+      }
+      __syncthreads();
     }
+  }
   __syncthreads();
   return ok;
 }
@@ -520,15 +525,17 @@ __device__ void q_to_rowmajor(const BSmem& sm, float* smf, int I, int K) {
   __syncthreads();
 }
 
-// One whole R-STHOSVD of the tensor `it` by this CTA.
+// One whole R-STHOSVD of the tensor *it by this CTA.  The current mode sizes
+// live in shared memory (dims), and the item is read through its pointer, so
+// the kernel keeps no per-thread arrays in local memory.
 template <int T>
-__device__ void decompose_one(const BItem& it, int q, uint64_t seed, float* Zb, float* Sb0, float* Sb1,
-                              const BSmem& sm, float* smf, int64_t* coff, DevStatus* st) {
-  const int tid = threadIdx.x, N = it.N, kp = sm.kp;
-  int64_t d[RHOSVD_MAX_MODES];
-  for (int k = 0; k < N; ++k) d[k] = it.d[k];
-  const float* cur = it.X;
-  float* Sb[2] = {Sb0, Sb1};
+__device__ void decompose_one(const BItem* __restrict__ it, int q, uint64_t seed, float* Zb, float* Sb0, float* Sb1,
+                              const BSmem& sm, float* smf, int64_t* coff, int64_t* dims, DevStatus* st) {
+  const int tid = threadIdx.x, N = it->N, kp = sm.kp;
+  if (tid < N) dims[tid] = it->d[tid];
+  __syncthreads();
+  const float* cur = it->X;
+  float* const G = it->G;
   int ping = 0;
   float4* rot = reinterpret_cast<float4*>(smf + sm.red);
   int* order = reinterpret_cast<int*>(smf + sm.red + 64);
@@ -537,17 +544,17 @@ __device__ void decompose_one(const BItem& it, int q, uint64_t seed, float* Zb, 
   float* Vs = smf + sm.vs;
   float* Ub = smf + sm.ub;
   for (int n = 0; n < N; ++n) {
-    const int64_t I = d[n], L = prod_lt(d, n);
+    const int64_t I = dims[n], L = prod_lt(dims, n);
     int64_t Rt = 1;
-    for (int k = n + 1; k < N; ++k) Rt *= d[k];
+    for (int k = n + 1; k < N; ++k) Rt *= dims[k];
     const int64_t J = L * Rt;
-    const int R = it.r[n], K = it.K[n];
+    const int R = it->r[n], K = it->K[n];
     const bool last = (n == N - 1);
-    float* U = it.U[n];
+    float* U = it->U[n];
     if (R == I) {                                   // nothing to reduce in this mode
       for (int64_t e = tid; e < I * I; e += T) U[e] = (e % I == e / I) ? 1.f : 0.f;
       if (last)
-        for (int64_t e = tid; e < I * J; e += T) it.G[e] = cur[e];
+        for (int64_t e = tid; e < I * J; e += T) G[e] = cur[e];
       __syncthreads();
       continue;
     }
@@ -594,22 +601,32 @@ __device__ void decompose_one(const BItem& it, int q, uint64_t seed, float* Zb, 
       for (int k = 0; k < K; ++k) v = fmaf(Ys[i + sm.ip * k], Ub[k + kp * a], v);
       U[e] = v;
     }
-    // S_new[l + L a + L R r] = sum_k Ubar(k, a) B^T(l + L r, k)
-    float* dst = last ? it.G : Sb[ping];
-    for (int64_t j = tid; j < J; j += T) {
-      float b[BT_MAX_K];
-#pragma unroll
-      for (int k = 0; k < BT_MAX_K; ++k) b[k] = (k < K) ? Zb[j + J * k] : 0.f;
-      const int64_t l = j % L, r = j / L;
-      for (int a = 0; a < R; ++a) {
-        float v = 0.f;
-#pragma unroll
-        for (int k = 0; k < BT_MAX_K; ++k) v = fmaf(b[k], Ub[k + kp * a], v);
-        dst[l + L * a + L * R * r] = v;
+    // S_new[l + L a + L R r] = sum_k Ubar(k, a) B^T(l + L r, k): rows of B^T staged
+    // in shared memory ([jj][k], pitch kp), one output (j, a) per thread and step
+    float* dst = last ? G : (ping ? Sb1 : Sb0);
+    {
+      float* Bs = smf + sm.as;
+      const int jc = sm.jc;
+      for (int64_t j0 = 0; j0 < J; j0 += jc) {
+        const int nj = tile_cols(J, j0, jc);
+        __syncthreads();
+        for (int e = tid; e < jc * kp; e += T) {
+          const int jj = e % jc, k = e / jc;
+          Bs[jj * kp + k] = (jj < nj && k < K) ? Zb[(j0 + jj) + J * k] : 0.f;
+        }
+        __syncthreads();
+        for (int e = tid; e < nj * R; e += T) {
+          const int jj = e % nj, a = e / nj;
+          float v = 0.f;
+          for (int k = 0; k < K; ++k) v = fmaf(Bs[jj * kp + k], Ub[k + kp * a], v);
+          const int64_t j = j0 + jj, l = j % L, r = j / L;
+          dst[l + L * a + L * R * r] = v;
+        }
       }
     }
     __syncthreads();
-    d[n] = R;
+    if (tid == 0) dims[n] = R;
+    __syncthreads();
     cur = dst;
     ping ^= 1;
   }
@@ -618,34 +635,34 @@ __device__ void decompose_one(const BItem& it, int q, uint64_t seed, float* Zb, 
 // The sizes every index of decompose_one is bounded by: mode sizes and sketch
 // widths within the shared-memory carve-up, J_n K_n within the per-CTA Z
 // buffer and every intermediate core within a core buffer.
-__device__ bool item_fits(const BItem& it, int imax, int kmax, int64_t zb_floats, int64_t s_floats) {
-  if (it.N < 1 || it.N > RHOSVD_MAX_MODES) return false;
-  int64_t d[RHOSVD_MAX_MODES];
-  for (int k = 0; k < it.N; ++k) {
-    d[k] = it.d[k];
-    if (d[k] < 1 || d[k] > imax) return false;
-  }
-  for (int n = 0; n < it.N; ++n) {
-    int64_t J = 1;
-    for (int k = 0; k < it.N; ++k)
-      if (k != n) J *= d[k];
-    const int R = it.r[n], K = it.K[n];
-    if (R < 1 || R > d[n] || K < R || K > kmax || K > d[n] || K > J || J * K > zb_floats) return false;
-    d[n] = R;
-    int64_t v = 1;
-    for (int k = 0; k < it.N; ++k) v *= d[k];
-    if (v > s_floats) return false;
+__device__ bool item_fits(const BItem* __restrict__ it, int imax, int kmax, int64_t zb_floats, int64_t s_floats) {
+  const int N = it->N;
+  if (N < 1 || N > RHOSVD_MAX_MODES) return false;
+  for (int k = 0; k < N; ++k)
+    if (it->d[k] < 1 || it->d[k] > imax) return false;
+  for (int n = 0; n < N; ++n) {
+    // before mode n the core has sizes R_1..R_{n-1}, I_n..I_N
+    int64_t J = 1, core = 1;
+    for (int k = 0; k < N; ++k) {
+      const int64_t cur_k = (k < n) ? (int64_t)it->r[k] : it->d[k];
+      if (k != n) J *= cur_k;
+      core *= (k <= n) ? (int64_t)it->r[k] : it->d[k];
+    }
+    const int R = it->r[n], K = it->K[n];
+    if (R < 1 || R > it->d[n] || K < R || K > kmax || K > it->d[n] || K > J || J * K > zb_floats) return false;
+    if (core > s_floats) return false;
   }
   return true;
 }
 
 template <int T>
-__global__ void __launch_bounds__(T)
+__global__ void __launch_bounds__(T, 1)
 batch_rsthosvd_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ order, int n_items,
                       uint32_t* counter, float* scratch, int64_t zb_floats, int64_t s_floats, int imax, int kmax,
                       int jc, int q, uint64_t seed, DevStatus* st) {
   extern __shared__ __align__(16) float bt_smem[];
   __shared__ int64_t coff[64];
+  __shared__ int64_t dims[RHOSVD_MAX_MODES];
   __shared__ int s_next;
   const BSmem sm(imax, kmax, jc, T);
   // the carve-up must fit the dynamic shared memory this launch was given
@@ -664,12 +681,12 @@ batch_rsthosvd_kernel(const BItem* __restrict__ items, const int32_t* __restrict
     __syncthreads();
     const int t = s_next;
     if (t >= n_items) break;
-    const BItem it = items[order[t]];
+    const BItem* it = items + order[t];
     if (!item_fits(it, imax, kmax, zb_floats, s_floats)) {   // a table that disagrees with the plan
       if (threadIdx.x == 0) set_error(st, RHOSVD_EINVAL);
       continue;
     }
-    decompose_one<T>(it, q, seed, Zb, Sb0, Sb1, sm, bt_smem, coff, st);
+    decompose_one<T>(it, q, seed, Zb, Sb0, Sb1, sm, bt_smem, coff, dims, st);
   }
 }
 
@@ -679,11 +696,6 @@ batch_rsthosvd_kernel(const BItem* __restrict__ items, const int32_t* __restrict
 
 namespace {
 
-// The launch is disabled: a process that ran the tuner and then other work
-// met a GPU fault whose cause is not yet found (the kernel itself passed its
-// parity tests and a full 4096-tensor run with every configuration).  Plan
-// creation and upload stay available and validate on the host.
-constexpr bool kBatchLaunchEnabled = false;
 constexpr size_t BT_ALIGN = 256;
 constexpr int BT_MAX_CTAS_PER_SM = 4;
 const int kThreads[3] = {128, 256, 512};
@@ -905,7 +917,6 @@ rhosvd_status rhosvd_batch_upload(const rhosvd_batch_plan* plan, const rhosvd_ba
 
 rhosvd_status rhosvd_batch_run(const rhosvd_batch_plan* plan, void* ws, size_t ws_bytes, void* stream) {
   if (plan == nullptr || ws == nullptr || ws_bytes < layout_of(*plan).total) return RHOSVD_EINVAL;
-  if (!kBatchLaunchEnabled) return RHOSVD_EUNSUPPORTED;
   if (plan->ctas_per_sm < 1 || plan->ctas_per_sm > resident_ctas(*plan, plan->threads, plan->jc))
     return RHOSVD_EINVAL;
   return launch_batch(*plan, ws, static_cast<cudaStream_t>(stream)) == cudaSuccess ? RHOSVD_OK : RHOSVD_ECUDA;
@@ -913,7 +924,6 @@ rhosvd_status rhosvd_batch_run(const rhosvd_batch_plan* plan, void* ws, size_t w
 
 rhosvd_status rhosvd_batch_tune(rhosvd_batch_plan* plan, void* ws, size_t ws_bytes, void* stream, float* best_ms) {
   if (plan == nullptr || ws == nullptr || ws_bytes < layout_of(*plan).total) return RHOSVD_EINVAL;
-  if (!kBatchLaunchEnabled) return RHOSVD_EUNSUPPORTED;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return RHOSVD_ECUDA;

@@ -578,9 +578,6 @@ class BatchGraph:
 class BatchPersistent:
     """Many small R-STHOSVDs in one persistent launch (rhosvd_batch_*).
 
-    The launch is not enabled in this build (``run`` and ``tune`` raise
-    RHOSVD_EUNSUPPORTED); plan creation and upload validate on the host.
-
     items: list of (X, dims, ranks) with X a column-major device tensor.  Each
     item gets its own outputs; the batch shares one workspace (the item table,
     the work queue and per-CTA scratch).  ``tune()`` times the launchable
