@@ -505,6 +505,8 @@ def main():
                     help="arithmetic of the sketch passes (reduced-precision copy of X)")
     ap.add_argument("--refine", type=int, default=0, help="RP-HOOI sweeps after the decomposition")
     ap.add_argument("--kron", action="store_true", help="R-PET with Kronecker-structured factor sketches")
+    ap.add_argument("--concurrent", type=int, default=4, metavar="P",
+                    help="independent decompositions in flight per step (each its own tensor)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -544,30 +546,53 @@ def main():
     del x
     X = x_host.cuda()
     dims, ranks = w.dims, w.ranks
+    P = max(1, int(args.concurrent))
     kw = dict(algo=w.algo, p=w.p, q=w.q, seed=w.omega_seed, K=w.K, S=w.S, dtype=args.dtype, refine=args.refine,
               kron=args.kron)
-    ws = R.Workspace(R.rhosvd_workspace_size(dims, ranks, w.algo, w.p, w.q, K=w.K, S=w.S, dtype=args.dtype,
-                                             refine=args.refine, kron=args.kron))
-    G = R.empty_colmajor(ranks)
-    Us = [R.empty_colmajor((dims[n], ranks[n])) for n in range(len(dims))]
-    out = (G, Us)
+    need = R.rhosvd_workspace_size(dims, ranks, w.algo, w.p, w.q, K=w.K, S=w.S, dtype=args.dtype,
+                                   refine=args.refine, kron=args.kron)
     stream = torch.cuda.current_stream()
 
-    def eager_step():
-        R.rhosvd_decompose(X, dims, ranks, ws=ws, out=out, check=False, **kw)
+    def new_outputs():
+        return (R.empty_colmajor(ranks), [R.empty_colmajor((dims[n], ranks[n])) for n in range(len(dims))])
+
+    # P independent decompositions per step, each on its own tensor (a copy of the
+    # workload's), workspace and outputs; graph form: one graph, P parallel branches
+    Xs = [X] + [X.clone() for _ in range(P - 1)]
+    wss = [R.Workspace(need) for _ in range(P)]
+    outs = [new_outputs() for _ in range(P)]
+    side = [torch.cuda.Stream() for _ in range(P)]
+
+    def eager_set(xs, wsl, outl):
+        def run():
+            for s_ in side:
+                s_.wait_stream(stream)
+            for b in range(P):
+                R.rhosvd_decompose(xs[b], dims, ranks, ws=wsl[b], out=outl[b], check=False, stream=side[b], **kw)
+            for s_ in side:
+                stream.wait_stream(s_)
+        return run
+
+    def graph_set(xs, wsl, outl):
+        g_ = R.BatchGraph([(xs[b], dims, ranks) for b in range(P)], branches=P, warmup=1, **kw)
+        # the graph keeps its own workspaces and outputs; point the set's lists at them
+        for b in range(P):
+            wsl[b] = g_.items[b][3]
+            outl[b] = g_.items[b][4]
+        return g_.replay
 
     for _ in range(args.warmup):
-        eager_step()
-    step = eager_step
-    if not args.no_graph:
-        # the whole decomposition as one CUDA graph launch (same kernels, same buffers)
-        graph = R.DecomposeGraph(X, dims, ranks, ws=ws, out=out, warmup=1, **kw)
-        step = graph.replay
-        for _ in range(2):
-            step()
-    code, flags = R.rhosvd_device_status(ws)
-    if code != 0:
-        raise RuntimeError(f"device status {code} after warm-up")
+        eager_set(Xs, wss, outs)()
+    step = eager_set(Xs, wss, outs) if args.no_graph else graph_set(Xs, wss, outs)
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    ws, out = wss[0], outs[0]
+    G, Us = out
+    for b in range(P):
+        code, flags = R.rhosvd_device_status(wss[b])
+        if code != 0:
+            raise RuntimeError(f"device status {code} after warm-up")
     # code, flags, orth_fail, fallbacks, fallback_rows, eig_sweeps
     st_words = ws.buf[:24].view(torch.int32).cpu().tolist()
 
@@ -588,30 +613,42 @@ def main():
         barrier()
     elapsed_ms = slowest_rank_ms(ev0.elapsed_time(ev1), dist, "cuda")
     clocks = clk.summary()
-    code, _ = R.rhosvd_device_status(ws)
-    if code != 0:
-        raise RuntimeError(f"device status {code} in timed region")
-    value = job_rate(args.steps, world, elapsed_ms)
+    for b in range(P):
+        code, _ = R.rhosvd_device_status(wss[b])
+        if code != 0:
+            raise RuntimeError(f"device status {code} in timed region")
+    value = job_rate(args.steps * P, world, elapsed_ms)
+
+    # latency of one decomposition alone (one graph launch, nothing else in flight)
+    single = R.DecomposeGraph(X, dims, ranks, ws=R.Workspace(need), out=new_outputs(), warmup=1, **kw)
+    for _ in range(3):
+        single.replay()
+    torch.cuda.synchronize()
+    lat_reps = max(5, min(args.steps, 100))
+    ev0.record(stream)
+    for _ in range(lat_reps):
+        single.replay()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    single_ms = ev0.elapsed_time(ev1) / lat_reps
+    del single
 
     # ---------------------------------------------------------------- e2e through host buffers
-    # Every step copies its tensor from pinned host memory and reads its factors and
-    # core back.  Two device inputs alternate: step i's host-to-device copy runs on a
-    # copy stream while step i-1 computes (the usual double buffering a caller does).
+    # Every step copies its P tensors from pinned host memory and reads their factors
+    # and cores back.  Two device sets alternate: step i's host-to-device copies run on
+    # a copy stream while step i-1 computes (the usual double buffering a caller does).
     xh = x_host.pin_memory()
     nbuf = 2
-    Xb = [X] + [torch.empty_like(X) for _ in range(nbuf - 1)]
-    outs = [out] + [(R.empty_colmajor(ranks), [R.empty_colmajor((dims[n], ranks[n])) for n in range(len(dims))])
-                    for _ in range(nbuf - 1)]
-    wss = [ws] + [R.Workspace(ws.nbytes) for _ in range(nbuf - 1)]
-    if args.no_graph:
-        runs = [(lambda b=b: R.rhosvd_decompose(Xb[b], dims, ranks, ws=wss[b], out=outs[b], check=False, **kw))
-                for b in range(nbuf)]
-    else:
-        gs = [graph] + [R.DecomposeGraph(Xb[b], dims, ranks, ws=wss[b], out=outs[b], warmup=1, **kw)
-                        for b in range(1, nbuf)]
-        runs = [g.replay for g in gs]
-    host_out = [(torch.empty(G.numel(), dtype=torch.float32).pin_memory(),
-                 [torch.empty(u.numel(), dtype=torch.float32).pin_memory() for u in Us]) for _ in range(nbuf)]
+    sets = [(Xs, wss, outs, step)]
+    for _ in range(nbuf - 1):
+        xs2 = [torch.empty_like(X) for _ in range(P)]
+        ws2 = [R.Workspace(need) for _ in range(P)]
+        out2 = [new_outputs() for _ in range(P)]
+        run2 = eager_set(xs2, ws2, out2) if args.no_graph else graph_set(xs2, ws2, out2)
+        sets.append((xs2, ws2, out2, run2))
+    host_out = [[(torch.empty(G.numel(), dtype=torch.float32).pin_memory(),
+                  [torch.empty(u.numel(), dtype=torch.float32).pin_memory() for u in Us]) for _ in range(P)]
+                for _ in range(nbuf)]
     copy_stream = torch.cuda.Stream()
     h2d_done = [torch.cuda.Event() for _ in range(nbuf)]
     buf_free = [torch.cuda.Event() for _ in range(nbuf)]
@@ -619,19 +656,20 @@ def main():
         e.record(stream)
 
     def e2e_step(i):
-        b = i % nbuf
+        bset = i % nbuf
+        xs_b, _, outs_b, run_b = sets[bset]
         with torch.cuda.stream(copy_stream):
-            copy_stream.wait_event(buf_free[b])          # step i - nbuf has finished with this buffer
-            Xb[b].copy_(xh, non_blocking=True)
-            h2d_done[b].record(copy_stream)
-        stream.wait_event(h2d_done[b])
-        runs[b]()
-        gh, uh = host_out[b]
-        gd, ud = outs[b]
-        gh.copy_(gd, non_blocking=True)
-        for a, c in zip(uh, ud):
-            a.copy_(c, non_blocking=True)
-        buf_free[b].record(stream)
+            copy_stream.wait_event(buf_free[bset])       # step i - nbuf has finished with this set
+            for xb in xs_b:
+                xb.copy_(xh, non_blocking=True)
+            h2d_done[bset].record(copy_stream)
+        stream.wait_event(h2d_done[bset])
+        run_b()
+        for (gh, uh), (gd, ud) in zip(host_out[bset], outs_b):
+            gh.copy_(gd, non_blocking=True)
+            for a_, c_ in zip(uh, ud):
+                a_.copy_(c_, non_blocking=True)
+        buf_free[bset].record(stream)
 
     e2e_steps = max(3, min(args.steps, 50))
     for i in range(2 * nbuf):
@@ -646,9 +684,9 @@ def main():
     torch.cuda.synchronize()
     barrier()
     e2e_ms = slowest_rank_ms(ev0.elapsed_time(ev1), dist, "cuda")
-    e2e_value = job_rate(e2e_steps, world, e2e_ms)
-    h2d = X.numel() * 4
-    d2h = (G.numel() + sum(u.numel() for u in Us)) * 4
+    e2e_value = job_rate(e2e_steps * P, world, e2e_ms)
+    h2d = P * X.numel() * 4
+    d2h = P * (G.numel() + sum(u.numel() for u in Us)) * 4
 
     # ---------------------------------------------------------------- dominant kernel: mode-1 sketch pass
     peaks, peak_src = _peaks()
@@ -703,8 +741,8 @@ def main():
         cpu = {"value": 1.0 / t_or, "unit": UNIT, "cores": _CORES, "kind": "oracle",
                "sample": f"one full decomposition of the {w.name} workload in FP64 NumPy (seeded Philox test matrices)"}
 
-    launches = R.rhosvd_launch_count(dims, ranks, w.algo, w.p, w.q, K=w.K, S=w.S, dtype=args.dtype,
-                                     refine=args.refine, kron=args.kron)
+    launches = P * R.rhosvd_launch_count(dims, ranks, w.algo, w.p, w.q, K=w.K, S=w.S, dtype=args.dtype,
+                                         refine=args.refine, kron=args.kron)
     if rank == 0:
         line = {
             "metric": metric_name(w, args.dtype, args.refine, args.kron), "value": value, "unit": UNIT, "n_gpus": world,
@@ -713,10 +751,14 @@ def main():
             "data": "synthetic (seeded low-rank tensor, device-drawn Philox test matrices)",
             "config": {"workload": w.name, "dims": list(dims), "ranks": list(ranks), "algo": w.algo, "p": w.p,
                        "q": w.q, "parallelism": f"replicas{world}", "l2_flush": _l2_note(w),
-                       "launch": "eager" if args.no_graph else "cuda_graph"},
+                       "launch": "eager" if args.no_graph else "cuda_graph",
+                       "concurrent_decompositions": P,
+                       "step": f"{P} independent decompositions, each on its own copy of the tensor, "
+                               f"on parallel graph branches"},
+            "single_decomposition_ms": single_ms,
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": e2e_steps, "overlap": "double-buffered: step i's H2D copy runs during step i-1"},
+                    "steps": e2e_steps, "overlap": "double-buffered: step i's H2D copies run during step i-1"},
             "gpu_launches": launches * args.steps,
             "roofline": roofline,
             "cpu_baseline": cpu,
