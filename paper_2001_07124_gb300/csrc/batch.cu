@@ -656,7 +656,7 @@ __device__ bool item_fits(const BItem* __restrict__ it, int imax, int kmax, int6
 }
 
 template <int T>
-__global__ void __launch_bounds__(T, 1)
+__global__ void __launch_bounds__(T, T == 512 ? 1 : 65536 / (T * 128))
 batch_rsthosvd_kernel(const BItem* __restrict__ items, const int32_t* __restrict__ order, int n_items,
                       uint32_t* counter, float* scratch, int64_t zb_floats, int64_t s_floats, int imax, int kmax,
                       int jc, int q, uint64_t seed, DevStatus* st) {
