@@ -55,6 +55,13 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const 
     if ((it & 63u) == 63u && globaltimer_ns() - t0 > kWaitLimitNs) return false;
   }
 }
+// The same bounded wait with a first try before the timer is read, for a
+// single issuing thread whose waits are usually already complete (the timer
+// read then stays off its critical path).
+__device__ __forceinline__ bool mbar_wait_fast(uint64_t* bar, uint32_t parity, const volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  return mbar_wait(bar, parity, abort_flag);
+}
 
 // ---------------------------------------------------------------- TMA
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tmap, int x, int y, uint64_t* bar) {

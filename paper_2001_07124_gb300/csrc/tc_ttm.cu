@@ -192,16 +192,15 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
     }
   } else if (warp == MMA_WARP) {
     if (lane == 0) {
+      int ks0 = 0, gs = 0;                             // stage within the tile, segment over the CTA
       for (int g = 0; g < total && ok; ++g) {
-        const int tl = g / nst, ks0 = g % nst;
-        const int gs = tl * nseg + ks0 / SEG;          // segment of this stage, counted over the CTA
         const int buf = gs % NBUF;
         const bool seg_first = (ks0 % SEG) == 0, seg_last = (ks0 % SEG) == SEG - 1 || ks0 == nst - 1;
         if (seg_first) {                               // the segment's buffer must have been drained
-          if (!mbar_wait(&sm.d_empty[buf], ((uint32_t)(gs / NBUF) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+          if (!mbar_wait_fast(&sm.d_empty[buf], ((uint32_t)(gs / NBUF) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
         }
         const int a = g % A_STAGES;
-        if (!mbar_wait(&sm.full_a[a], (uint32_t)(g / A_STAGES) & 1u, abort_flag)) { ok = false; break; }
+        if (!mbar_wait_fast(&sm.full_a[a], (uint32_t)(g / A_STAGES) & 1u, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(D_COL0 + buf * D_COLS);
         const uint32_t ahi = tmem + (uint32_t)(A_COL0 + a * A_STAGE_COLS);
@@ -213,7 +212,11 @@ tc_ttm_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ C
           mma_tf32_ts(d, ahi + BI + ks * 8, db, idesc1, 1u);
         }
         mma_commit(&sm.empty_a[a]);
-        if (seg_last) mma_commit(&sm.d_full[buf]);
+        if (seg_last) {
+          mma_commit(&sm.d_full[buf]);
+          ++gs;
+        }
+        if (++ks0 == nst) ks0 = 0;
       }
       mma_commit(&sm.drain);
     }
