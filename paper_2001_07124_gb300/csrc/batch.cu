@@ -51,18 +51,21 @@ struct BItem {
   int32_t pad;
 };
 
-// Shared-memory carve-up (floats), identical on host and device.
+// Shared-memory carve-up (floats), identical on host and device.  The tiles
+// of the streamed passes are double-buffered: the next tile is copied in
+// (cp.async) while the current one is used.
 struct BSmem {
-  int ip, kp, jc, T;
+  int ip, kp, jc, T, arow, abuf, wbuf;
   int as, ws, ys, ms, gs, vs, ub, red, total;
   __host__ __device__ BSmem(int imax, int kmax, int jc_, int T_) : jc(jc_), T(T_) {
     ip = imax | 1;                                  // odd pitch: conflict-free both ways
     kp = (kmax + 3) & ~3;
-    const int arow = ip > kp ? ip : kp;
+    arow = ip > kp ? ip : kp;
+    abuf = (jc * arow + 3) & ~3;
+    wbuf = jc * kp;
     int o = 0;
-    as = o; o += jc * arow;                         // S tile [jj][i] (also a Z tile [jj][k])
-    o = (o + 3) & ~3;
-    ws = o; o += jc * kp;                           // Omega / Z tile [jj][k]
+    as = o; o += 2 * abuf;                          // 2 S tiles [jj][i] (or Z tiles [jj][k], pitch kp)
+    ws = o; o += 2 * wbuf;                          // 2 Omega / Z tiles [jj][k]
     ys = o; o += ip * kp;                           // Y, Q column-major (ld ip)
     o = (o + 3) & ~3;
     ms = o; o += ip * kp;                           // Q row-major [i][k] for the TTM
@@ -84,30 +87,78 @@ __device__ __forceinline__ int tile_cols(int64_t J, int64_t j0, int jc) {
   return (int)(J - j0 < (int64_t)jc ? J - j0 : (int64_t)jc);
 }
 
-// Load the tile S_(n)(0:I, j0:j0+jc) into As[jj * arow + i] (zeros past J).
+// 4-byte asynchronous global -> shared copy; an invalid element is written as
+// zero (source size 0, nothing is read from src).
+__device__ __forceinline__ void cp_async_f32(float* dst, const float* src, bool valid) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// wait until at most one group of this thread's copies is still in flight
+__device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Start copying the tile S_(n)(0:I, j0:j0+jc) to As[jj * arow + i] (zeros past J).
 template <int T>
-__device__ void load_tile(const float* __restrict__ S, int64_t L, int64_t I, int64_t J, int64_t j0, int jc,
-                          float* As, int arow, int64_t* coff) {
+__device__ __forceinline__ void stage_s_tile(const float* S, int64_t L, int I, int64_t J, int64_t j0, int jc,
+                                             float* As, int arow) {
   const int tid = threadIdx.x;
   const int nj = tile_cols(J, j0, jc);
-  if (tid < jc) {
-    const int64_t j = j0 + tid;
-    coff[tid] = (tid < nj) ? (j % L) + L * I * (j / L) : -1;
+  if (L == 1) {          // mode 1: the columns j0.. of S_(1) are one run of nj I floats
+    const float* src = S + (int64_t)I * j0;
+    const int nv = nj * I, n = jc * I;
+    const int qd = T / I, rm = T - qd * I;        // a step of T elements = qd columns + rm rows
+    int jj = tid / I, i = tid - jj * I;
+    for (int e = tid; e < n; e += T) {
+      cp_async_f32(As + jj * arow + i, e < nv ? src + e : S, e < nv);
+      i += rm;
+      jj += qd;
+      if (i >= I) {
+        i -= I;
+        ++jj;
+      }
+    }
+  } else {               // T is a multiple of jc: a thread keeps one column of the tile
+    const int jj = tid % jc;
+    const int64_t j = j0 + jj;
+    const bool ok = jj < nj;
+    const float* col = ok ? S + (j % L) + L * (int64_t)I * (j / L) : S;
+    for (int i = tid / jc; i < I; i += T / jc) cp_async_f32(As + jj * arow + i, ok ? col + L * i : S, ok);
   }
-  __syncthreads();
-  const int n = jc * (int)I;
-  if (L == 1) {                                   // mode 1: contiguous along i
-    for (int e = tid; e < n; e += T) {
-      const int i = e % (int)I, jj = e / (int)I;
-      const int64_t off = coff[jj];
-      As[jj * arow + i] = (off >= 0) ? __ldg(S + off + i) : 0.f;
-    }
-  } else {                                        // contiguous along l
-    for (int e = tid; e < n; e += T) {
-      const int jj = e % jc, i = e / jc;
-      const int64_t off = coff[jj];
-      As[jj * arow + i] = (off >= 0) ? __ldg(S + off + L * i) : 0.f;
-    }
+}
+
+// Start copying rows j0..j0+jc of the J x K matrix Z (ld J) to Zs[jj * kp + k]
+// (zeros past J and for K <= k < kp).
+template <int T>
+__device__ __forceinline__ void stage_z_tile(const float* Z, int64_t J, int K, int64_t j0, int jc, int kp,
+                                             float* Zs) {
+  const int tid = threadIdx.x;
+  const int jj = tid % jc;
+  const bool row_ok = jj < tile_cols(J, j0, jc);
+  for (int k = tid / jc; k < kp; k += T / jc) {
+    const bool ok = row_ok && k < K;
+    cp_async_f32(Zs + jj * kp + k, ok ? Z + (j0 + jj) + J * k : Z, ok);
+  }
+}
+
+// body(j0, nj, Zs) for every row tile of Z (ld J) staged in shared memory, the
+// next tile copied in while body runs on the current one.
+template <int T, class F>
+__device__ __forceinline__ void stream_z_tiles(const float* Z, int64_t J, int K, const BSmem& sm, float* smf,
+                                               F&& body) {
+  const int jc = sm.jc, kp = sm.kp;
+  const int ntiles = (int)((J + jc - 1) / jc);
+  __syncthreads();                                  // the staging buffers are free
+  stage_z_tile<T>(Z, J, K, 0, jc, kp, smf + sm.as);
+  cp_async_commit();
+  for (int t = 0; t < ntiles; ++t) {
+    const int b = t & 1;
+    const int64_t j0 = (int64_t)t * jc;
+    if (t + 1 < ntiles) stage_z_tile<T>(Z, J, K, j0 + jc, jc, kp, smf + sm.as + (b ^ 1) * sm.abuf);
+    cp_async_commit();
+    cp_async_wait_one();
+    __syncthreads();
+    body(j0, tile_cols(J, j0, jc), static_cast<const float*>(smf + sm.as + b * sm.abuf));
+    __syncthreads();                                // the tile may be refilled
   }
 }
 
@@ -115,39 +166,43 @@ __device__ void load_tile(const float* __restrict__ S, int64_t L, int64_t I, int
 // Gaussian test matrix (Zg == nullptr; the omega kernel's values, stream
 // `stream`) or the J x K matrix Zg in global memory (ld J).
 template <int T>
-__device__ void blk_sketch(const float* __restrict__ S, int64_t L, int64_t I, int64_t J, int K,
-                           const float* __restrict__ Zg, uint64_t seed, uint32_t stream, const BSmem& sm,
-                           float* smf, int64_t* coff) {
-  float* As = smf + sm.as;
-  float* Ws = smf + sm.ws;
+__device__ void blk_sketch(const float* S, int64_t L, int64_t I, int64_t J, int K, const float* Zg, uint64_t seed,
+                           uint32_t stream, const BSmem& sm, float* smf) {
   float* Ys = smf + sm.ys;
-  const int tid = threadIdx.x, jc = sm.jc, kp = sm.kp;
-  const int arow = sm.ip > sm.kp ? sm.ip : sm.kp;
+  const int tid = threadIdx.x, jc = sm.jc, kp = sm.kp, arow = sm.arow;
   const int kg = (K + 3) / 4;
   const int ng = (int)I * kg;
+  const int ntiles = (int)((J + jc - 1) / jc);
   float acc[BT_GMAX][4];
 #pragma unroll
   for (int u = 0; u < BT_GMAX; ++u)
 #pragma unroll
     for (int t = 0; t < 4; ++t) acc[u][t] = 0.f;
-  for (int64_t j0 = 0; j0 < J; j0 += jc) {
-    __syncthreads();                                  // the previous tile is consumed
-    load_tile<T>(S, L, I, J, j0, jc, As, arow, coff);
-    const int nj = tile_cols(J, j0, jc);
+  __syncthreads();                                  // the staging buffers are free
+  stage_s_tile<T>(S, L, (int)I, J, 0, jc, smf + sm.as, arow);
+  if (Zg != nullptr) stage_z_tile<T>(Zg, J, K, 0, jc, kp, smf + sm.ws);
+  cp_async_commit();
+  for (int t = 0; t < ntiles; ++t) {
+    const int b = t & 1;
+    const int64_t j0 = (int64_t)t * jc;
+    const float* As = smf + sm.as + b * sm.abuf;
+    float* Ws = smf + sm.ws + b * sm.wbuf;
+    if (t + 1 < ntiles) {                           // the next tile streams in meanwhile
+      stage_s_tile<T>(S, L, (int)I, J, j0 + jc, jc, smf + sm.as + (b ^ 1) * sm.abuf, arow);
+      if (Zg != nullptr) stage_z_tile<T>(Zg, J, K, j0 + jc, jc, kp, smf + sm.ws + (b ^ 1) * sm.wbuf);
+    }
+    cp_async_commit();
     if (Zg == nullptr) {
+      const int nj = tile_cols(J, j0, jc);
       for (int e = tid; e < jc * kg; e += T) {
         const int jj = e % jc, g = e / jc;
         float z[4] = {0.f, 0.f, 0.f, 0.f};
         if (jj < nj) omega_quad(seed, stream, (uint64_t)(j0 + jj), (uint32_t)g, z);
 #pragma unroll
-        for (int t = 0; t < 4; ++t) Ws[jj * kp + 4 * g + t] = (4 * g + t < K) ? z[t] : 0.f;
-      }
-    } else {
-      for (int e = tid; e < jc * kp; e += T) {
-        const int jj = e % jc, k = e / jc;
-        Ws[jj * kp + k] = (jj < nj && k < K) ? Zg[(j0 + jj) + J * k] : 0.f;
+        for (int t2 = 0; t2 < 4; ++t2) Ws[jj * kp + 4 * g + t2] = (4 * g + t2 < K) ? z[t2] : 0.f;
       }
     }
+    cp_async_wait_one();
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < BT_GMAX; ++u) {
@@ -165,6 +220,7 @@ __device__ void blk_sketch(const float* __restrict__ S, int64_t L, int64_t I, in
         }
       }
     }
+    __syncthreads();                                // this tile's buffers may be refilled
   }
 #pragma unroll
   for (int u = 0; u < BT_GMAX; ++u) {
@@ -181,17 +237,23 @@ __device__ void blk_sketch(const float* __restrict__ S, int64_t L, int64_t I, in
 
 // Out (J x K, global, ld J) = S_(n)^T M with M (I x K) row-major in shared memory (Ms).
 template <int T>
-__device__ void blk_ttm(const float* __restrict__ S, int64_t L, int64_t I, int64_t J, int K, float* __restrict__ out,
-                        const BSmem& sm, float* smf, int64_t* coff) {
-  float* As = smf + sm.as;
+__device__ void blk_ttm(const float* S, int64_t L, int64_t I, int64_t J, int K, float* __restrict__ out,
+                        const BSmem& sm, float* smf) {
   const float* Ms = smf + sm.ms;
-  const int tid = threadIdx.x, jc = sm.jc, kp = sm.kp;
-  const int arow = sm.ip > sm.kp ? sm.ip : sm.kp;
+  const int tid = threadIdx.x, jc = sm.jc, kp = sm.kp, arow = sm.arow;
   const int kg = (K + 3) / 4;
   const int ng = jc * kg;
-  for (int64_t j0 = 0; j0 < J; j0 += jc) {
-    __syncthreads();
-    load_tile<T>(S, L, I, J, j0, jc, As, arow, coff);
+  const int ntiles = (int)((J + jc - 1) / jc);
+  __syncthreads();                                  // the staging buffers are free
+  stage_s_tile<T>(S, L, (int)I, J, 0, jc, smf + sm.as, arow);
+  cp_async_commit();
+  for (int t = 0; t < ntiles; ++t) {
+    const int b = t & 1;
+    const int64_t j0 = (int64_t)t * jc;
+    const float* As = smf + sm.as + b * sm.abuf;
+    if (t + 1 < ntiles) stage_s_tile<T>(S, L, (int)I, J, j0 + jc, jc, smf + sm.as + (b ^ 1) * sm.abuf, arow);
+    cp_async_commit();
+    cp_async_wait_one();
     __syncthreads();
 #pragma unroll
     for (int u = 0; u < BT_TMAX; ++u) {
@@ -212,13 +274,13 @@ __device__ void blk_ttm(const float* __restrict__ S, int64_t L, int64_t I, int64
         if (j < J) {
           const float v[4] = {a0, a1, a2, a3};
 #pragma unroll
-          for (int t = 0; t < 4; ++t)
-            if (4 * c + t < K) out[j + J * (4 * c + t)] = v[t];
+          for (int t2 = 0; t2 < 4; ++t2)
+            if (4 * c + t2 < K) out[j + J * (4 * c + t2)] = v[t2];
         }
       }
     }
+    __syncthreads();                                // this tile's buffer may be refilled
   }
-  __syncthreads();
 }
 
 // (bi <= bj) of block pair p, pairs enumerated column by column of the upper triangle
@@ -236,10 +298,9 @@ __device__ __forceinline__ void block_pair(int p, int& bi, int& bj) {
 // block pair over every `phases`-th row, then the phases are summed in order.
 template <int T>
 __device__ void blk_gram(const float* __restrict__ Z, int64_t J, int K, const BSmem& sm, float* smf) {
-  float* Zs = smf + sm.as;                            // [jj][k], pitch kp
   float* Gs = smf + sm.gs;
   float* red = smf + sm.red;
-  const int tid = threadIdx.x, jc = sm.jc, kp = sm.kp;
+  const int tid = threadIdx.x, kp = sm.kp;
   const int nb = kp / 4, npairs = nb * (nb + 1) / 2;
   const int phases = T / npairs;
   const int ph = tid / npairs, p = tid % npairs;
@@ -249,14 +310,7 @@ __device__ void blk_gram(const float* __restrict__ Z, int64_t J, int K, const BS
   float acc[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) acc[e] = 0.f;
-  for (int64_t j0 = 0; j0 < J; j0 += jc) {
-    __syncthreads();
-    const int nj = tile_cols(J, j0, jc);
-    for (int e = tid; e < jc * kp; e += T) {
-      const int jj = e % jc, k = e / jc;
-      Zs[jj * kp + k] = (jj < nj && k < K) ? Z[(j0 + jj) + J * k] : 0.f;
-    }
-    __syncthreads();
+  stream_z_tiles<T>(Z, J, K, sm, smf, [&](int64_t, int nj, const float* Zs) {
     if (active)
       for (int jj = ph; jj < nj; jj += phases) {
         const float4 a = *reinterpret_cast<const float4*>(Zs + jj * kp + 4 * bi);
@@ -267,7 +321,7 @@ __device__ void blk_gram(const float* __restrict__ Z, int64_t J, int K, const BS
 #pragma unroll
           for (int v = 0; v < 4; ++v) acc[4 * u + v] = fmaf(av[u], bv[v], acc[4 * u + v]);
       }
-  }
+  });
   __syncthreads();
   if (active)
 #pragma unroll
@@ -490,24 +544,16 @@ __device__ bool blk_range_basis(float* __restrict__ Z, int64_t J, int K, const B
   __syncthreads();
   const bool ok = *flag != 0;
   if (ok) {
-    // Z <- Z L^-T tile by tile: rows staged in shared memory ([jj][k], pitch kp)
-    float* Zs = smf + sm.as;
-    const int jc = sm.jc;
-    for (int64_t j0 = 0; j0 < J; j0 += jc) {
-      const int nj = tile_cols(J, j0, jc);
-      for (int e = tid; e < jc * kp; e += T) {
-        const int jj = e % jc, k = e / jc;
-        Zs[jj * kp + k] = (jj < nj && k < K) ? Z[(j0 + jj) + J * k] : 0.f;
-      }
-      __syncthreads();
+    // Z <- Z L^-T tile by tile: rows staged in shared memory ([jj][k], pitch kp);
+    // a tile is rewritten in place while the next one is copied in
+    stream_z_tiles<T>(Z, J, K, sm, smf, [&](int64_t j0, int nj, const float* Zs) {
       for (int e = tid; e < nj * K; e += T) {
         const int jj = e % nj, k = e / nj;
         float v = 0.f;
         for (int c = 0; c <= k; ++c) v = fmaf(Zs[jj * kp + c], Li[k + kp * c], v);
         Z[(j0 + jj) + J * k] = v;
       }
-      __syncthreads();
-    }
+    });
   }
   __syncthreads();
   return ok;
@@ -530,7 +576,7 @@ __device__ void q_to_rowmajor(const BSmem& sm, float* smf, int I, int K) {
 // the kernel keeps no per-thread arrays in local memory.
 template <int T>
 __device__ void decompose_one(const BItem* __restrict__ it, int q, uint64_t seed, float* Zb, float* Sb0, float* Sb1,
-                              const BSmem& sm, float* smf, int64_t* coff, int64_t* dims, DevStatus* st) {
+                              const BSmem& sm, float* smf, int64_t* dims, DevStatus* st) {
   const int tid = threadIdx.x, N = it->N, kp = sm.kp;
   if (tid < N) dims[tid] = it->d[tid];
   __syncthreads();
@@ -559,20 +605,20 @@ __device__ void decompose_one(const BItem* __restrict__ it, int q, uint64_t seed
       continue;
     }
     // Y = S_(n) Omega_n, Q = orth(Y)
-    blk_sketch<T>(cur, L, I, J, K, nullptr, seed, (uint32_t)n, sm, smf, coff);
+    blk_sketch<T>(cur, L, I, J, K, nullptr, seed, (uint32_t)n, sm, smf);
     if (tid < 32 && !warp_mgs2(Ys, sm.ip, (int)I, K) && tid == 0) set_error(st, RHOSVD_ENONFINITE);
     __syncthreads();
     for (int p = 0; p < q; ++p) {
       q_to_rowmajor<T>(sm, smf, (int)I, K);
-      blk_ttm<T>(cur, L, I, J, K, Zb, sm, smf, coff);            // Z = S_(n)^T Q
+      blk_ttm<T>(cur, L, I, J, K, Zb, sm, smf);            // Z = S_(n)^T Q
       blk_range_basis<T>(Zb, J, K, sm, smf);                     // a basis of range(Z)
-      blk_sketch<T>(cur, L, I, J, K, Zb, seed, 0, sm, smf, coff);   // Y = S_(n) Z
+      blk_sketch<T>(cur, L, I, J, K, Zb, seed, 0, sm, smf);   // Y = S_(n) Z
       if (tid < 32 && !warp_mgs2(Ys, sm.ip, (int)I, K) && tid == 0) set_error(st, RHOSVD_ENONFINITE);
       __syncthreads();
     }
     // B^T = S_(n)^T Q, G = B B^T, leading eigenvectors Ubar_R
     q_to_rowmajor<T>(sm, smf, (int)I, K);
-    blk_ttm<T>(cur, L, I, J, K, Zb, sm, smf, coff);
+    blk_ttm<T>(cur, L, I, J, K, Zb, sm, smf);
     blk_gram<T>(Zb, J, K, sm, smf);
     if (tid < 32) {
       const int sweeps = warp_jacobi(Gs, Vs, kp, K, rot);
@@ -604,26 +650,15 @@ __device__ void decompose_one(const BItem* __restrict__ it, int q, uint64_t seed
     // S_new[l + L a + L R r] = sum_k Ubar(k, a) B^T(l + L r, k): rows of B^T staged
     // in shared memory ([jj][k], pitch kp), one output (j, a) per thread and step
     float* dst = last ? G : (ping ? Sb1 : Sb0);
-    {
-      float* Bs = smf + sm.as;
-      const int jc = sm.jc;
-      for (int64_t j0 = 0; j0 < J; j0 += jc) {
-        const int nj = tile_cols(J, j0, jc);
-        __syncthreads();
-        for (int e = tid; e < jc * kp; e += T) {
-          const int jj = e % jc, k = e / jc;
-          Bs[jj * kp + k] = (jj < nj && k < K) ? Zb[(j0 + jj) + J * k] : 0.f;
-        }
-        __syncthreads();
-        for (int e = tid; e < nj * R; e += T) {
-          const int jj = e % nj, a = e / nj;
-          float v = 0.f;
-          for (int k = 0; k < K; ++k) v = fmaf(Bs[jj * kp + k], Ub[k + kp * a], v);
-          const int64_t j = j0 + jj, l = j % L, r = j / L;
-          dst[l + L * a + L * R * r] = v;
-        }
+    stream_z_tiles<T>(Zb, J, K, sm, smf, [&](int64_t j0, int nj, const float* Bs) {
+      for (int e = tid; e < nj * R; e += T) {
+        const int jj = e % nj, a = e / nj;
+        float v = 0.f;
+        for (int k = 0; k < K; ++k) v = fmaf(Bs[jj * kp + k], Ub[k + kp * a], v);
+        const int64_t j = j0 + jj, l = j % L, r = j / L;
+        dst[l + L * a + L * R * r] = v;
       }
-    }
+    });
     __syncthreads();
     if (tid == 0) dims[n] = R;
     __syncthreads();
@@ -661,14 +696,13 @@ batch_rsthosvd_kernel(const BItem* __restrict__ items, const int32_t* __restrict
                       uint32_t* counter, float* scratch, int64_t zb_floats, int64_t s_floats, int imax, int kmax,
                       int jc, int q, uint64_t seed, DevStatus* st) {
   extern __shared__ __align__(16) float bt_smem[];
-  __shared__ int64_t coff[64];
   __shared__ int64_t dims[RHOSVD_MAX_MODES];
   __shared__ int s_next;
   const BSmem sm(imax, kmax, jc, T);
   // the carve-up must fit the dynamic shared memory this launch was given
   uint32_t dyn_bytes;
   asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn_bytes));
-  if ((size_t)sm.total * sizeof(float) > dyn_bytes || jc > 64 || kmax > BT_MAX_K) {
+  if ((size_t)sm.total * sizeof(float) > dyn_bytes || jc > 64 || T % jc != 0 || kmax > BT_MAX_K) {
     if (threadIdx.x == 0 && blockIdx.x == 0) set_error(st, RHOSVD_EINVAL);
     return;
   }
@@ -686,7 +720,7 @@ batch_rsthosvd_kernel(const BItem* __restrict__ items, const int32_t* __restrict
       if (threadIdx.x == 0) set_error(st, RHOSVD_EINVAL);
       continue;
     }
-    decompose_one<T>(it, q, seed, Zb, Sb0, Sb1, sm, bt_smem, coff, dims, st);
+    decompose_one<T>(it, q, seed, Zb, Sb0, Sb1, sm, bt_smem, dims, st);
   }
 }
 

@@ -602,15 +602,15 @@ tc_ttm_lp_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
     }
   } else if (warp == LPT_MMA) {
     if (lane == 0) {
+      int ks0 = 0, gs = 0;                             // stage within the tile, segment over the CTA
       for (int g = 0; g < total && ok; ++g) {
-        const int tl = g / nst, ks0 = g % nst;
-        const int gs = tl * nseg + ks0 / LP_SEG, buf = gs % NBUF;
+        const int buf = gs % NBUF;
         const bool seg_first = (ks0 % LP_SEG) == 0, seg_end = (ks0 % LP_SEG) == LP_SEG - 1 || ks0 == nst - 1;
         if (seg_first) {
-          if (!mbar_wait(&sm.d_empty[buf], ((uint32_t)(gs / NBUF) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
+          if (!mbar_wait_fast(&sm.d_empty[buf], ((uint32_t)(gs / NBUF) & 1u) ^ 1u, abort_flag)) { ok = false; break; }
         }
         const int a = g % LPT_A_STAGES;
-        if (!mbar_wait(&sm.full_a[a], (uint32_t)(g / LPT_A_STAGES) & 1u, abort_flag)) { ok = false; break; }
+        if (!mbar_wait_fast(&sm.full_a[a], (uint32_t)(g / LPT_A_STAGES) & 1u, abort_flag)) { ok = false; break; }
         tc_fence_after();
         const uint32_t d = tmem + (uint32_t)(LPT_D_COL0 + buf * D_COLS);
 #pragma unroll
@@ -622,7 +622,11 @@ tc_ttm_lp_kernel(const __grid_constant__ CUtensorMap tmX, const __grid_constant_
           else mma_e4m3_ts(d, at, db, idesc, acc);
         }
         mma_commit(&sm.empty_a[a]);
-        if (seg_end) mma_commit(&sm.d_full[buf]);
+        if (seg_end) {
+          mma_commit(&sm.d_full[buf]);
+          ++gs;
+        }
+        if (++ks0 == nst) ks0 = 0;
       }
       mma_commit(&sm.drain);
     }
