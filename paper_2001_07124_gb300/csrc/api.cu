@@ -117,9 +117,11 @@ void op_ttm(Ctx& c, const View& x, const float* M, int64_t m_i, int64_t m_k, int
 // used for the intermediate bases of the power iteration (Alg. 1),
 // where only range(Q) matters: a second pass would re-orthonormalise Q1 within
 // range(Q1) without changing it, and Q1 from the FP64-accurate first pass is
-// well conditioned whenever that pass succeeds.  The apply Y R^-1 runs as a
-// tensor-core GEMM with the explicit R^-1 on tall matrices (m >= 32768), where
-// it is twice as fast as the row-wise triangular solve used otherwise.
+// well conditioned whenever that pass succeeds.  On tall matrices
+// (m >= 32768) the apply Y R^-1 multiplies by the explicit R^-1: row by row on
+// the CUDA cores up to K = 64 (independent dot products, memory-bound), as a
+// tensor-core GEMM beyond; shorter matrices take the row-wise triangular solve,
+// which needs no inverse from the factorisation.
 void op_orth(Ctx& c, float* Y, int64_t m, int K, int64_t ld, int passes = 2) {
   Scope sc(c);
   double* G = c.take<double>((size_t)K * K);
@@ -127,13 +129,16 @@ void op_orth(Ctx& c, float* Y, int64_t m, int K, int64_t ld, int passes = 2) {
   const int ldm = (K + 3) & ~3;
   float* Minv = c.take<float>((size_t)ldm * K);
   const View yv = matrix_view(Y, m, K, ld);
-  // the GEMM apply pays for forming R^-1 only on tall matrices
-  const bool gemm = c.st != nullptr && m >= 32768 && tc_ttm_supported(yv, 1, ldm, K, OView{Y, ld, 0});
+  // forming R^-1 pays only on tall matrices
+  const bool rows = c.st != nullptr && m >= 32768 && K <= RHOSVD_APPLY_RINV_MAX_K;
+  const bool gemm = !rows && c.st != nullptr && m >= 32768 && tc_ttm_supported(yv, 1, ldm, K, OView{Y, ld, 0});
   for (int pass = 0; pass < passes; ++pass) {
     op_gram_matrix(c, Y, m, K, ld, G, pass == 0);
     c.launches += 2;
-    if (!c.dry) c.check(launch_chol(G, K, L, gemm ? Minv : nullptr, ldm, pass, 0, c.st, c.s));
-    if (gemm) {
+    if (!c.dry) c.check(launch_chol(G, K, L, (rows || gemm) ? Minv : nullptr, ldm, pass, 0, c.st, c.s));
+    if (rows) {
+      if (!c.dry) c.check(launch_apply_rinv_rows(Y, m, K, ld, Minv, ldm, c.st, c.s));
+    } else if (gemm) {
       if (!c.dry) c.check(launch_tc_ttm(yv, Minv, ldm, K, OView{Y, ld, 0}, c.st, c.st, c.s));
     } else {
       if (!c.dry) c.check(launch_trsm_rows(Y, m, K, ld, L, 0, c.st, c.s));

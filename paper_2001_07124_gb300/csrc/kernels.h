@@ -152,6 +152,11 @@ cudaError_t launch_chol(const double* G, int K, float* L, float* Minv, int ldm, 
 // Skipped when skip is non-NULL and orth_fail is set.
 cudaError_t launch_trsm_rows(float* Y, int64_t m, int K, int64_t ld, const float* L, int mode,
                              const DevStatus* skip, cudaStream_t stream);
+// Q = Y R^-1 in place with the explicit upper-triangular R^-1 (K x K, ld ldm),
+// one thread per row (K <= RHOSVD_APPLY_RINV_MAX_K).
+constexpr int RHOSVD_APPLY_RINV_MAX_K = 64;
+cudaError_t launch_apply_rinv_rows(float* Y, int64_t m, int K, int64_t ld, const float* Minv, int ldm,
+                                   const DevStatus* skip, cudaStream_t stream);
 // Householder QR of A (m x K, ld) into its Q factor, in place; runs only when
 // orth_fail is set (or always if force).
 cudaError_t launch_householder(float* A, int64_t m, int K, int64_t ld, DevStatus* st, bool force,

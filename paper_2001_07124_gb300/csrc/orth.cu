@@ -207,6 +207,63 @@ trsm_rows_kernel(float* __restrict__ Y, int64_t m, int K, int64_t ld, const floa
     if (c < K) Y[row + (int64_t)c * ld] = q[c];
 }
 
+// The CholeskyQR apply Q = Y R^-1 in place with the explicit inverse
+// R^-1 = Minv (K x K upper triangular, column-major, ld ldm, written by
+// chol_kernel): q_c = sum_{i <= c} y_i R^-1(i, c).  One thread per row with
+// the row in registers; column c of R^-1 sits in shared memory as one
+// contiguous run read as broadcast float4.  Unlike the forward substitution
+// no output waits for another, so the K dot products overlap; each is an FP32
+// multiply-add chain rounded to nearest.  A finite Gram (checked by the
+// factorisation) implies a finite Y, so the zero padding of R^-1 past the
+// diagonal adds exact zeros.  (Persistent CTAs that stage R^-1 once and loop
+// over row blocks measured slower: the loads of a block then wait behind the
+// arithmetic of the previous one.)
+template <int KB>
+__global__ void __launch_bounds__(TR_ROWS, KB <= 32 ? 4 : KB <= 48 ? 3 : 2)
+apply_rinv_rows_kernel(float* __restrict__ Y, int64_t m, int K, int64_t ld, const float* __restrict__ Minv,
+                       int ldm, const DevStatus* skip) {
+  if (skip != nullptr && skip->orth_fail) return;
+  __shared__ __align__(16) float Mc[KB * KB];     // Mc[c * KB + i] = R^-1(i, c), zero for i > c
+  const int tid = threadIdx.x;
+  const int64_t row = (int64_t)blockIdx.x * TR_ROWS + tid;
+  const bool live = row < m;
+  float y[KB];
+#pragma unroll
+  for (int i = 0; i < KB; ++i) y[i] = (live && i < K) ? Y[row + (int64_t)i * ld] : 0.f;
+  // the loads of R^-1 are issued together (unrolled), behind those of the row:
+  // the prologue costs one memory latency
+  constexpr int MU = (KB * KB + TR_ROWS - 1) / TR_ROWS;
+  float mv[MU];
+#pragma unroll
+  for (int u = 0; u < MU; ++u) {
+    const int e = tid + u * TR_ROWS, c = e / KB, i = e - c * KB;
+    mv[u] = (e < KB * KB && c < K && i <= c) ? Minv[i + (int64_t)c * ldm] : 0.f;
+  }
+#pragma unroll
+  for (int u = 0; u < MU; ++u) {
+    const int e = tid + u * TR_ROWS;
+    if (e < KB * KB) Mc[e] = mv[u];
+  }
+  __syncthreads();
+  if (!live) return;
+#pragma unroll
+  for (int c = 0; c < KB; ++c) {
+    if (c < K) {
+      const float4* mc = reinterpret_cast<const float4*>(Mc + c * KB);
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int i4 = 0; i4 <= c / 4; ++i4) {
+        const float4 w = mc[i4];
+        s0 = fmaf(y[4 * i4], w.x, s0);
+        s1 = fmaf(y[4 * i4 + 1], w.y, s1);
+        s0 = fmaf(y[4 * i4 + 2], w.z, s0);
+        s1 = fmaf(y[4 * i4 + 3], w.w, s1);
+      }
+      Y[row + (int64_t)c * ld] = s0 + s1;
+    }
+  }
+}
+
 constexpr int HH_THREADS = 1024;
 constexpr int HH_GROUP = 8;
 
@@ -354,6 +411,24 @@ cudaError_t launch_trsm_rows(float* Y, int64_t m, int K, int64_t ld, const float
   if (K <= 64) return launch_trsm_kb<64>(Y, m, K, ld, L, mode, skip, stream);
   if (K <= 96) return launch_trsm_kb<96>(Y, m, K, ld, L, mode, skip, stream);
   return launch_trsm_kb<128>(Y, m, K, ld, L, mode, skip, stream);
+}
+
+template <int KB>
+static cudaError_t launch_rinv_kb(float* Y, int64_t m, int K, int64_t ld, const float* Minv, int ldm,
+                                  const DevStatus* skip, cudaStream_t stream) {
+  const unsigned grid = (unsigned)((m + TR_ROWS - 1) / TR_ROWS);
+  apply_rinv_rows_kernel<KB><<<grid, TR_ROWS, 0, stream>>>(Y, m, K, ld, Minv, ldm, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_apply_rinv_rows(float* Y, int64_t m, int K, int64_t ld, const float* Minv, int ldm,
+                                   const DevStatus* skip, cudaStream_t stream) {
+  if (m == 0) return cudaSuccess;
+  if (K < 1 || K > RHOSVD_APPLY_RINV_MAX_K || ldm < K) return cudaErrorInvalidValue;
+  if (K <= 16) return launch_rinv_kb<16>(Y, m, K, ld, Minv, ldm, skip, stream);
+  if (K <= 32) return launch_rinv_kb<32>(Y, m, K, ld, Minv, ldm, skip, stream);
+  if (K <= 48) return launch_rinv_kb<48>(Y, m, K, ld, Minv, ldm, skip, stream);
+  return launch_rinv_kb<64>(Y, m, K, ld, Minv, ldm, skip, stream);
 }
 
 cudaError_t launch_householder(float* A, int64_t m, int K, int64_t ld, DevStatus* st, bool force,

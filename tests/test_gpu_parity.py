@@ -292,7 +292,10 @@ def _orth_checks(Y, Q, fb_expected=None, fb=None):
         assert fb == fb_expected
 
 
-@pytest.mark.parametrize("m,K", [(1000, 37), (512, 42), (262144, 42), (300, 128), (65, 64)])
+# m >= 32768 takes the explicit-inverse apply (row kernel up to K = 64, one
+# case per register width and a ragged last block), shorter ones the solve
+@pytest.mark.parametrize("m,K", [(1000, 37), (512, 42), (262144, 42), (300, 128), (65, 64),
+                                 (40001, 13), (50000, 30), (33000, 64), (40000, 100)])
 def test_orth_well_conditioned(m, K):
     y = np.random.default_rng(m + K).standard_normal((m, K)).astype(np.float32)
     Q, fb = R().rhosvd_orth(torch.from_numpy(y).cuda(), report_fallback=True)
@@ -301,9 +304,10 @@ def test_orth_well_conditioned(m, K):
     assert M.max_principal_sine(host(Q), A.orth(y.astype(np.float64))) <= 1e-5
 
 
-def test_orth_ill_conditioned_cond_1e5():
+@pytest.mark.parametrize("m", [4000, 70000])
+def test_orth_ill_conditioned_cond_1e5(m):
     rng = np.random.default_rng(5)
-    u, _ = np.linalg.qr(rng.standard_normal((4000, 40)))
+    u, _ = np.linalg.qr(rng.standard_normal((m, 40)))
     v, _ = np.linalg.qr(rng.standard_normal((40, 40)))
     y = ((u * np.logspace(0, -5, 40)) @ v.T).astype(np.float32)
     Q, fb = R().rhosvd_orth(torch.from_numpy(y).cuda(), report_fallback=True)
@@ -311,7 +315,7 @@ def test_orth_ill_conditioned_cond_1e5():
     assert fb is False
 
 
-@pytest.mark.parametrize("m,K,rank", [(300, 20, 5), (20000, 24, 10)])
+@pytest.mark.parametrize("m,K,rank", [(300, 20, 5), (20000, 24, 10), (40000, 24, 10)])
 def test_orth_rank_deficient_uses_householder(m, K, rank):
     rng = np.random.default_rng(6)
     y = (rng.standard_normal((m, rank)) @ rng.standard_normal((rank, K))).astype(np.float32)
