@@ -505,7 +505,7 @@ def main():
                     help="arithmetic of the sketch passes (reduced-precision copy of X)")
     ap.add_argument("--refine", type=int, default=0, help="RP-HOOI sweeps after the decomposition")
     ap.add_argument("--kron", action="store_true", help="R-PET with Kronecker-structured factor sketches")
-    ap.add_argument("--concurrent", type=int, default=4, metavar="P",
+    ap.add_argument("--concurrent", type=int, default=8, metavar="P",
                     help="independent decompositions in flight per step (each its own tensor)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
