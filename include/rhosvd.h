@@ -295,7 +295,7 @@ typedef struct rhosvd_batch_plan {
  * each CTA takes the next tensor from a work queue (largest work first) and
  * decomposes it by itself in FP32 on the CUDA cores -- sketch and TTMs through
  * shared-memory tiles with the test matrices generated in the kernel (the same
- * values as rhosvd_decompose with the same seed: mode n on stream_id n), MGS2
+ * values as rhosvd_decompose with the same seed: mode n on stream_id n), CGS2
  * for the bases Q, one shifted CholeskyQR pass for the intermediate Z,
  * two-sided Jacobi on B B^T for the truncation.  Restrictions: opts.algo =
  * RHOSVD_ALGO_RSTHOSVD, dtype F32, no refinement or flags, q <= 8, every

@@ -6,7 +6,7 @@
 // decomposition of that tensor by itself:
 //   for n = 1..N on the current core S (geometry [L, I_n, Rt], J = L Rt):
 //     Y = S_(n) Omega_n               (Omega_n generated in the kernel, stream n)
-//     Q = orth(Y)                     (MGS2 in one warp, Y in shared memory)
+//     Q = orth(Y)                     (CGS2 by the CTA, Y in shared memory)
 //     q times: Z = S_(n)^T Q, Z = a basis of range(Z) (one shifted CholeskyQR
 //              pass, Fukaya et al. 2020), Y = S_(n) Z, Q = orth(Y)
 //     B^T = S_(n)^T Q, G = B B^T, eigenvectors of G (two-sided Jacobi in one
@@ -340,45 +340,74 @@ __device__ void blk_gram(const float* __restrict__ Z, int64_t J, int K, const BS
   __syncthreads();
 }
 
-// Q = orth(Y) in place for Y (I x K, column-major, ld `ld`) in shared memory, by
-// one warp: modified Gram-Schmidt with one reorthogonalisation ("twice is
-// enough", Giraud, Langou, Rozloznik 2005).  A column left at rounding level by
-// the projections (rank below K) is replaced by the next unit vector that is
-// still independent of the columns before it, orthogonalised the same way.
-// Returns false if a column norm was not finite.
-__device__ bool warp_mgs2(float* Y, int ld, int I, int K) {
-  const int lane = threadIdx.x & 31;
+
+// ||y||^2 (y of length I in shared memory) by the whole CTA, summed in a
+// fixed order; every thread returns the same value.  wp: T/32 floats.
+template <int T>
+__device__ float blk_norm2(const float* y, int I, float* wp) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float s = 0.f;
+  for (int i = tid; i < I; i += T) s = fmaf(y[i], y[i], s);
+  s = warp_sum(s);
+  __syncthreads();                                  // earlier readers of wp are done
+  if (lane == 0) wp[warp] = s;
+  __syncthreads();
+  float t = 0.f;
+#pragma unroll
+  for (int w = 0; w < T / 32; ++w) t += wp[w];
+  return t;
+}
+
+// Q = orth(Y) in place for Y (I x K, column-major, ld `ld`) in shared memory,
+// by the whole CTA: classical Gram-Schmidt with one reorthogonalisation per
+// column (CGS2; Giraud, Langou, Rozloznik, van den Eshof 2005: orthogonal to
+// working precision, like MGS2), the projections on all earlier columns of a
+// pass computed together, one warp per column.  A column left at rounding
+// level by the projections (rank below K) is replaced by the next unit vector
+// that is still independent of the columns before it, orthogonalised the same
+// way.  `red` holds 32 + T/32 floats of scratch.  Returns false (on every
+// thread) if a column norm was not finite.
+template <int T>
+__device__ bool blk_cgs2(float* Y, int ld, int I, int K, float* red) {
+  constexpr int NW = T / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* d = red;                                   // projections d_c, c < k <= 32
+  float* wp = red + 32;                             // per-warp partial sums
   bool finite = true;
   int e_next = 0;
   for (int k = 0; k < K; ++k) {
     float* y = Y + (size_t)ld * k;
-    float n0 = 0.f;
-    for (int i = lane; i < I; i += 32) n0 = fmaf(y[i], y[i], n0);
-    n0 = warp_sum(n0);
+    float n0 = blk_norm2<T>(y, I, wp);
     if (!isfinite(n0)) finite = false;
     float n1 = 0.f;
     for (int attempt = 0;; ++attempt) {
-      for (int pass = 0; pass < 2; ++pass)
-        for (int c = 0; c < k; ++c) {
+      for (int pass = 0; pass < 2 && k > 0; ++pass) {
+        for (int c = warp; c < k; c += NW) {        // d_c = q_c^T y
           const float* qc = Y + (size_t)ld * c;
-          float d = 0.f;
-          for (int i = lane; i < I; i += 32) d = fmaf(qc[i], y[i], d);
-          d = warp_sum(d);
-          for (int i = lane; i < I; i += 32) y[i] = fmaf(-d, qc[i], y[i]);
+          float v = 0.f;
+          for (int i = lane; i < I; i += 32) v = fmaf(qc[i], y[i], v);
+          v = warp_sum(v);
+          if (lane == 0) d[c] = v;
         }
-      n1 = 0.f;
-      for (int i = lane; i < I; i += 32) n1 = fmaf(y[i], y[i], n1);
-      n1 = warp_sum(n1);
+        __syncthreads();
+        for (int i = tid; i < I; i += T) {          // y -= Q(:, 0:k) d
+          float v = y[i];
+          for (int c = 0; c < k; ++c) v = fmaf(-d[c], Y[i + (size_t)ld * c], v);
+          y[i] = v;
+        }
+        __syncthreads();
+      }
+      n1 = blk_norm2<T>(y, I, wp);
       if ((n1 > 1e-11f * n0 && n1 > 0.f && isfinite(n1)) || e_next >= I || attempt > I) break;
       // dependent (or non-finite) column: restart from the next unit vector
-      for (int i = lane; i < I; i += 32) y[i] = (i == e_next) ? 1.f : 0.f;
+      for (int i = tid; i < I; i += T) y[i] = (i == e_next) ? 1.f : 0.f;
       ++e_next;
       n0 = 1.f;
-      __syncwarp();
+      __syncthreads();
     }
     const float inv = (n1 > 0.f && isfinite(n1)) ? rsqrtf(n1) : 0.f;
-    for (int i = lane; i < I; i += 32) y[i] *= inv;
-    __syncwarp();
+    for (int i = tid; i < I; i += T) y[i] *= inv;
+    __syncthreads();
   }
   return finite;
 }
@@ -387,31 +416,57 @@ __device__ bool warp_mgs2(float* Y, int ld, int I, int K) {
 // memory: for every pair (p, q, c, s) of the round, columns p and q become
 // c a_p - s a_q and s a_p + c a_q; lane r takes row r.
 __device__ __forceinline__ void rotate_cols(float* A, int kp, int K, const float4* rot, int npairs) {
+  // the pairs of a round are disjoint: every element is loaded before the first
+  // store, so the round costs one shared-memory latency rather than one per pair
+  constexpr int NP = BT_MAX_K / 2;
   const int r = threadIdx.x & 31;
-  if (r < K)
-    for (int w = 0; w < npairs; ++w) {
+  if (r < K) {
+    float gp[NP], gq[NP];
+#pragma unroll
+    for (int w = 0; w < NP; ++w) {
+      const float4 t = rot[w < npairs ? w : 0];
+      const int p = __float_as_int(t.x), q = __float_as_int(t.y);
+      const bool live = w < npairs && q >= 0;
+      gp[w] = live ? A[r + kp * p] : 0.f;
+      gq[w] = live ? A[r + kp * q] : 0.f;
+    }
+#pragma unroll
+    for (int w = 0; w < NP; ++w) {
+      if (w >= npairs) break;
       const float4 t = rot[w];
       const int p = __float_as_int(t.x), q = __float_as_int(t.y);
       if (q < 0) continue;
-      const float gp = A[r + kp * p], gq = A[r + kp * q];
-      A[r + kp * p] = t.z * gp - t.w * gq;
-      A[r + kp * q] = t.w * gp + t.z * gq;
+      A[r + kp * p] = t.z * gp[w] - t.w * gq[w];
+      A[r + kp * q] = t.w * gp[w] + t.z * gq[w];
     }
+  }
   __syncwarp();
 }
 
 // The row sweep of the same round (rows p and q); lane c takes column c.
 __device__ __forceinline__ void rotate_rows(float* A, int kp, int K, const float4* rot, int npairs) {
+  constexpr int NP = BT_MAX_K / 2;
   const int col = threadIdx.x & 31;
-  if (col < K)
-    for (int w = 0; w < npairs; ++w) {
+  if (col < K) {
+    float gp[NP], gq[NP];
+#pragma unroll
+    for (int w = 0; w < NP; ++w) {
+      const float4 t = rot[w < npairs ? w : 0];
+      const int p = __float_as_int(t.x), q = __float_as_int(t.y);
+      const bool live = w < npairs && q >= 0;
+      gp[w] = live ? A[p + kp * col] : 0.f;
+      gq[w] = live ? A[q + kp * col] : 0.f;
+    }
+#pragma unroll
+    for (int w = 0; w < NP; ++w) {
+      if (w >= npairs) break;
       const float4 t = rot[w];
       const int p = __float_as_int(t.x), q = __float_as_int(t.y);
       if (q < 0) continue;
-      const float gp = A[p + kp * col], gq = A[q + kp * col];
-      A[p + kp * col] = t.z * gp - t.w * gq;
-      A[q + kp * col] = t.w * gp + t.z * gq;
+      A[p + kp * col] = t.z * gp[w] - t.w * gq[w];
+      A[q + kp * col] = t.w * gp[w] + t.z * gq[w];
     }
+  }
   __syncwarp();
 }
 
@@ -525,7 +580,8 @@ __device__ bool warp_chol_inv(float* A, float* Linv, int kp, int K, float shift)
 // one shifted CholeskyQR pass (Fukaya, Kannan, Nakatsukasa, Yamamoto,
 // Yanagisawa 2020).  The power iteration needs only range(Z); the shift keeps
 // the FP32 factorisation from breaking down whatever cond(Z), and the next
-// basis is formed by MGS2, which any conditioning of Y = S_(n) Z survives.
+// basis is formed by CGS2 with dependent columns replaced, which any
+// conditioning of Y = S_(n) Z survives.
 // Returns false (Z unchanged) if the factorisation failed.
 template <int T>
 __device__ bool blk_range_basis(float* __restrict__ Z, int64_t J, int K, const BSmem& sm, float* smf) {
@@ -606,15 +662,13 @@ __device__ void decompose_one(const BItem* __restrict__ it, int q, uint64_t seed
     }
     // Y = S_(n) Omega_n, Q = orth(Y)
     blk_sketch<T>(cur, L, I, J, K, nullptr, seed, (uint32_t)n, sm, smf);
-    if (tid < 32 && !warp_mgs2(Ys, sm.ip, (int)I, K) && tid == 0) set_error(st, RHOSVD_ENONFINITE);
-    __syncthreads();
+    if (!blk_cgs2<T>(Ys, sm.ip, (int)I, K, smf + sm.red) && tid == 0) set_error(st, RHOSVD_ENONFINITE);
     for (int p = 0; p < q; ++p) {
       q_to_rowmajor<T>(sm, smf, (int)I, K);
       blk_ttm<T>(cur, L, I, J, K, Zb, sm, smf);            // Z = S_(n)^T Q
       blk_range_basis<T>(Zb, J, K, sm, smf);                     // a basis of range(Z)
       blk_sketch<T>(cur, L, I, J, K, Zb, seed, 0, sm, smf);   // Y = S_(n) Z
-      if (tid < 32 && !warp_mgs2(Ys, sm.ip, (int)I, K) && tid == 0) set_error(st, RHOSVD_ENONFINITE);
-      __syncthreads();
+      if (!blk_cgs2<T>(Ys, sm.ip, (int)I, K, smf + sm.red) && tid == 0) set_error(st, RHOSVD_ENONFINITE);
     }
     // B^T = S_(n)^T Q, G = B B^T, leading eigenvectors Ubar_R
     q_to_rowmajor<T>(sm, smf, (int)I, K);
