@@ -333,6 +333,28 @@ def run_serving(args):
         rk = [r for r in res if not fixed_acc[r.rid]]
         if rk:
             line[f"slots{slots}"]["fixed_rank"] = serving.latency_summary(rk)
+    if not args.no_cpu_baseline:
+        # the FP64 oracle on one fixed-rank request (rank 32, p = 10, q = 1) per size bucket
+        # of the stream, one after another on the host cores
+        from oracle import algorithms as A
+        from oracle import philox
+        per_size = {}
+        for I in (64, 128, 256, 512, 768):
+            if I not in pool:
+                continue
+            x = pool[I].numpy().astype(np.float64).reshape((I, I, I), order="F")
+            rk3 = (min(32, I),) * 3
+            t0 = time.perf_counter()
+            om = [philox.omega(0, m, r, c).astype(np.float64)
+                  for m, (r, c) in enumerate(A.omega_shapes("rsthosvd", (I,) * 3, rk3, 10))]
+            A.rsthosvd(x, rk3, 1, om)
+            per_size[str(I)] = time.perf_counter() - t0
+            del x
+        if per_size:
+            line["cpu_baseline"] = {"value": len(per_size) / sum(per_size.values()), "unit": "requests/s",
+                                    "cores": _CORES, "kind": "oracle",
+                                    "sample": "one fixed-rank request (rank 32) per size bucket, serially",
+                                    "seconds_per_request": per_size}
     print(json.dumps(line), flush=True)
 
 
@@ -419,6 +441,20 @@ def run_batch(args):
     for (g, us), it in zip(persistent.results(), persistent.items):
         e_pers.append(rel_err(it[0], it[1], g, us))
     e_graph, e_pers = np.array(e_graph), np.array(e_pers)
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the FP64 oracle's R-STHOSVD (same test matrices) on the first 64 tensors, one after another
+        from oracle import algorithms as A
+        from oracle import philox
+        ns = min(n, 64)
+        hosts = [(X.double().cpu().numpy().reshape(dims, order="F"), dims, rk) for X, dims, rk in items[:ns]]
+        t0 = time.perf_counter()
+        for x, dims, rk in hosts:
+            om = [philox.omega(0, m, r, c).astype(np.float64)
+                  for m, (r, c) in enumerate(A.omega_shapes("rsthosvd", dims, rk, 5))]
+            A.rsthosvd(x, rk, 1, om)
+        cpu = {"value": ns / (time.perf_counter() - t0), "unit": "decomps/s", "cores": _CORES, "kind": "oracle",
+               "sample": f"the first {ns} of the {n} tensors, one after another (FP64 NumPy)"}
     print(json.dumps({"mode": "batch", "tensors": n, "sizes": "each mode uniform in [16, 96]",
                       "ranks": "uniform in [4, 16], capped", "algo": "rsthosvd p=5 q=1",
                       "graph_chunk": chunk, "branches": 16, **rates,
@@ -430,7 +466,7 @@ def run_batch(args):
                       "rel_error_graph_mean": float(e_graph.mean()),
                       "rel_error_persistent_mean": float(e_pers.mean()),
                       "rel_error_max_abs_diff": float(np.max(np.abs(e_pers - e_graph))),
-                      "device_status": status}), flush=True)
+                      "device_status": status, "cpu_baseline": cpu}), flush=True)
 
 
 def run_primitive(args, w):
