@@ -374,7 +374,10 @@ def run_batch(args):
         dims = tuple(int(v) for v in rng.integers(16, 97, size=3))
         ranks = tuple(int(min(r, d)) for r, d in zip(rng.integers(4, 17, size=3), dims))
         core = torch.randn(*ranks, device="cuda", generator=g)
-        U = [torch.linalg.qr(torch.randn(d, r, device="cuda", generator=g))[0] for d, r in zip(dims, ranks)]
+        # the orthonormal factors come from a host QR (the device linear-algebra
+        # library does not load under the profiler)
+        U = [torch.linalg.qr(torch.randn(d, r, device="cuda", generator=g).cpu())[0].cuda()
+             for d, r in zip(dims, ranks)]
         x = torch.einsum("abc,ia,jb,kc->kji", core, U[0], U[1], U[2])
         noise = torch.randn(x.shape, device="cuda", generator=g)
         x = x + 1e-3 * x.norm() / noise.norm() * noise

@@ -95,6 +95,8 @@ def test_persistent_batch_of_small_uneven_tensors_matches_oracle():
     ((40, 30, 16), (6, 5, 16), 5, 2),             # last mode skipped, two power steps
     ((200, 24), (7, 7), 6, 0),                    # 2-way, a 200-row mode, no power step
     ((33, 17, 65), (5, 4, 6), 3, 1),              # odd sizes, ragged tiles
+    ((256, 24, 10), (6, 5, 4), 5, 1),             # the largest mode size (shared-memory bound)
+    ((256, 256), (20, 20), 6, 1),                 # 2-way, both modes at the limit, K = 26
 ])
 def test_persistent_batch_shapes(dims, ranks, p, q):
     x = lowrank_tensor(dims, ranks, 77, noise=1e-3)
