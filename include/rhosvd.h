@@ -56,7 +56,7 @@ typedef enum rhosvd_status {
   RHOSVD_ENONFINITE = 4,    /* a NaN/Inf reached a sketch or Gram matrix */
   RHOSVD_EBREAKDOWN = 5,    /* orthonormalisation failed even after the fallback */
   RHOSVD_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
-  RHOSVD_EUNSUPPORTED = 7   /* valid request outside what this build implements */
+  RHOSVD_EUNSUPPORTED = 7   /* valid request outside what the library implements */
 } rhosvd_status;
 
 typedef enum rhosvd_algo {
