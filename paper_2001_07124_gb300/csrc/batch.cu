@@ -60,7 +60,7 @@ struct BSmem {
   __host__ __device__ BSmem(int imax, int kmax, int jc_, int T_) : jc(jc_), T(T_) {
     ip = imax | 1;                                  // odd pitch: conflict-free both ways
     kp = (kmax + 3) & ~3;
-    arow = ip > kp ? ip : kp;
+    arow = ip > kp + 1 ? ip : kp + 1;              // room for the odd-pitch Z tiles
     abuf = (jc * arow + 3) & ~3;
     wbuf = jc * kp;
     int o = 0;
@@ -126,34 +126,39 @@ __device__ __forceinline__ void stage_s_tile(const float* S, int64_t L, int I, i
   }
 }
 
-// Start copying rows j0..j0+jc of the J x K matrix Z (ld J) to Zs[jj * kp + k]
-// (zeros past J and for K <= k < kp).
+// Start copying rows j0..j0+jc of the J x K matrix Z (ld J) to Zs[jj * pitch + k]
+// for k < kfill (zeros past J and for K <= k < kfill).
 template <int T>
-__device__ __forceinline__ void stage_z_tile(const float* Z, int64_t J, int K, int64_t j0, int jc, int kp,
-                                             float* Zs) {
+__device__ __forceinline__ void stage_z_tile(const float* Z, int64_t J, int K, int64_t j0, int jc, int kfill,
+                                             int pitch, float* Zs) {
   const int tid = threadIdx.x;
   const int jj = tid % jc;
   const bool row_ok = jj < tile_cols(J, j0, jc);
-  for (int k = tid / jc; k < kp; k += T / jc) {
+  for (int k = tid / jc; k < kfill; k += T / jc) {
     const bool ok = row_ok && k < K;
-    cp_async_f32(Zs + jj * kp + k, ok ? Z + (j0 + jj) + J * k : Z, ok);
+    cp_async_f32(Zs + jj * pitch + k, ok ? Z + (j0 + jj) + J * k : Z, ok);
   }
 }
 
 // body(j0, nj, Zs) for every row tile of Z (ld J) staged in shared memory, the
-// next tile copied in while body runs on the current one.
+// next tile copied in while body runs on the current one.  A tile row holds
+// K_pad = kp columns at pitch kp when the body reads float4 (zero-filled past
+// K), or the K columns at the odd pitch kp + 1 (odd_pitch) when it reads single
+// words with lanes on consecutive rows: then neither the copies nor the reads
+// conflict in shared-memory banks.
 template <int T, class F>
 __device__ __forceinline__ void stream_z_tiles(const float* Z, int64_t J, int K, const BSmem& sm, float* smf,
-                                               F&& body) {
+                                               bool odd_pitch, F&& body) {
   const int jc = sm.jc, kp = sm.kp;
+  const int pitch = odd_pitch ? kp + 1 : kp, kfill = odd_pitch ? K : kp;
   const int ntiles = (int)((J + jc - 1) / jc);
   __syncthreads();                                  // the staging buffers are free
-  stage_z_tile<T>(Z, J, K, 0, jc, kp, smf + sm.as);
+  stage_z_tile<T>(Z, J, K, 0, jc, kfill, pitch, smf + sm.as);
   cp_async_commit();
   for (int t = 0; t < ntiles; ++t) {
     const int b = t & 1;
     const int64_t j0 = (int64_t)t * jc;
-    if (t + 1 < ntiles) stage_z_tile<T>(Z, J, K, j0 + jc, jc, kp, smf + sm.as + (b ^ 1) * sm.abuf);
+    if (t + 1 < ntiles) stage_z_tile<T>(Z, J, K, j0 + jc, jc, kfill, pitch, smf + sm.as + (b ^ 1) * sm.abuf);
     cp_async_commit();
     cp_async_wait_one();
     __syncthreads();
@@ -180,7 +185,7 @@ __device__ void blk_sketch(const float* S, int64_t L, int64_t I, int64_t J, int 
     for (int t = 0; t < 4; ++t) acc[u][t] = 0.f;
   __syncthreads();                                  // the staging buffers are free
   stage_s_tile<T>(S, L, (int)I, J, 0, jc, smf + sm.as, arow);
-  if (Zg != nullptr) stage_z_tile<T>(Zg, J, K, 0, jc, kp, smf + sm.ws);
+  if (Zg != nullptr) stage_z_tile<T>(Zg, J, K, 0, jc, kp, kp, smf + sm.ws);
   cp_async_commit();
   for (int t = 0; t < ntiles; ++t) {
     const int b = t & 1;
@@ -189,7 +194,7 @@ __device__ void blk_sketch(const float* S, int64_t L, int64_t I, int64_t J, int 
     float* Ws = smf + sm.ws + b * sm.wbuf;
     if (t + 1 < ntiles) {                           // the next tile streams in meanwhile
       stage_s_tile<T>(S, L, (int)I, J, j0 + jc, jc, smf + sm.as + (b ^ 1) * sm.abuf, arow);
-      if (Zg != nullptr) stage_z_tile<T>(Zg, J, K, j0 + jc, jc, kp, smf + sm.ws + (b ^ 1) * sm.wbuf);
+      if (Zg != nullptr) stage_z_tile<T>(Zg, J, K, j0 + jc, jc, kp, kp, smf + sm.ws + (b ^ 1) * sm.wbuf);
     }
     cp_async_commit();
     if (Zg == nullptr) {
@@ -310,7 +315,7 @@ __device__ void blk_gram(const float* __restrict__ Z, int64_t J, int K, const BS
   float acc[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) acc[e] = 0.f;
-  stream_z_tiles<T>(Z, J, K, sm, smf, [&](int64_t, int nj, const float* Zs) {
+  stream_z_tiles<T>(Z, J, K, sm, smf, false, [&](int64_t, int nj, const float* Zs) {
     if (active)
       for (int jj = ph; jj < nj; jj += phases) {
         const float4 a = *reinterpret_cast<const float4*>(Zs + jj * kp + 4 * bi);
@@ -600,13 +605,13 @@ __device__ bool blk_range_basis(float* __restrict__ Z, int64_t J, int K, const B
   __syncthreads();
   const bool ok = *flag != 0;
   if (ok) {
-    // Z <- Z L^-T tile by tile: rows staged in shared memory ([jj][k], pitch kp);
+    // Z <- Z L^-T tile by tile: rows staged in shared memory ([jj][k], pitch kp + 1);
     // a tile is rewritten in place while the next one is copied in
-    stream_z_tiles<T>(Z, J, K, sm, smf, [&](int64_t j0, int nj, const float* Zs) {
+    stream_z_tiles<T>(Z, J, K, sm, smf, true, [&](int64_t j0, int nj, const float* Zs) {
       for (int e = tid; e < nj * K; e += T) {
         const int jj = e % nj, k = e / nj;
         float v = 0.f;
-        for (int c = 0; c <= k; ++c) v = fmaf(Zs[jj * kp + c], Li[k + kp * c], v);
+        for (int c = 0; c <= k; ++c) v = fmaf(Zs[jj * (kp + 1) + c], Li[k + kp * c], v);
         Z[(j0 + jj) + J * k] = v;
       }
     });
@@ -702,13 +707,13 @@ __device__ void decompose_one(const BItem* __restrict__ it, int q, uint64_t seed
       U[e] = v;
     }
     // S_new[l + L a + L R r] = sum_k Ubar(k, a) B^T(l + L r, k): rows of B^T staged
-    // in shared memory ([jj][k], pitch kp), one output (j, a) per thread and step
+    // in shared memory ([jj][k], pitch kp + 1), one output (j, a) per thread and step
     float* dst = last ? G : (ping ? Sb1 : Sb0);
-    stream_z_tiles<T>(Zb, J, K, sm, smf, [&](int64_t j0, int nj, const float* Bs) {
+    stream_z_tiles<T>(Zb, J, K, sm, smf, true, [&](int64_t j0, int nj, const float* Bs) {
       for (int e = tid; e < nj * R; e += T) {
         const int jj = e % nj, a = e / nj;
         float v = 0.f;
-        for (int k = 0; k < K; ++k) v = fmaf(Bs[jj * kp + k], Ub[k + kp * a], v);
+        for (int k = 0; k < K; ++k) v = fmaf(Bs[jj * (kp + 1) + k], Ub[k + kp * a], v);
         const int64_t j = j0 + jj, l = j % L, r = j / L;
         dst[l + L * a + L * R * r] = v;
       }
