@@ -33,7 +33,7 @@ namespace rhosvd {
 
 namespace {
 
-constexpr int BT_GMAX = 8;      // sketch output groups (1 row x 4 columns) per thread, at most
+constexpr int BT_GMAX = 4;      // sketch output groups (1 row x 8 columns) per thread, at most
 constexpr int BT_TMAX = 4;      // TTM output groups per thread, at most
 constexpr int BT_MAX_I = 256;   // largest mode size of a batched tensor
 constexpr int BT_MAX_K = 32;    // largest sketch width
@@ -176,13 +176,13 @@ __device__ void blk_sketch(const float* S, int64_t L, int64_t I, int64_t J, int 
   float* Ys = smf + sm.ys;
   const int tid = threadIdx.x, jc = sm.jc, kp = sm.kp, arow = sm.arow;
   const int kg = (K + 3) / 4;
-  const int ng = (int)I * kg;
+  const int ng = (int)I * ((kg + 1) / 2);           // groups of one row and 8 columns
   const int ntiles = (int)((J + jc - 1) / jc);
-  float acc[BT_GMAX][4];
+  float acc[BT_GMAX][8];
 #pragma unroll
   for (int u = 0; u < BT_GMAX; ++u)
 #pragma unroll
-    for (int t = 0; t < 4; ++t) acc[u][t] = 0.f;
+    for (int t = 0; t < 8; ++t) acc[u][t] = 0.f;
   __syncthreads();                                  // the staging buffers are free
   stage_s_tile<T>(S, L, (int)I, J, 0, jc, smf + sm.as, arow);
   if (Zg != nullptr) stage_z_tile<T>(Zg, J, K, 0, jc, kp, kp, smf + sm.ws);
@@ -213,15 +213,34 @@ __device__ void blk_sketch(const float* S, int64_t L, int64_t I, int64_t J, int 
     for (int u = 0; u < BT_GMAX; ++u) {
       const int g = tid + T * u;
       if (g < ng) {
-        const int i = g % (int)I, c = g / (int)I;
+        // one row i against two 4-column groups of W: a shared load of S_(n)
+        // serves 8 multiply-adds (the second group is absent at an odd kg)
+        const int i = g % (int)I, c = 2 * (g / (int)I);
+        if (c + 1 < kg) {
 #pragma unroll 8
-        for (int jj = 0; jj < jc; ++jj) {
-          const float a = As[jj * arow + i];
-          const float4 w = *reinterpret_cast<const float4*>(Ws + jj * kp + 4 * c);
-          acc[u][0] = fmaf(a, w.x, acc[u][0]);
-          acc[u][1] = fmaf(a, w.y, acc[u][1]);
-          acc[u][2] = fmaf(a, w.z, acc[u][2]);
-          acc[u][3] = fmaf(a, w.w, acc[u][3]);
+          for (int jj = 0; jj < jc; ++jj) {
+            const float a = As[jj * arow + i];
+            const float4 w0 = *reinterpret_cast<const float4*>(Ws + jj * kp + 4 * c);
+            const float4 w1 = *reinterpret_cast<const float4*>(Ws + jj * kp + 4 * c + 4);
+            acc[u][0] = fmaf(a, w0.x, acc[u][0]);
+            acc[u][1] = fmaf(a, w0.y, acc[u][1]);
+            acc[u][2] = fmaf(a, w0.z, acc[u][2]);
+            acc[u][3] = fmaf(a, w0.w, acc[u][3]);
+            acc[u][4] = fmaf(a, w1.x, acc[u][4]);
+            acc[u][5] = fmaf(a, w1.y, acc[u][5]);
+            acc[u][6] = fmaf(a, w1.z, acc[u][6]);
+            acc[u][7] = fmaf(a, w1.w, acc[u][7]);
+          }
+        } else {
+#pragma unroll 8
+          for (int jj = 0; jj < jc; ++jj) {
+            const float a = As[jj * arow + i];
+            const float4 w0 = *reinterpret_cast<const float4*>(Ws + jj * kp + 4 * c);
+            acc[u][0] = fmaf(a, w0.x, acc[u][0]);
+            acc[u][1] = fmaf(a, w0.y, acc[u][1]);
+            acc[u][2] = fmaf(a, w0.z, acc[u][2]);
+            acc[u][3] = fmaf(a, w0.w, acc[u][3]);
+          }
         }
       }
     }
@@ -231,9 +250,9 @@ __device__ void blk_sketch(const float* S, int64_t L, int64_t I, int64_t J, int 
   for (int u = 0; u < BT_GMAX; ++u) {
     const int g = tid + T * u;
     if (g < ng) {
-      const int i = g % (int)I, c = g / (int)I;
+      const int i = g % (int)I, c = 2 * (g / (int)I);
 #pragma unroll
-      for (int t = 0; t < 4; ++t)
+      for (int t = 0; t < 8; ++t)
         if (4 * c + t < K) Ys[i + sm.ip * (4 * c + t)] = acc[u][t];
     }
   }
@@ -833,7 +852,7 @@ int resident_ctas(const rhosvd_batch_plan& p, int threads, int jc) {
   const void* k = kernel_of(threads);
   if (k == nullptr || (jc != 32 && jc != 64)) return 0;
   const int kg = (p.kmax + 3) / 4;
-  if (p.imax * kg > BT_GMAX * threads || jc * kg > BT_TMAX * threads) return 0;
+  if (p.imax * ((kg + 1) / 2) > BT_GMAX * threads || jc * kg > BT_TMAX * threads) return 0;
   const size_t smem = smem_bytes(p, threads, jc);
   if (smem > 200 * 1024) return 0;
   if (allow_dynamic_smem(k, smem) != cudaSuccess) return 0;
