@@ -27,7 +27,7 @@ def test_reference_arm_prints_one_contract_line():
     for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
                 "dtype", "data", "config", "cpu_baseline", "e2e"):
         assert key in d, key
-    assert d["steps"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
+    assert d["steps"] == 2 and d["steps_requested"] == 2 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["higher_is_better"] is True and d["value"] > 0
     assert abs(d["ms_per_step"] - 1e3 / d["value"]) <= 1e-6 * d["ms_per_step"]
     assert d["config"]["workload"] == "lowrank100_rhosvd"
